@@ -1,0 +1,369 @@
+/*
+ * FP64 CPU oracle for (Fast) Iterative Filtering -- TEST INFRASTRUCTURE ONLY.
+ * See fif_oracle.h for the contract.  Every routine here is deliberately the
+ * plain, slow form of its definition: no blocking, no fusion, no reordering
+ * beyond what the cited passage states.
+ *
+ * Readings of the paper that this file implements (the paper is silent or
+ * ambiguous on these points):
+ *  - periodic sampling x_j = j/n for any n (Sec. 3 uses j/(n-1), n odd);
+ *  - the discrete triangle is the continuous triangle of eq. triangular with
+ *    half-support L sampled at integer offsets: c_d = (L-|d|)/L^2, |d| < L,
+ *    then normalised by its sum as Sec. 3 says the implemented code does;
+ *  - an extremum of the periodic sequence r is an index i with
+ *    d_{i-1} d_i < 0, d_i = r[(i+1) mod n] - r[i]; flat steps count none;
+ *  - L = mask_scale * floor(nu*n/k) evaluated in binary64 as ((nu*n)/k),
+ *    clamped to 2; the loop stops when 2L-1 > n (window wider than the
+ *    period, Sec. 3.1 asks l <= (n-1)/2);
+ *  - m counts applications of (I-W); SD_j compares iterates j and j-1;
+ *    m = first j in [1, max_inner] with SD_j < delta, else max_inner;
+ *  - 0^0 = 1 (the DC bin keeps weight 1 at j = 1).
+ */
+#include "fif_oracle.h"
+
+#ifndef M_PI
+#define M_PI 3.14159265358979323846
+#endif
+
+#include <complex.h>
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* ------------------------------------------------------------------ DFT */
+
+/* Definition of the DFT, O(n^2): X_k = sum_j x_j exp(sign*2*pi*i*j*k/n).
+ * The product j*k is reduced mod n in integers before the angle is formed. */
+void fifo_dft_bruteforce(const double* re, const double* im, long n, int sign, double* ore,
+                         double* oim) {
+  for (long k = 0; k < n; k++) {
+    double sr = 0.0, si = 0.0;
+    for (long j = 0; j < n; j++) {
+      long q = (long)(((long long)j * (long long)k) % (long long)n);
+      double a = (double)sign * 2.0 * M_PI * (double)q / (double)n;
+      double c = cos(a), s = sin(a);
+      double xr = re[j], xi = im ? im[j] : 0.0;
+      sr += xr * c - xi * s;
+      si += xr * s + xi * c;
+    }
+    ore[k] = sr;
+    oim[k] = si;
+  }
+}
+
+static long smallest_prime_factor(long n) {
+  for (long p = 2; p * p <= n; p++)
+    if (n % p == 0) return p;
+  return n;
+}
+
+/* Recursive decimation in time on the smallest prime factor p of n:
+ * with j = p*t + r,  X_k = sum_r w_n^{r k} Y_r[k mod m],  m = n/p,
+ * Y_r = DFT_m of the subsequence x[r], x[r+p], ...  (Cooley-Tukey). */
+static void fft_rec(const double complex* in, long stride, long n, int sign, double complex* out,
+                    double complex* tmp) {
+  if (n == 1) {
+    out[0] = in[0];
+    return;
+  }
+  long p = smallest_prime_factor(n), m = n / p;
+  for (long r = 0; r < p; r++) fft_rec(in + r * stride, stride * p, m, sign, out + r * m, tmp);
+  for (long k = 0; k < n; k++) {
+    double complex acc = 0.0;
+    for (long r = 0; r < p; r++) {
+      long q = (long)(((long long)r * (long long)k) % (long long)n);
+      double a = (double)sign * 2.0 * M_PI * (double)q / (double)n;
+      acc += (cos(a) + I * sin(a)) * out[r * m + (k % m)];
+    }
+    tmp[k] = acc;
+  }
+  memcpy(out, tmp, (size_t)n * sizeof(double complex));
+}
+
+int fifo_fft(double* re, double* im, long n, int sign) {
+  if (n < 1) return -1;
+  double complex* x = malloc((size_t)n * sizeof(double complex));
+  double complex* y = malloc((size_t)n * sizeof(double complex));
+  double complex* t = malloc((size_t)n * sizeof(double complex));
+  if (!x || !y || !t) {
+    free(x), free(y), free(t);
+    return -2;
+  }
+  for (long j = 0; j < n; j++) x[j] = re[j] + I * (im ? im[j] : 0.0);
+  fft_rec(x, 1, n, sign, y, t);
+  for (long j = 0; j < n; j++) {
+    re[j] = creal(y[j]);
+    if (im) im[j] = cimag(y[j]);
+  }
+  free(x), free(y), free(t);
+  return 0;
+}
+
+/* ------------------------------------------------------ window and mask */
+
+/* Triangle of eq. triangular with half-support L, sampled at the integer
+ * offsets d (|d| < L), stored circularly at index d mod n, then divided by
+ * its sum so that W is row stochastic (Sec. 3, rectangle-rule remark). */
+void fifo_triangle_taps(long n, int L, double* c) {
+  for (long i = 0; i < n; i++) c[i] = 0.0;
+  double sum = 0.0;
+  for (long d = -(L - 1); d <= L - 1; d++) {
+    double v = ((double)L - fabs((double)d)) / ((double)L * (double)L);
+    long idx = ((d % n) + n) % n;
+    c[idx] += v;
+    sum += v;
+  }
+  for (long i = 0; i < n; i++) c[i] /= sum;
+}
+
+/* |sin(pi*q/n)| for an integer q, with the argument reduced exactly. */
+static double abs_sinpi_ratio(long long q, long n) {
+  long long t = q % (long long)n;
+  if (t < 0) t += n;
+  if (t > n - t) t = n - t; /* |sin| is symmetric about n/2 */
+  return sin(M_PI * (double)t / (double)n);
+}
+
+/* Eigenvalues of the circulant W built from the triangle taps (eq. Lambdas,
+ * eq. eig2).  The taps are the autocorrelation of a length-L box, so
+ * lambda_k = |DFT(box)_k|^2 = [sin(pi k L/n) / (L sin(pi k/n))]^2, lambda_0
+ * = 1 (the discrete counterpart of eq. triangular_fourier).  Clamped to
+ * [0, 1] (Corollary 2). */
+void fifo_window_spectrum(long n, int L, double* w) {
+  for (long k = 0; k < n; k++) {
+    double v;
+    if (k == 0) {
+      v = 1.0;
+    } else {
+      double num = abs_sinpi_ratio((long long)k * (long long)L, n);
+      double den = (double)L * abs_sinpi_ratio(k, n);
+      v = (num / den) * (num / den);
+    }
+    if (v > 1.0) v = 1.0;
+    if (v < 0.0) v = 0.0;
+    w[k] = v;
+  }
+}
+
+long fifo_count_extrema(const double* r, long n) {
+  long count = 0;
+  for (long i = 0; i < n; i++) {
+    double dprev = r[i] - r[(i - 1 + n) % n];
+    double dnext = r[(i + 1) % n] - r[i];
+    if ((dprev > 0.0 && dnext < 0.0) || (dprev < 0.0 && dnext > 0.0)) count++;
+  }
+  return count;
+}
+
+long fifo_count_zero_crossings(const double* r, long n) {
+  long count = 0;
+  for (long i = 0; i < n; i++) {
+    double a = r[i], b = r[(i + 1) % n];
+    if ((a > 0.0 && b < 0.0) || (a < 0.0 && b > 0.0)) count++;
+  }
+  return count;
+}
+
+/* eq. Unif_Mask_length, l = 2 floor(nu N / k); mask_scale selects the
+ * leading factor (1 = half-support L = floor(nu n/k)). */
+int fifo_mask_length(long n, long k, double nu, int mask_scale) {
+  double t = nu * (double)n;
+  t = t / (double)k;
+  return mask_scale * (int)floor(t);
+}
+
+/* ------------------------------------------------------------ outer loop */
+
+static int check_args(const double* s, long n, const fifo_params* p, const fifo_outputs* o) {
+  if (!s || n < 1 || !p || !o || !o->imfs || !o->m || !o->L || !o->kext || !o->n_imfs ||
+      !o->status || !o->sd_m || !o->sd_prev)
+    return -1;
+  if (!(p->delta > 0.0) || p->max_inner < 1 || p->max_imfs < 0) return -1;
+  if (!p->L_in && (!(p->nu > 0.0) || p->mask_scale < 1)) return -1;
+  return 0;
+}
+
+/* Outer-loop test shared by both tiers (Algorithm 2 "while #extrema >= 2",
+ * the max_imfs cap, the window-length limit).  Returns 0 to continue with
+ * *L set, else the stop reason. */
+static int outer_test(const double* r, long n, int K, const fifo_params* p, int* kext, int* L,
+                      int* flags) {
+  long k = fifo_count_extrema(r, n);
+  kext[K] = (int)k;
+  if (p->L_in) {
+    if (K == p->max_imfs) return FIFO_STOP_MAX_IMFS;
+    *L = p->L_in[K];
+    if (*L <= 0) return FIFO_STOP_FORCED_END;
+    if (2L * (long)(*L) - 1 > n) return FIFO_STOP_MASK;
+    return 0;
+  }
+  if (k < 2) return FIFO_STOP_EXTREMA;
+  *L = fifo_mask_length(n, k, p->nu, p->mask_scale);
+  if (*L < 2) {
+    *L = 2;
+    *flags |= FIFO_FLAG_L_CLAMPED;
+  }
+  if (2L * (long)(*L) - 1 > n) return FIFO_STOP_MASK;
+  if (K == p->max_imfs) return FIFO_STOP_MAX_IMFS;
+  return 0;
+}
+
+static int near_tie(double sd, double delta) { return fabs(sd - delta) <= 1e-6 * delta; }
+
+static void finish(const double* r, long n, int K, int reason, int flags, const fifo_outputs* o) {
+  memcpy(o->imfs + (size_t)K * (size_t)n, r, (size_t)n * sizeof(double));
+  *o->n_imfs = K;
+  *o->status = reason | flags;
+}
+
+static int all_finite(const double* s, long n) {
+  for (long i = 0; i < n; i++)
+    if (!isfinite(s[i])) return 0;
+  return 1;
+}
+
+/* Tier A: Algorithm 2 with a fixed mask length per inner loop (eq.
+ * First_IMF_fixed_length), u_j = u_{j-1} - W u_{j-1} by direct periodic
+ * convolution with the circulant W of eq. W_m (first column = the taps),
+ * stopping rule eq. SD. */
+int fifo_iterative(const double* s, long n, const fifo_params* p, const fifo_outputs* o) {
+  if (check_args(s, n, p, o)) return -1;
+  double* r = malloc((size_t)n * sizeof(double));
+  double* u = malloc((size_t)n * sizeof(double));
+  double* v = malloc((size_t)n * sizeof(double));
+  double* c = malloc((size_t)n * sizeof(double));
+  if (!r || !u || !v || !c) {
+    free(r), free(u), free(v), free(c);
+    return -2;
+  }
+  memcpy(r, s, (size_t)n * sizeof(double));
+  int K = 0, flags = 0, reason = 0;
+  if (!all_finite(s, n)) {
+    finish(r, n, 0, FIFO_STOP_NONFINITE, 0, o);
+    free(r), free(u), free(v), free(c);
+    return 0;
+  }
+  for (;;) {
+    int L = 0;
+    reason = outer_test(r, n, K, p, o->kext, &L, &flags);
+    if (reason) break;
+    fifo_triangle_taps(n, L, c);
+    memcpy(u, r, (size_t)n * sizeof(double));
+    double sd = INFINITY, sd_prev = INFINITY;
+    int j;
+    for (j = 1; j <= p->max_inner; j++) {
+      /* v = W u, (W u)_i = sum_d c[d mod n] u[(i-d) mod n] */
+      for (long i = 0; i < n; i++) {
+        double acc = 0.0;
+        for (long d = -(L - 1); d <= L - 1; d++) {
+          long cd = ((d % n) + n) % n;
+          long ui = (((i - d) % n) + n) % n;
+          acc += c[cd] * u[ui];
+        }
+        v[i] = acc;
+      }
+      double num = 0.0, den = 0.0;
+      for (long i = 0; i < n; i++) {
+        num += v[i] * v[i]; /* ||u_j - u_{j-1}||^2 */
+        den += u[i] * u[i]; /* ||u_{j-1}||^2 */
+      }
+      for (long i = 0; i < n; i++) u[i] -= v[i];
+      sd_prev = sd;
+      if (p->absolute)
+        sd = sqrt(num);
+      else
+        sd = den > 0.0 ? sqrt(num / den) : 0.0;
+      if (o->sd_trace) o->sd_trace[(size_t)K * (size_t)p->max_inner + (size_t)(j - 1)] = sd;
+      if (sd < p->delta) break;
+    }
+    int m = j > p->max_inner ? p->max_inner : j;
+    if (j > p->max_inner) flags |= FIFO_FLAG_MAX_INNER_HIT;
+    if (near_tie(sd, p->delta) || (m > 1 && near_tie(sd_prev, p->delta)))
+      flags |= FIFO_FLAG_NEAR_DELTA_TIE;
+    o->m[K] = m;
+    o->L[K] = L;
+    o->sd_m[K] = sd;
+    o->sd_prev[K] = sd_prev;
+    memcpy(o->imfs + (size_t)K * (size_t)n, u, (size_t)n * sizeof(double));
+    for (long i = 0; i < n; i++) r[i] -= u[i];
+    K++;
+  }
+  finish(r, n, K, reason, flags, o);
+  free(r), free(u), free(v), free(c);
+  return 0;
+}
+
+/* Tier B: the FIF direct method.  IMF = IDFT((1 - w_hat)^m DFT(r))
+ * (eq. One step_algo), m found by evaluating eq. SD for successively larger
+ * m through Parseval: ||u_j - u_{j-1}||^2 = (1/n) sum_k |R_k|^2
+ * (1-w_k)^{2(j-1)} w_k^2 and ||u_{j-1}||^2 = (1/n) sum_k |R_k|^2
+ * (1-w_k)^{2(j-1)} (proof of Theorem 2, Theorem 5). */
+int fifo_direct(const double* s, long n, const fifo_params* p, const fifo_outputs* o) {
+  if (check_args(s, n, p, o)) return -1;
+  double* r = malloc((size_t)n * sizeof(double));
+  double* Rre = malloc((size_t)n * sizeof(double));
+  double* Rim = malloc((size_t)n * sizeof(double));
+  double* w = malloc((size_t)n * sizeof(double));
+  double* E = malloc((size_t)n * sizeof(double));
+  if (!r || !Rre || !Rim || !w || !E) {
+    free(r), free(Rre), free(Rim), free(w), free(E);
+    return -2;
+  }
+  memcpy(r, s, (size_t)n * sizeof(double));
+  int K = 0, flags = 0, reason = 0;
+  if (!all_finite(s, n)) {
+    finish(r, n, 0, FIFO_STOP_NONFINITE, 0, o);
+    free(r), free(Rre), free(Rim), free(w), free(E);
+    return 0;
+  }
+  for (;;) {
+    int L = 0;
+    reason = outer_test(r, n, K, p, o->kext, &L, &flags);
+    if (reason) break;
+    for (long i = 0; i < n; i++) {
+      Rre[i] = r[i];
+      Rim[i] = 0.0;
+    }
+    fifo_fft(Rre, Rim, n, -1);
+    fifo_window_spectrum(n, L, w);
+    for (long k = 0; k < n; k++) E[k] = Rre[k] * Rre[k] + Rim[k] * Rim[k];
+    double sd = INFINITY, sd_prev = INFINITY;
+    int j;
+    for (j = 1; j <= p->max_inner; j++) {
+      double num = 0.0, den = 0.0;
+      for (long k = 0; k < n; k++) {
+        num += E[k] * w[k] * w[k];
+        den += E[k];
+      }
+      sd_prev = sd;
+      if (p->absolute)
+        sd = sqrt(num / (double)n);
+      else
+        sd = den > 0.0 ? sqrt(num / den) : 0.0;
+      if (o->sd_trace) o->sd_trace[(size_t)K * (size_t)p->max_inner + (size_t)(j - 1)] = sd;
+      if (sd < p->delta) break;
+      for (long k = 0; k < n; k++) E[k] *= (1.0 - w[k]) * (1.0 - w[k]);
+    }
+    int m = j > p->max_inner ? p->max_inner : j;
+    if (j > p->max_inner) flags |= FIFO_FLAG_MAX_INNER_HIT;
+    if (near_tie(sd, p->delta) || (m > 1 && near_tie(sd_prev, p->delta)))
+      flags |= FIFO_FLAG_NEAR_DELTA_TIE;
+    for (long k = 0; k < n; k++) {
+      double g = pow(1.0 - w[k], (double)m);
+      Rre[k] *= g;
+      Rim[k] *= g;
+    }
+    fifo_fft(Rre, Rim, n, +1);
+    double* imf = o->imfs + (size_t)K * (size_t)n;
+    for (long i = 0; i < n; i++) imf[i] = Rre[i] / (double)n;
+    for (long i = 0; i < n; i++) r[i] -= imf[i];
+    o->m[K] = m;
+    o->L[K] = L;
+    o->sd_m[K] = sd;
+    o->sd_prev[K] = sd_prev;
+    K++;
+  }
+  finish(r, n, K, reason, flags, o);
+  free(r), free(Rre), free(Rim), free(w), free(E);
+  return 0;
+}

@@ -1,0 +1,319 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+Each test checks the oracle against something other than itself: the DFT
+definition (brute force), closed forms derived from the paper's theorems,
+invariants the paper proves, exact symmetries, and the agreement of the two
+independent tiers (time-domain Algorithm 2 vs. the spectral direct method of
+Sec. 4).
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_1802_01359_gb300 import signals
+
+SMOOTH_SMALL = [n for n in signals.smooth_lengths_between(1, 2048)]
+
+
+def rel(a, b):
+    return np.linalg.norm(np.asarray(a) - np.asarray(b)) / max(np.linalg.norm(np.asarray(b)), 1e-300)
+
+
+# ----------------------------------------------------------------- FFT
+
+@pytest.mark.parametrize("n", list(range(1, 65)) + [96, 243, 256, 729, 1024, 1536, 2048])
+def test_fft_matches_bruteforce_dft(oracle_mod, n):
+    rng = np.random.default_rng(n)
+    x = rng.standard_normal(n) + 1j * rng.standard_normal(n)
+    for sign in (-1, +1):
+        X = oracle_mod.fft(x, sign)
+        D = oracle_mod.dft(x.real, x.imag, sign)
+        assert rel(X, D) < 1e-13
+    # the definition itself, on an impulse and a constant (exact closed forms)
+    e = np.zeros(n); e[min(1, n - 1)] = 1.0
+    k = np.arange(n)
+    assert np.allclose(oracle_mod.dft(e), np.exp(-2j * np.pi * k * min(1, n - 1) / n), atol=1e-13)
+    assert np.allclose(oracle_mod.dft(np.ones(n)), np.where(k == 0, n, 0), atol=1e-12 * n)
+
+
+def test_fft_against_numpy_pocketfft(oracle_mod):
+    for n in SMOOTH_SMALL:
+        x = np.random.default_rng(n + 7).standard_normal(n)
+        assert rel(oracle_mod.fft(x), np.fft.fft(x)) < 1e-13
+
+
+# --------------------------------------------------------- window spectrum
+
+@pytest.mark.parametrize("n,L", [(64, 8), (64, 5), (65, 7), (243, 40), (256, 2), (1000, 333),
+                                 (2048, 409), (729, 364), (4096, 409)])
+def test_window_spectrum_is_dft_of_taps(oracle_mod, n, L):
+    """eq. Lambdas: the circulant's eigenvalues are the DFT of its first row; the
+    closed form must equal the brute-force DFT of the sampled, normalised taps."""
+    c = oracle_mod.taps(n, L)
+    assert abs(c.sum() - 1.0) < 1e-15 and (c >= 0).all()            # row stochastic (eq. W_m)
+    assert np.allclose(c[1:], c[1:][::-1], atol=0)                  # symmetric: c_{n-j} = c_j
+    lam = oracle_mod.dft(c)
+    assert np.abs(lam.imag).max() < 1e-13                           # real spectrum (Theorem 4)
+    w = oracle_mod.window_spectrum(n, L)
+    assert np.abs(w - lam.real).max() < 1e-13
+
+
+@pytest.mark.parametrize("n,L", [(64, 8), (243, 40), (4096, 409), (16384, 7), (16384, 8191)])
+def test_window_spectrum_range(oracle_mod, n, L):
+    """Theorem 4 / Corollary 2: lambda_0 = 1, every other eigenvalue in [0, 1)."""
+    w = oracle_mod.window_spectrum(n, L)
+    assert w[0] == 1.0
+    assert w[1:].min() >= 0.0 and w[1:].max() < 1.0
+    # zeros exactly where k*L is a multiple of n (sin(pi k L / n) = 0)
+    k = np.arange(1, n)
+    assert np.array_equal(w[1:] == 0.0, (k * L) % n == 0)
+
+
+# ------------------------------------------------------------ mask length
+
+def test_mask_length_rule(oracle_mod):
+    # eq. Unif_Mask_length with leading factor 1 and 2
+    assert oracle_mod.mask_length(4096, 16) == 409          # floor(409.6)
+    assert oracle_mod.mask_length(4096, 16, mask_scale=2) == 818
+    assert oracle_mod.mask_length(1000, 16) == 100          # exact integer quotient
+    assert oracle_mod.mask_length(4096, 606) == 10
+    assert oracle_mod.mask_length(10, 9) == 1               # clamped later to 2
+
+
+def test_extrema_and_zero_crossings_small(oracle_mod):
+    assert oracle_mod.count_extrema([0, 1, 0, 1]) == 4       # periodic alternation
+    assert oracle_mod.count_extrema([0, 1, 2, 3]) == 2       # ramp: max at 3, min at 0 (wrap)
+    assert oracle_mod.count_extrema([1, 1, 1, 1]) == 0
+    assert oracle_mod.count_extrema([0, 1, 1, 0]) == 0       # flat tops count no strict extremum
+    assert oracle_mod.count_extrema([0, 2, 1, 2]) == 4
+    n = 4096
+    j = np.arange(n)
+    assert oracle_mod.count_extrema(np.cos(2 * np.pi * 8 * j / n + 0.3)) == 16
+    assert oracle_mod.count_zero_crossings(np.cos(2 * np.pi * 8 * j / n + 0.3)) == 16
+    assert oracle_mod.count_zero_crossings([1, -1, 1, -1]) == 4
+
+
+# -------------------------------------------------------- Theorem 2 / 5
+
+def test_pure_tone_scaled_by_multiplier(oracle_mod):
+    """A tone at bin k0 is an eigenvector of W: Algorithm 2 returns it scaled by
+    (1 - lambda_k0)^m (eq. IMF_IF_stop, eq. IMF1_direct), and SD_j = lambda_k0
+    for every j (eq. SD with Parseval), so m is 1 or max_inner."""
+    n, k0, phi = 4096, 8, 0.3
+    j = np.arange(n)
+    s = np.cos(2 * np.pi * k0 * j / n + phi)
+    a = oracle_mod.iterative(s, max_imfs=1, trace=True)
+    # 16 extrema, L = floor(1.6*4096/16) = 409
+    assert a["kext"][0] == 16 and a["L"][0] == 409
+    lam = oracle_mod.dft(oracle_mod.taps(n, 409)).real[k0]      # eigenvalue by the definition
+    assert abs(lam - 0.05541415768287662) < 1e-14
+    assert lam > 1e-3 and a["m"][0] == 200                         # SD never drops below delta
+    assert a["status"] & oracle_mod.FLAG_MAX_INNER_HIT
+    assert np.allclose(a["sd_trace"][0], lam, rtol=1e-11, atol=0)
+    scale = (1 - lam) ** 200
+    assert abs(scale - 1.1176000063634996e-05) < 1e-15
+    # 200 steps of round-off stay at ~1e-15 of ||s|| (the IMF itself is 1e-5 ||s||)
+    assert np.linalg.norm(a["imfs"][0] - scale * s) < 1e-13 * np.linalg.norm(s)
+    b = oracle_mod.direct(s, max_imfs=1)
+    assert b["m"][0] == 200
+    assert np.linalg.norm(b["imfs"][0] - scale * s) < 1e-13 * np.linalg.norm(s)
+    # a tone at a zero of the window spectrum passes unchanged after one step
+    s2 = np.cos(2 * np.pi * 16 * j / 256)
+    a2 = oracle_mod.iterative(s2, force_L=[16], max_imfs=1)          # 16*16 = 256: lambda_16 = 0
+    assert a2["m"][0] == 1 and rel(a2["imfs"][0], s2) < 1e-13
+
+
+def _two_tone_sd(lam4, j):
+    a = (1 - lam4) ** 2
+    return math.sqrt(lam4 ** 2 * a ** (j - 1) / (a ** (j - 1) + 1))
+
+
+def test_interior_m_closed_form(oracle_mod):
+    """Two equal tones, one on a zero of the window spectrum (bin 8, L = 8, n = 64)
+    and one at lambda_4: SD_j^2 = lambda_4^2 a^{j-1} / (a^{j-1} + 1), a =
+    (1-lambda_4)^2, first below delta = 1e-3 at j = 13 (interior m)."""
+    n = 64
+    j = np.arange(n)
+    s = np.cos(2 * np.pi * 8 * j / n) + np.cos(2 * np.pi * 4 * j / n)
+    lam = oracle_mod.dft(oracle_mod.taps(n, 8)).real
+    assert abs(lam[8]) < 1e-15
+    lam4 = lam[4]
+    assert abs(lam4 - 1 / (64 * math.sin(math.pi / 16) ** 2)) < 1e-14
+    sd = [_two_tone_sd(lam4, jj) for jj in range(1, 40)]
+    m_expected = next(jj for jj in range(1, 40) if sd[jj - 1] < 1e-3)
+    assert m_expected == 13
+    for tier in (oracle_mod.iterative, oracle_mod.direct):
+        r = tier(s, force_L=[8], max_imfs=1, delta=1e-3, trace=True)
+        assert r["m"][0] == 13
+        assert np.allclose(r["sd_trace"][0][:13], sd[:13], rtol=1e-10, atol=0)
+        g = (1 - lam) ** 13
+        expected = np.real(np.fft.ifft(g * np.fft.fft(s)))           # eq. One step_algo
+        assert rel(r["imfs"][0], expected) < 1e-12
+
+
+def test_absolute_criterion_bound(oracle_mod):
+    """Theorem 5: under the absolute rule (eq. Discrete_Abs_StopCond) the
+    iteration stops no later than the a-priori N0 of eq. N0_discrete.  With m
+    counting applications of (I-W), the rule is met for m - 1 >= N0."""
+    for seed, n in [(1, 256), (2, 384), (3, 512)]:
+        s = signals.component_signal(99, seed, n).astype(np.float64)
+        s /= np.linalg.norm(s)                                        # Sec. 3: WLOG ||s||_2 = 1
+        delta = 1e-3
+        r = oracle_mod.iterative(s, max_imfs=1, delta=delta, absolute=True, max_inner=100000)
+        L = int(r["L"][0])
+        lam = oracle_mod.window_spectrum(n, L)
+        kz = int((lam[1:] == 0).sum())
+        st = np.abs(oracle_mod.fft(s)) / math.sqrt(n)                # unitary DFT (U^T s)
+        bound = delta / (st.max() * math.sqrt(n - 1 - kz))
+        # smallest N0 with N0^N0 / (N0+1)^(N0+1) < bound, in logs
+        N0 = next(N for N in range(1, 10 ** 8)
+                  if N * math.log(N) - (N + 1) * math.log(N + 1) < math.log(bound))
+        m_abs = int(r["m"][0])
+        assert m_abs - 1 <= N0, (m_abs, N0)
+        d = oracle_mod.direct(s, max_imfs=1, delta=delta, absolute=True, max_inner=100000)
+        assert d["m"][0] == m_abs
+
+
+# ----------------------------------------------- direct = iterative (Thm 5)
+
+CASES = [(0, 128, 1e-3), (1, 256, 1e-2), (2, 384, 1e-3), (3, 729, 1e-2), (4, 1024, 1e-2),
+         (5, 243, 5e-2), (6, 512, 3e-2)]
+
+
+@pytest.mark.parametrize("seed,n,delta", CASES)
+def test_direct_equals_iterative(oracle_mod, seed, n, delta):
+    s = signals.component_signal(98, seed, n).astype(np.float64)
+    kw = dict(max_imfs=5, max_inner=80, delta=delta, trace=True)
+    a = oracle_mod.iterative(s, **kw)
+    b = oracle_mod.direct(s, **kw)
+    assert a["n_imfs"] == b["n_imfs"] and a["status"] == b["status"]
+    assert np.array_equal(a["m"], b["m"]) and np.array_equal(a["L"], b["L"])
+    assert np.array_equal(a["kext"], b["kext"])
+    for i in range(a["n_imfs"]):
+        assert rel(a["imfs"][i], b["imfs"][i]) < 1e-11
+        mm = a["m"][i]
+        # Parseval: the time-domain SD sequence equals the spectral one
+        assert np.allclose(a["sd_trace"][i][:mm], b["sd_trace"][i][:mm], rtol=1e-10, atol=0)
+    assert rel(a["remainder"], b["remainder"]) < 1e-11
+
+
+def test_interior_m_occurs_in_random_cases(oracle_mod):
+    """At least some of the parametrised cases above exercise 1 < m < max_inner."""
+    ms = []
+    for seed, n, delta in CASES:
+        s = signals.component_signal(98, seed, n).astype(np.float64)
+        ms += list(oracle_mod.direct(s, max_imfs=5, max_inner=80, delta=delta)["m"])
+    assert any(1 < m < 80 for m in ms)
+
+
+# ------------------------------------------------------------ invariants
+
+@pytest.mark.parametrize("tier", ["iterative", "direct"])
+def test_reconstruction_and_zero_mean(oracle_mod, tier):
+    """Algorithm 1/2 telescopes: s = sum of IMFs + remainder.  Every IMF has zero
+    mean (lambda_0 = 1 removes the DC bin)."""
+    s = signals.single_4096().astype(np.float64)[:1024]
+    r = getattr(oracle_mod, tier)(s, max_imfs=6)
+    assert r["n_imfs"] == 6
+    assert np.abs(r["imfs"].sum(0) + r["remainder"] - s).max() < 1e-13
+    assert np.abs(r["imfs"].mean(axis=1)).max() < 1e-14
+
+
+def test_sd_monotone_nonincreasing(oracle_mod):
+    """SD_j^2 is the mean of lambda^2 under weights |r_k|^2 (1-lambda_k)^{2(j-1)};
+    raising j reweights towards small lambda, so SD_j never increases."""
+    for seed in range(6):
+        s = signals.component_signal(97, seed, 512).astype(np.float64)
+        r = oracle_mod.direct(s, max_imfs=3, max_inner=200, delta=1e-9, trace=True)
+        for i in range(r["n_imfs"]):
+            t = r["sd_trace"][i]
+            assert (np.diff(t) <= 1e-15 * t[:-1]).all()
+
+
+def test_linearity_with_fixed_schedule(oracle_mod):
+    """With L and m fixed, each IMF is a fixed linear map of s (eq. MatrixForm),
+    so the decomposition superposes (the nonlinearity of Sec. 2 comes only from
+    choosing L from the data)."""
+    n = 512
+    x = signals.component_signal(96, 0, n).astype(np.float64)
+    y = signals.component_signal(96, 1, n).astype(np.float64)
+    kw = dict(force_L=[4, 12, 40], max_imfs=3, max_inner=30, delta=1e-300)
+    for tier in (oracle_mod.iterative, oracle_mod.direct):
+        rx, ry = tier(x, **kw), tier(y, **kw)
+        rz = tier(2.5 * x - 0.75 * y, **kw)
+        assert (rz["m"] == 30).all() and rz["n_imfs"] == 3
+        assert rel(rz["imfs"], 2.5 * rx["imfs"] - 0.75 * ry["imfs"]) < 1e-12
+        assert rel(rz["remainder"], 2.5 * rx["remainder"] - 0.75 * ry["remainder"]) < 1e-12
+
+
+def test_exact_symmetries(oracle_mod):
+    """Negation and power-of-two scaling are exact in binary64: identical integers and
+    exactly transformed outputs.  A circular shift leaves the integers unchanged and
+    shifts every IMF."""
+    s = signals.component_signal(95, 3, 768).astype(np.float64)
+    kw = dict(max_imfs=4, max_inner=60, delta=1e-2)
+    b = oracle_mod.direct(s, **kw)
+    for f in (-1.0, 4.0, 0.125):
+        t = oracle_mod.direct(f * s, **kw)
+        assert np.array_equal(t["m"], b["m"]) and np.array_equal(t["L"], b["L"])
+        assert np.array_equal(t["imfs"], f * b["imfs"])
+    a = oracle_mod.iterative(s, **kw)
+    for f in (-1.0, 4.0):
+        t = oracle_mod.iterative(f * s, **kw)
+        assert np.array_equal(t["m"], a["m"]) and np.array_equal(t["imfs"], f * a["imfs"])
+    sh = oracle_mod.direct(np.roll(s, 37), **kw)
+    assert np.array_equal(sh["m"], b["m"]) and np.array_equal(sh["L"], b["L"])
+    assert rel(sh["imfs"], np.roll(b["imfs"], 37, axis=1)) < 1e-12
+
+
+def test_trivial_and_degenerate_inputs(oracle_mod):
+    for tier in (oracle_mod.iterative, oracle_mod.direct):
+        z = tier(np.zeros(64))
+        assert z["n_imfs"] == 0 and z["stop"] == oracle_mod.STOP_EXTREMA
+        assert (z["remainder"] == 0).all()
+        c = tier(np.full(100, 3.25))
+        assert c["n_imfs"] == 0 and (c["remainder"] == 3.25).all()
+        one = tier(np.array([1.0]))
+        assert one["n_imfs"] == 0
+        # a single period of a cosine has k = 2: L = floor(1.6 n/2) makes 2L-1 > n
+        n = 128
+        cos1 = np.cos(2 * np.pi * np.arange(n) / n)
+        t = tier(cos1)
+        assert t["n_imfs"] == 0 and t["stop"] == oracle_mod.STOP_MASK
+        nan = np.ones(16); nan[3] = np.nan
+        t = tier(nan)
+        assert t["stop"] == oracle_mod.STOP_NONFINITE and t["n_imfs"] == 0
+        # max_imfs = 0: no IMF, the signal is the remainder
+        t = tier(signals.component_signal(94, 0, 256).astype(np.float64), max_imfs=0)
+        assert t["n_imfs"] == 0 and t["stop"] == oracle_mod.STOP_MAX_IMFS
+        # a tiny L is clamped to 2 and flagged (alternating signal: k = n)
+        alt = np.tile([1.0, -1.0], 32)
+        t = tier(alt, max_imfs=1)
+        assert t["L"][0] == 2 and t["status"] & oracle_mod.FLAG_L_CLAMPED
+
+
+def test_config_single_4096_saturates_max_inner(oracle_mod):
+    """The three-component n=4096 signal at delta=1e-3: SD_200 stays above delta for
+    every IMF (m = max_inner), the outer loop stops on max_imfs = 10."""
+    s = signals.single_4096().astype(np.float64)
+    b = oracle_mod.direct(s)
+    assert b["n_imfs"] == 10 and b["stop"] == oracle_mod.STOP_MAX_IMFS
+    assert (b["m"] == 200).all()
+    assert b["status"] & oracle_mod.FLAG_MAX_INNER_HIT
+    assert set(b["L"].tolist()) <= {10, 11}
+
+
+def test_golden_single_4096_regression(oracle_mod):
+    """Regression fixture written by tests/golden/make_golden.py (oracle only): both tiers
+    still produce the stored integers on the n=4096 three-component signal."""
+    import json
+    import os
+    with open(os.path.join(os.path.dirname(__file__), "golden", "single_4096_oracle.json")) as f:
+        g = json.load(f)
+    s = signals.single_4096().astype(np.float64)
+    b = oracle_mod.direct(s)
+    assert b["m"].tolist() == g["direct"]["m"] and b["L"].tolist() == g["direct"]["L"]
+    assert b["kext"].tolist() == g["direct"]["kext"] and b["status"] == g["direct"]["status"]
+    assert g["iterative"]["m"] == g["direct"]["m"] and g["iterative"]["L"] == g["direct"]["L"]
+    assert np.allclose([np.linalg.norm(x) for x in b["imfs"]], g["direct"]["imf_l2"], rtol=1e-12)
