@@ -297,34 +297,42 @@ int fifo_iterative(const double* s, long n, const fifo_params* p, const fifo_out
  * (eq. One step_algo), m found by evaluating eq. SD for successively larger
  * m through Parseval: ||u_j - u_{j-1}||^2 = (1/n) sum_k |R_k|^2
  * (1-w_k)^{2(j-1)} w_k^2 and ||u_{j-1}||^2 = (1/n) sum_k |R_k|^2
- * (1-w_k)^{2(j-1)} (proof of Theorem 2, Theorem 5). */
+ * (1-w_k)^{2(j-1)} (proof of Theorem 2, Theorem 5).
+ * The remainder r - IMF (Algorithm 2) is kept in the spectral domain as
+ * well: R <- (1 - (1-w)^m) R, the DFT of r - IMF by linearity, with
+ * 1 - (1-w)^m = -expm1(m log1p(-w)).  Where w_k = 0 exactly this empties bin
+ * k exactly, as exact arithmetic does; a time-domain subtraction would leave
+ * round-off there, and at large j that round-off (weight 1, w = 0) would
+ * decide SD_j. */
 int fifo_direct(const double* s, long n, const fifo_params* p, const fifo_outputs* o) {
   if (check_args(s, n, p, o)) return -1;
   double* r = malloc((size_t)n * sizeof(double));
   double* Rre = malloc((size_t)n * sizeof(double));
   double* Rim = malloc((size_t)n * sizeof(double));
+  double* Ire = malloc((size_t)n * sizeof(double));
+  double* Iim = malloc((size_t)n * sizeof(double));
   double* w = malloc((size_t)n * sizeof(double));
   double* E = malloc((size_t)n * sizeof(double));
-  if (!r || !Rre || !Rim || !w || !E) {
-    free(r), free(Rre), free(Rim), free(w), free(E);
+  if (!r || !Rre || !Rim || !Ire || !Iim || !w || !E) {
+    free(r), free(Rre), free(Rim), free(Ire), free(Iim), free(w), free(E);
     return -2;
   }
   memcpy(r, s, (size_t)n * sizeof(double));
   int K = 0, flags = 0, reason = 0;
   if (!all_finite(s, n)) {
     finish(r, n, 0, FIFO_STOP_NONFINITE, 0, o);
-    free(r), free(Rre), free(Rim), free(w), free(E);
+    free(r), free(Rre), free(Rim), free(Ire), free(Iim), free(w), free(E);
     return 0;
   }
+  for (long i = 0; i < n; i++) {
+    Rre[i] = s[i];
+    Rim[i] = 0.0;
+  }
+  fifo_fft(Rre, Rim, n, -1);
   for (;;) {
     int L = 0;
     reason = outer_test(r, n, K, p, o->kext, &L, &flags);
     if (reason) break;
-    for (long i = 0; i < n; i++) {
-      Rre[i] = r[i];
-      Rim[i] = 0.0;
-    }
-    fifo_fft(Rre, Rim, n, -1);
     fifo_window_spectrum(n, L, w);
     for (long k = 0; k < n; k++) E[k] = Rre[k] * Rre[k] + Rim[k] * Rim[k];
     double sd = INFINITY, sd_prev = INFINITY;
@@ -350,12 +358,15 @@ int fifo_direct(const double* s, long n, const fifo_params* p, const fifo_output
       flags |= FIFO_FLAG_NEAR_DELTA_TIE;
     for (long k = 0; k < n; k++) {
       double g = pow(1.0 - w[k], (double)m);
-      Rre[k] *= g;
-      Rim[k] *= g;
+      double keep = -expm1((double)m * log1p(-w[k]));
+      Ire[k] = g * Rre[k];
+      Iim[k] = g * Rim[k];
+      Rre[k] *= keep;
+      Rim[k] *= keep;
     }
-    fifo_fft(Rre, Rim, n, +1);
+    fifo_fft(Ire, Iim, n, +1);
     double* imf = o->imfs + (size_t)K * (size_t)n;
-    for (long i = 0; i < n; i++) imf[i] = Rre[i] / (double)n;
+    for (long i = 0; i < n; i++) imf[i] = Ire[i] / (double)n;
     for (long i = 0; i < n; i++) r[i] -= imf[i];
     o->m[K] = m;
     o->L[K] = L;
@@ -364,6 +375,6 @@ int fifo_direct(const double* s, long n, const fifo_params* p, const fifo_output
     K++;
   }
   finish(r, n, K, reason, flags, o);
-  free(r), free(Rre), free(Rim), free(w), free(E);
+  free(r), free(Rre), free(Rim), free(Ire), free(Iim), free(w), free(E);
   return 0;
 }

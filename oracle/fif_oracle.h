@@ -17,8 +17,14 @@
  *           (eq. One step_algo): DFT, multiply the spectrum by (1-w_hat)^m,
  *           inverse DFT, with m chosen by evaluating eq. SD for
  *           successively larger m through Parseval (Theorem 2 proof,
- *           Theorem 5).
- * Both run entirely in double precision.
+ *           Theorem 5); the remainder spectrum is updated by the factor
+ *           1 - (1-w_hat)^m.
+ * Both run entirely in double precision.  They agree (Theorem 5) except
+ * where a window eigenvalue is exactly 0 and the same L is used again: exact
+ * arithmetic leaves that bin of the remainder empty, tier B keeps it empty,
+ * tier A carries binary64 round-off in it, and at large j that round-off can
+ * decide m.  Tier B is the reference for such cases (it is pinned against
+ * Algorithm 2 run in 60-digit arithmetic).
  */
 #ifndef FIF_ORACLE_H
 #define FIF_ORACLE_H

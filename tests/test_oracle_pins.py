@@ -317,3 +317,85 @@ def test_golden_single_4096_regression(oracle_mod):
     assert b["kext"].tolist() == g["direct"]["kext"] and b["status"] == g["direct"]["status"]
     assert g["iterative"]["m"] == g["direct"]["m"] and g["iterative"]["L"] == g["direct"]["L"]
     assert np.allclose([np.linalg.norm(x) for x in b["imfs"]], g["direct"]["imf_l2"], rtol=1e-12)
+
+
+def _algorithm2_high_precision(s, *, max_imfs, max_inner, delta, nu=1.6, dps=60):
+    """Algorithm 2 (time-domain iteration, eq. s_m+1 and eq. SD) in 60-digit arithmetic,
+    written independently of the C oracle, for tiny n."""
+    import mpmath as mp
+    mp.mp.dps = dps
+    n = len(s)
+    r = [mp.mpf(float(x)) for x in s]
+    out = {"m": [], "L": [], "kext": []}
+
+    def extrema(v):
+        c = 0
+        for i in range(n):
+            a, b = v[i] - v[i - 1], v[(i + 1) % n] - v[i]
+            c += (a > 0 and b < 0) or (a < 0 and b > 0)
+        return c
+
+    K = 0
+    while True:
+        k = extrema(r)
+        out["kext"].append(k)
+        if k < 2:
+            out["stop"] = 1
+            break
+        L = int(math.floor((nu * n) / k))
+        L = max(L, 2)
+        if 2 * L - 1 > n:
+            out["stop"] = 2
+            break
+        if K == max_imfs:
+            out["stop"] = 3
+            break
+        taps = {d: mp.mpf(L - abs(d)) / (L * L) for d in range(-(L - 1), L)}
+        tot = sum(taps.values())
+        taps = {d: c / tot for d, c in taps.items()}
+        u = r[:]
+        for j in range(1, max_inner + 1):
+            v = [sum(c * u[(i - d) % n] for d, c in taps.items()) for i in range(n)]
+            num = sum(x * x for x in v)
+            den = sum(x * x for x in u)
+            u = [a - b for a, b in zip(u, v)]
+            if mp.sqrt(num / den) < delta:
+                break
+        out["m"].append(j)
+        out["L"].append(L)
+        r = [a - b for a, b in zip(r, u)]
+        K += 1
+    return out
+
+
+@pytest.mark.parametrize("seed,n,delta", [(1, 6, 2e-2), (0, 8, 1e-3), (2, 12, 2e-2), (3, 16, 1e-2),
+                                          (4, 16, 1e-3), (5, 12, 1e-3)])
+def test_direct_matches_high_precision_algorithm2(oracle_mod, seed, n, delta):
+    """Tier B against Algorithm 2 carried out in 60-digit arithmetic: same extrema counts,
+    L, m and number of IMFs.  The (seed 1, n 6) case uses L = 2 twice: the window
+    eigenvalue at n/2 is exactly 0, exact arithmetic empties that bin of the
+    remainder, and m of the second IMF is max_inner; a binary64 time-domain iteration
+    keeps round-off there that ends the second inner loop early."""
+    s = signals.component_signal(50, seed, n).astype(np.float64)
+    hp = _algorithm2_high_precision(s, max_imfs=4, max_inner=200, delta=delta)
+    b = oracle_mod.direct(s, max_imfs=4, max_inner=200, delta=delta)
+    assert b["m"].tolist() == hp["m"]
+    assert b["L"].tolist() == hp["L"]
+    assert b["kext"].tolist() == hp["kext"]
+    assert b["stop"] == hp["stop"]
+
+
+def test_exactly_zero_window_bins_stay_empty(oracle_mod):
+    """Where w_hat_k = 0 the multiplier (1 - w_hat_k)^m is 1: the IMF takes the whole bin
+    and the remainder spectrum is exactly 0 there (tier B)."""
+    n = 64
+    s = signals.component_signal(49, 0, n).astype(np.float64)
+    b = oracle_mod.direct(s, force_L=[8], max_imfs=1, max_inner=20, delta=1e-300)
+    w = oracle_mod.window_spectrum(n, 8)
+    zero = np.nonzero(w == 0.0)[0]
+    assert zero.size > 0
+    R = np.fft.fft(b["remainder"])
+    assert np.abs(R[zero]).max() < 1e-13 * np.abs(R).max()
+    I = np.fft.fft(b["imfs"][0])
+    S = np.fft.fft(s)
+    assert np.allclose(I[zero], S[zero], rtol=1e-12, atol=1e-12 * np.abs(S).max())
