@@ -1,0 +1,183 @@
+/*
+ * fif.h -- C ABI of the GB300 (sm_103a) FFT-based Iterative Filtering library
+ * (libfif.so).
+ *
+ * The method is the "FIF" direct form of Iterative Filtering from Cicone &
+ * Zhou, "Numerical Analysis for Iterative Filtering with New Efficient
+ * Implementations Based on FFT":
+ *
+ *   - outer loop (Algorithm 2, Sec. 3): while the remainder r has at least two
+ *     extrema, pick the window half-support L from the extrema count k
+ *     (eq. Unif_Mask_length, L = mask_scale * floor(nu*n/k)), extract one IMF,
+ *     subtract it; the final remainder is appended (Algorithm 1/2);
+ *   - inner loop, replaced by one spectral multiplier (Theorem 5,
+ *     eq. IMF1_direct, eq. One step_algo of Sec. 4):
+ *         IMF_hat_k = (1 - w_hat_k)^m * r_hat_k,
+ *     with w_hat the eigenvalues of the circulant window matrix (eq. Lambdas)
+ *     and m the number of inner iterations picked by the relative stopping
+ *     rule eq. SD, ||u_m - u_{m-1}|| / ||u_{m-1}|| < delta, evaluated in the
+ *     frequency domain through Parseval (proof of Theorem 2), capped by
+ *     max_inner (Sec. 3, after eq. SD).
+ *
+ * Signals are real, periodic (Sec. 4 requires a periodic extension), sampled
+ * on x_j = j/n.  The window is the triangle of eq. triangular, sampled at
+ * integer offsets (taps (L-|d|)/L^2, |d| < L): the autocorrelation of a
+ * length-L box, so 0 <= w_hat <= 1 (Corollary 2).
+ *
+ * Conventions for every entry point:
+ *   - All work is asynchronous on the plan's CUDA stream unless stated.
+ *   - Data pointers are DEVICE pointers unless the name or comment says host.
+ *     The library never allocates or frees caller memory; the plan owns its
+ *     own device tables and scratch and frees them in fif_plan_destroy.
+ *   - The return value reports argument and launch errors only.  Per-signal
+ *     outcomes are written to sig_status (stop reason | flags, see below).
+ *   - Integer outputs are int32; sample data is float32, row-major.
+ *   - A plan is not thread-safe: calls on one plan must not overlap.
+ */
+#ifndef FIF_H
+#define FIF_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct fif_plan_s* fif_plan_t;
+
+typedef enum {
+  FIF_OK = 0,
+  FIF_EINVAL = 1,        /* invalid argument (NULL pointer, bad size, bad descriptor) */
+  FIF_ENOMEM = 2,        /* the plan could not allocate its device tables or scratch */
+  FIF_ECUDA = 3,         /* a CUDA runtime call or kernel launch failed */
+  FIF_ETIMEOUT = 4,      /* a bounded device wait gave up */
+  FIF_EUNSUPPORTED = 5   /* valid request the library does not implement (e.g. n not 2^a 3^b) */
+} fif_status;
+
+typedef enum {
+  FIF_WIN_TRIANGLE = 0   /* eq. triangular, sampled; w_hat = [sin(pi k L/n) / (L sin(pi k/n))]^2 */
+} fif_window;
+
+typedef enum {
+  FIF_PREC_FP32 = 0      /* FP32 FFTs and multiplier; m chosen with an FP32 screen + FP64 tie-break */
+} fif_precision;
+
+/* ---- per-signal status word (sig_status): low byte = stop reason ---- */
+#define FIF_STOP_EXTREMA    1   /* remainder has < 2 extrema (Algorithm 1/2 outer test) */
+#define FIF_STOP_MASK       2   /* 2L-1 > n: the window would wrap the period (Sec. 3.1, l <= (n-1)/2) */
+#define FIF_STOP_MAX_IMFS   3   /* max_imfs IMFs extracted */
+#define FIF_STOP_FORCED_END 4   /* FIF_FORCE_L schedule ended (mask_len[K] <= 0) */
+#define FIF_STOP_NONFINITE  5   /* NaN or Inf in the input: no IMF, the input is copied as remainder */
+/* flags, OR-ed into sig_status (any IMF) and into fif_imf_diag.flags (that IMF) */
+#define FIF_FLAG_NEAR_DELTA_TIE  (1 << 8)  /* |SD_m - delta| or |SD_{m-1} - delta| <= 1e-6 delta */
+#define FIF_FLAG_EXTREMA_TIE     (1 << 9)  /* the extrema count could change under a perturbation of
+                                              r of 2^-18 max|s| (see fif_imf_diag) */
+#define FIF_FLAG_MAX_INNER_HIT   (1 << 10) /* SD_j >= delta for every j <= max_inner; m = max_inner */
+#define FIF_FLAG_FP64_TIEBREAK   (1 << 11) /* an m decision fell inside the FP32 screen's error band
+                                              and was re-evaluated in FP64 */
+#define FIF_FLAG_L_CLAMPED       (1 << 12) /* the mask rule gave L < 2; L = 2 used */
+
+/* ---- plan flags ---- */
+#define FIF_FORCE_L 1  /* mask_len[] is an INPUT: L for IMF K is mask_len[K]; a value <= 0 ends the
+                          decomposition (FIF_STOP_FORCED_END).  The extrema test is skipped.  For
+                          tests of linearity and worked examples. */
+
+typedef struct {
+  fif_window window;        /* FIF_WIN_TRIANGLE */
+  double nu;                /* eq. Unif_Mask_length tuning parameter (1.6) */
+  int32_t mask_scale;       /* leading factor of the mask rule: 1 (half-support L = floor(nu n/k))
+                               or 2 (the paper's l = 2 floor(nu N/k)) */
+  double delta;             /* stopping threshold of eq. SD, > 0 */
+  int32_t max_inner;        /* cap on m (number of inner iterations), 1 .. 1<<20 */
+  int32_t max_imfs;         /* cap on the number of IMFs (remainder not counted), 0 .. 64 */
+  fif_precision precision;  /* FIF_PREC_FP32 */
+  int64_t max_n;            /* largest signal length this plan accepts */
+  int32_t flags;            /* 0 or FIF_FORCE_L */
+} fif_plan_desc;
+
+/* Optional per-IMF diagnostics, one record per outer step: record K < n_imfs
+ * describes IMF K; record n_imfs describes the final remainder. */
+typedef struct {
+  int32_t k_extrema;       /* extrema count of the remainder at the outer test before IMF K
+                              (for record n_imfs: of the final remainder) */
+  int32_t zero_crossings;  /* zero crossings of that remainder (IMF definition, Sec. 1) */
+  int32_t flags;           /* FIF_FLAG_* raised while extracting IMF K */
+  float inf_norm;          /* ||IMF_K||_inf (significance, Sec. 2.3); record n_imfs: ||r||_inf */
+} fif_imf_diag;
+
+/* Create a plan.  desc is copied.  cuda_stream is a cudaStream_t (NULL = the
+ * legacy default stream).  Allocates the plan's device scratch for signals up
+ * to desc->max_n.  Window tables for a length n are built on the first call
+ * that sees n (fif_plan_prepare builds them ahead of time); building them
+ * allocates, so that first call must not be inside a stream capture.
+ * Errors: FIF_EINVAL (NULL out/desc, out-of-range field), FIF_ENOMEM,
+ * FIF_ECUDA. */
+fif_status fif_plan_create(fif_plan_t* out, const fif_plan_desc* desc, void* cuda_stream);
+
+/* Free the plan and everything it owns.  Synchronizes the plan's stream.
+ * NULL is accepted. */
+fif_status fif_plan_destroy(fif_plan_t plan);
+
+/* Change the stream later calls run on. */
+fif_status fif_plan_set_stream(fif_plan_t plan, void* cuda_stream);
+
+/* Build (if not yet built) the tables for every length in lengths[0..count)
+ * (HOST array).  Blocking.  Errors: FIF_EINVAL, FIF_EUNSUPPORTED (length not
+ * of the form 2^a 3^b, or above max_n), FIF_ENOMEM, FIF_ECUDA. */
+fif_status fif_plan_prepare(fif_plan_t plan, const int64_t* lengths, int64_t count);
+
+/* Decompose ONE signal of length n (2^a 3^b, 4 <= n <= max_n) with the plain
+ * staged path: one kernel launch per step of the method per outer iteration
+ * (R2C; m selection; multiplier and spectral remainder update; C2R with the
+ * remainder update and the extrema count), the remainder spectrum and work
+ * arrays staged through the plan's device scratch.
+ *   signal    [n]                      input samples
+ *   imfs      [(max_imfs+1) * n]       row K = IMF K, row n_imfs = final remainder;
+ *                                      rows after n_imfs are not written
+ *   m         [max_imfs]               inner iteration count per IMF
+ *   mask_len  [max_imfs]               L per IMF (input under FIF_FORCE_L)
+ *   n_imfs    [1]                      number of IMFs
+ *   sig_status[1]                      stop reason | flags
+ *   diag      [max_imfs+1] or NULL     optional fif_imf_diag records
+ * Errors: FIF_EINVAL, FIF_EUNSUPPORTED, FIF_ENOMEM, FIF_ECUDA. */
+fif_status fif_decompose(fif_plan_t plan, const float* signal, int64_t n, float* imfs, int32_t* m,
+                         int32_t* mask_len, int32_t* n_imfs, int32_t* sig_status, fif_imf_diag* diag);
+
+/* Decompose a batch of independent signals in one fused launch per length
+ * class: each CTA keeps a whole signal's spectrum, work array and remainder
+ * in shared memory and runs every outer iteration on chip.
+ *   signals     packed samples; signal i is signals[offsets[i] .. offsets[i+1])
+ *   offsets     HOST int64[batch+1], offsets[0] = 0, non-decreasing
+ *   imfs        packed outputs; signal i's (max_imfs+1) x n_i block starts at out_offsets[i]
+ *   out_offsets HOST int64[batch]
+ *   m, mask_len [batch * max_imfs]   (row i = signal i)
+ *   n_imfs, sig_status [batch]
+ *   diag        [batch * (max_imfs+1)] or NULL
+ * Lengths must be 2^a 3^b with 4 <= n_i <= min(max_n, fif_fused_max_n()).
+ * Errors: FIF_EINVAL, FIF_EUNSUPPORTED, FIF_ENOMEM, FIF_ECUDA. */
+fif_status fif_decompose_batch(fif_plan_t plan, const float* signals, const int64_t* offsets,
+                               int64_t batch, float* imfs, const int64_t* out_offsets, int32_t* m,
+                               int32_t* mask_len, int32_t* n_imfs, int32_t* sig_status,
+                               fif_imf_diag* diag);
+
+/* Same as fif_decompose_batch, but every data pointer (signals, imfs, m,
+ * mask_len, n_imfs, sig_status, diag) is a HOST pointer.  The plan copies the
+ * inputs to its device staging buffers, runs the batch and copies the results
+ * back; returns after the results are in host memory (blocking).  Pinned host
+ * memory makes the copies asynchronous DMA. */
+fif_status fif_decompose_batch_host(fif_plan_t plan, const float* signals, const int64_t* offsets,
+                                    int64_t batch, float* imfs, const int64_t* out_offsets,
+                                    int32_t* m, int32_t* mask_len, int32_t* n_imfs,
+                                    int32_t* sig_status, fif_imf_diag* diag);
+
+/* Largest n the fused (shared-memory resident) batch path supports on the
+ * current device (0 if the device query fails). */
+int64_t fif_fused_max_n(void);
+
+/* Static string for a status code. */
+const char* fif_status_string(fif_status status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FIF_H */

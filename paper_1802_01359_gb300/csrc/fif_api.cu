@@ -1,0 +1,460 @@
+// Host side of libfif.so: plan lifetime, per-length schedules and tables,
+// argument validation, and the C entry points declared in include/fif.h.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <map>
+#include <vector>
+
+#include "fif_internal.h"
+
+using namespace fif;
+
+namespace {
+
+struct LengthTables {
+  FftSched sched;
+  float2* tw = nullptr;
+  float2* tw_lo = nullptr;
+  float2* wtab = nullptr;
+  double* sin64 = nullptr;
+};
+
+struct BatchLayout {
+  std::vector<int64_t> offsets, out_offsets;
+  // classes: contiguous ranges of the sorted signal list sharing one length
+  struct Cls {
+    int first, count, smem, threads, grid, E;
+  };
+  std::vector<Cls> classes;
+  SigDesc* d_sigs = nullptr;
+  FftSched* d_scheds = nullptr;
+  int* d_counters = nullptr;
+};
+
+}  // namespace
+
+struct fif_plan_s {
+  fif_plan_desc desc;
+  MethodParams mp;
+  cudaStream_t stream = nullptr;
+  int num_sms = 0;
+  int smem_optin = 0;
+  std::map<int64_t, LengthTables> tables;
+  StagedScratch scr{};
+  int64_t scr_n = 0;
+  BatchLayout layout;
+  bool layout_valid = false;
+  // host-buffer entry point staging
+  void* h2d_buf = nullptr;
+  size_t h2d_cap = 0;
+};
+
+namespace {
+
+bool is_smooth(int64_t n) {
+  if (n < 1) return false;
+  while (n % 2 == 0) n /= 2;
+  while (n % 3 == 0) n /= 3;
+  return n == 1;
+}
+
+// Pick elements-per-thread E and the radix passes for a complex FFT of Nc
+// points (Nc = 2^p 3^q).  Every radix must divide E (a thread holds E/R
+// butterflies of one pass in registers); T = Nc/E threads, at most 512.
+bool make_fft_plan(int Nc, FftSched& s) {
+  int p = 0, q = 0, r = Nc;
+  while (r % 2 == 0) r /= 2, p++;
+  while (r % 3 == 0) r /= 3, q++;
+  if (r != 1) return false;
+  static const int prefs[] = {16, 24, 12, 18, 9, 27, 8, 6, 4, 3, 2};
+  for (int E : prefs) {
+    if (Nc % E) continue;
+    if (q > 0 && E % 3) continue;
+    if (p > 0 && E % 2) continue;
+    if (Nc / E > 512) continue;
+    s.E = E;
+    s.T = Nc / E;
+    s.npass = 0;
+    for (int i = 0; i < q; i++) s.radix[s.npass++] = 3;
+    int rem2 = 1 << p;
+    while (rem2 > 1) {
+      int R = 2;
+      for (int c : {16, 8, 4}) {
+        if (E % c == 0 && rem2 % c == 0) {
+          R = c;
+          break;
+        }
+      }
+      if (s.npass >= kMaxPass) return false;
+      s.radix[s.npass++] = R;
+      rem2 /= R;
+    }
+    return true;
+  }
+  return false;
+}
+
+bool make_sched(int64_t n64, FftSched& s) {
+  if (n64 < 4 || n64 > (1 << 24) || !is_smooth(n64)) return false;
+  const int n = (int)n64;
+  memset(&s, 0, sizeof(s));
+  s.n = n;
+  s.odd = n & 1;
+  s.Nc = s.odd ? n : n / 2;
+  s.P = s.odd ? (n + 1) / 2 : n / 2 + 1;
+  s.Lmax = (n + 1) / 2;
+  return make_fft_plan(s.Nc, s);
+}
+
+fif_status cuda_status(cudaError_t e) {
+  if (e == cudaSuccess) return FIF_OK;
+  if (e == cudaErrorMemoryAllocation) return FIF_ENOMEM;
+  return FIF_ECUDA;
+}
+
+int device_smem_optin() {
+  int dev = 0, v = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+  if (cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
+    return 0;
+  return v;
+}
+
+bool fused_fits(const FftSched& s, int smem_optin) {
+  return fused_smem_bytes(s) <= (size_t)smem_optin;
+}
+
+bool staged_fits(const FftSched& s, int smem_optin) {
+  const size_t work = work_points(s) * sizeof(float2);
+  const size_t ffb = (size_t)s.Nc * 16;
+  return (work > ffb ? work : ffb) + 1024 <= (size_t)smem_optin;
+}
+
+fif_status get_tables(fif_plan_t p, int64_t n, LengthTables** out) {
+  auto it = p->tables.find(n);
+  if (it != p->tables.end()) {
+    *out = &it->second;
+    return FIF_OK;
+  }
+  LengthTables t;
+  if (!make_sched(n, t.sched)) return FIF_EUNSUPPORTED;
+  const FftSched& s = t.sched;
+  cudaError_t e = cudaMalloc(&t.tw, sizeof(float2) * (size_t)s.n);
+  if (e == cudaSuccess) e = cudaMalloc(&t.tw_lo, sizeof(float2) * (size_t)s.n);
+  if (e == cudaSuccess) e = cudaMalloc(&t.sin64, sizeof(double) * (size_t)(s.n / 2 + 1));
+  if (e == cudaSuccess) e = cudaMalloc(&t.wtab, sizeof(float2) * (size_t)s.Lmax * (size_t)s.P);
+  if (e == cudaSuccess)
+    e = build_tables(s.n, s.P, s.Lmax, t.tw, t.tw_lo, t.wtab, t.sin64, p->stream);
+  if (e != cudaSuccess) {
+    cudaFree(t.tw);
+    cudaFree(t.tw_lo);
+    cudaFree(t.sin64);
+    cudaFree(t.wtab);
+    cudaGetLastError();
+    return cuda_status(e);
+  }
+  t.sched.tw = t.tw;
+  t.sched.tw_lo = t.tw_lo;
+  t.sched.wtab = t.wtab;
+  t.sched.sin64 = t.sin64;
+  auto res = p->tables.emplace(n, t);
+  *out = &res.first->second;
+  return FIF_OK;
+}
+
+void free_layout(BatchLayout& l) {
+  cudaFree(l.d_sigs);
+  cudaFree(l.d_scheds);
+  cudaFree(l.d_counters);
+  l = BatchLayout();
+}
+
+fif_status validate_desc(const fif_plan_desc* d) {
+  if (!d) return FIF_EINVAL;
+  if (d->window != FIF_WIN_TRIANGLE) return FIF_EINVAL;
+  if (d->precision != FIF_PREC_FP32) return FIF_EUNSUPPORTED;
+  if (!(d->delta > 0.0) || !isfinite(d->delta)) return FIF_EINVAL;
+  if (d->max_inner < 1 || d->max_inner > (1 << 20)) return FIF_EINVAL;
+  if (d->max_imfs < 0 || d->max_imfs > kMaxImfs) return FIF_EINVAL;
+  if (d->max_n < 4 || d->max_n > (1 << 24)) return FIF_EINVAL;
+  if (d->flags & ~FIF_FORCE_L) return FIF_EINVAL;
+  if (!(d->flags & FIF_FORCE_L)) {
+    if (!(d->nu > 0.0) || !isfinite(d->nu)) return FIF_EINVAL;
+    if (d->mask_scale < 1 || d->mask_scale > 2) return FIF_EINVAL;
+  }
+  return FIF_OK;
+}
+
+// Sort signals by length (longest first), one class per distinct length, and
+// upload the descriptors.  Reused while the same layout is passed again.
+fif_status prepare_layout(fif_plan_t p, const int64_t* offsets, const int64_t* out_offsets,
+                          int64_t batch) {
+  BatchLayout& l = p->layout;
+  if (p->layout_valid && (int64_t)l.out_offsets.size() == batch &&
+      std::equal(l.offsets.begin(), l.offsets.end(), offsets) &&
+      std::equal(l.out_offsets.begin(), l.out_offsets.end(), out_offsets))
+    return FIF_OK;
+  free_layout(l);
+  p->layout_valid = false;
+  std::vector<int> order((size_t)batch);
+  for (int64_t i = 0; i < batch; i++) order[(size_t)i] = (int)i;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+    return offsets[a + 1] - offsets[a] > offsets[b + 1] - offsets[b];
+  });
+  std::vector<SigDesc> sigs((size_t)batch);
+  std::vector<FftSched> scheds;
+  std::map<int64_t, int> sched_idx;
+  for (int64_t r = 0; r < batch; r++) {
+    const int i = order[(size_t)r];
+    const int64_t n = offsets[i + 1] - offsets[i];
+    LengthTables* t = nullptr;
+    fif_status st = get_tables(p, n, &t);
+    if (st != FIF_OK) return st;
+    if (!sched_idx.count(n)) {
+      sched_idx[n] = (int)scheds.size();
+      scheds.push_back(t->sched);
+    }
+    sigs[(size_t)r] = SigDesc{offsets[i], out_offsets[i], sched_idx[n], (int)n, i, 0};
+    if (r == 0 || sigs[(size_t)r - 1].n != (int)n) {
+      const int smem = (int)fused_smem_bytes(t->sched);
+      const int threads = sched_threads(t->sched);
+      l.classes.push_back(BatchLayout::Cls{(int)r, 0, smem, threads, 0, t->sched.E});
+    }
+    l.classes.back().count++;
+  }
+  for (auto& c : l.classes) {
+    const int occ = fused_blocks_per_sm(c.E, c.smem, c.threads);
+    if (occ <= 0) return FIF_EUNSUPPORTED;
+    c.grid = std::min(c.count, occ * p->num_sms);
+  }
+  cudaError_t e = cudaMalloc(&l.d_sigs, sizeof(SigDesc) * (size_t)std::max<int64_t>(batch, 1));
+  if (e == cudaSuccess) e = cudaMalloc(&l.d_scheds, sizeof(FftSched) * std::max<size_t>(scheds.size(), 1));
+  if (e == cudaSuccess) e = cudaMalloc(&l.d_counters, sizeof(int) * std::max<size_t>(l.classes.size(), 1));
+  if (e == cudaSuccess && batch)
+    e = cudaMemcpyAsync(l.d_sigs, sigs.data(), sizeof(SigDesc) * (size_t)batch,
+                        cudaMemcpyHostToDevice, p->stream);
+  if (e == cudaSuccess && !scheds.empty())
+    e = cudaMemcpyAsync(l.d_scheds, scheds.data(), sizeof(FftSched) * scheds.size(),
+                        cudaMemcpyHostToDevice, p->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
+  if (e != cudaSuccess) {
+    free_layout(l);
+    return cuda_status(e);
+  }
+  l.offsets.assign(offsets, offsets + batch + 1);
+  l.out_offsets.assign(out_offsets, out_offsets + batch);
+  p->layout_valid = true;
+  return FIF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* fif_status_string(fif_status s) {
+  switch (s) {
+    case FIF_OK: return "FIF_OK";
+    case FIF_EINVAL: return "FIF_EINVAL: invalid argument";
+    case FIF_ENOMEM: return "FIF_ENOMEM: device allocation failed";
+    case FIF_ECUDA: return "FIF_ECUDA: CUDA runtime or launch error";
+    case FIF_ETIMEOUT: return "FIF_ETIMEOUT: bounded device wait gave up";
+    case FIF_EUNSUPPORTED: return "FIF_EUNSUPPORTED: request not implemented";
+  }
+  return "unknown fif_status";
+}
+
+int64_t fif_fused_max_n(void) {
+  const int optin = device_smem_optin();
+  if (optin <= 0) return 0;
+  int64_t best = 0;
+  for (int64_t p3 = 1; p3 <= (1 << 24); p3 *= 3) {
+    for (int64_t n = p3; n <= (1 << 24); n *= 2) {
+      FftSched s;
+      if (n > best && make_sched(n, s) && fused_fits(s, optin)) best = n;
+    }
+  }
+  return best;
+}
+
+fif_status fif_plan_create(fif_plan_t* out, const fif_plan_desc* desc, void* cuda_stream) {
+  if (!out) return FIF_EINVAL;
+  *out = nullptr;
+  fif_status st = validate_desc(desc);
+  if (st != FIF_OK) return st;
+  fif_plan_s* p = new (std::nothrow) fif_plan_s();
+  if (!p) return FIF_ENOMEM;
+  p->desc = *desc;
+  p->mp.nu = desc->nu;
+  p->mp.delta = desc->delta;
+  p->mp.mask_scale = desc->mask_scale;
+  p->mp.max_inner = desc->max_inner;
+  p->mp.max_imfs = desc->max_imfs;
+  p->mp.force_L = (desc->flags & FIF_FORCE_L) ? 1 : 0;
+  p->stream = (cudaStream_t)cuda_stream;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&p->num_sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e == cudaSuccess) p->smem_optin = device_smem_optin();
+  // scratch of the staged single-signal path, sized for max_n
+  const int64_t n = desc->max_n;
+  if (e == cudaSuccess) e = cudaMalloc(&p->scr.spec, sizeof(float2) * (size_t)(n / 2 + 2));
+  if (e == cudaSuccess) e = cudaMalloc(&p->scr.work, sizeof(float2) * (size_t)(n + 2));
+  if (e == cudaSuccess) e = cudaMalloc(&p->scr.rem, sizeof(float) * (size_t)n);
+  if (e == cudaSuccess) e = cudaMalloc(&p->scr.state, sizeof(int) * 16);
+  if (e != cudaSuccess) {
+    fif_plan_destroy(p);
+    cudaGetLastError();
+    return cuda_status(e);
+  }
+  p->scr_n = n;
+  *out = p;
+  return FIF_OK;
+}
+
+fif_status fif_plan_destroy(fif_plan_t p) {
+  if (!p) return FIF_OK;
+  cudaStreamSynchronize(p->stream);
+  for (auto& kv : p->tables) {
+    cudaFree(kv.second.tw);
+    cudaFree(kv.second.tw_lo);
+    cudaFree(kv.second.wtab);
+    cudaFree(kv.second.sin64);
+  }
+  free_layout(p->layout);
+  cudaFree(p->scr.spec);
+  cudaFree(p->scr.work);
+  cudaFree(p->scr.rem);
+  cudaFree(p->scr.state);
+  cudaFree(p->h2d_buf);
+  delete p;
+  return FIF_OK;
+}
+
+fif_status fif_plan_set_stream(fif_plan_t p, void* cuda_stream) {
+  if (!p) return FIF_EINVAL;
+  p->stream = (cudaStream_t)cuda_stream;
+  return FIF_OK;
+}
+
+fif_status fif_plan_prepare(fif_plan_t p, const int64_t* lengths, int64_t count) {
+  if (!p || count < 0 || (count > 0 && !lengths)) return FIF_EINVAL;
+  for (int64_t i = 0; i < count; i++) {
+    if (lengths[i] > p->desc.max_n) return FIF_EUNSUPPORTED;
+    LengthTables* t = nullptr;
+    fif_status st = get_tables(p, lengths[i], &t);
+    if (st != FIF_OK) return st;
+  }
+  return cuda_status(cudaStreamSynchronize(p->stream));
+}
+
+fif_status fif_decompose(fif_plan_t p, const float* signal, int64_t n, float* imfs, int32_t* m,
+                         int32_t* mask_len, int32_t* n_imfs, int32_t* sig_status,
+                         fif_imf_diag* diag) {
+  if (!p || !signal || !imfs || !n_imfs || !sig_status) return FIF_EINVAL;
+  if (p->desc.max_imfs > 0 && (!m || !mask_len)) return FIF_EINVAL;
+  if (n < 4 || n > p->desc.max_n) return n < 4 ? FIF_EINVAL : FIF_EUNSUPPORTED;
+  LengthTables* t = nullptr;
+  fif_status st = get_tables(p, n, &t);
+  if (st != FIF_OK) return st;
+  if (!staged_fits(t->sched, p->smem_optin) || t->sched.T > 512) return FIF_EUNSUPPORTED;
+  Outputs o{imfs, m, mask_len, n_imfs, sig_status, diag};
+  return cuda_status(launch_staged(t->sched, nullptr, p->mp, signal, o, p->scr, p->stream));
+}
+
+static fif_status check_batch(fif_plan_t p, const float* signals, const int64_t* offsets,
+                              int64_t batch, const float* imfs, const int64_t* out_offsets,
+                              const int32_t* m, const int32_t* mask_len, const int32_t* n_imfs,
+                              const int32_t* sig_status) {
+  if (!p || batch < 0 || batch > (1LL << 30)) return FIF_EINVAL;
+  if (batch == 0) return FIF_OK;
+  if (!signals || !offsets || !imfs || !out_offsets || !n_imfs || !sig_status) return FIF_EINVAL;
+  if (p->desc.max_imfs > 0 && (!m || !mask_len)) return FIF_EINVAL;
+  if (offsets[0] != 0) return FIF_EINVAL;
+  for (int64_t i = 0; i < batch; i++) {
+    const int64_t n = offsets[i + 1] - offsets[i];
+    if (n < 4 || out_offsets[i] < 0) return FIF_EINVAL;
+    if (n > p->desc.max_n || !is_smooth(n)) return FIF_EUNSUPPORTED;
+    FftSched s;
+    if (!make_sched(n, s) || !fused_fits(s, p->smem_optin)) return FIF_EUNSUPPORTED;
+  }
+  return FIF_OK;
+}
+
+fif_status fif_decompose_batch(fif_plan_t p, const float* signals, const int64_t* offsets,
+                               int64_t batch, float* imfs, const int64_t* out_offsets, int32_t* m,
+                               int32_t* mask_len, int32_t* n_imfs, int32_t* sig_status,
+                               fif_imf_diag* diag) {
+  fif_status st = check_batch(p, signals, offsets, batch, imfs, out_offsets, m, mask_len, n_imfs,
+                              sig_status);
+  if (st != FIF_OK || batch == 0) return st;
+  st = prepare_layout(p, offsets, out_offsets, batch);
+  if (st != FIF_OK) return st;
+  Outputs o{imfs, m, mask_len, n_imfs, sig_status, diag};
+  const BatchLayout& l = p->layout;
+  for (size_t c = 0; c < l.classes.size(); c++) {
+    const auto& cl = l.classes[c];
+    cudaError_t e = launch_fused(cl.E, l.d_sigs + cl.first, cl.count, l.d_scheds, cl.smem, cl.threads,
+                                 cl.grid, p->mp, signals, o, l.d_counters + c, p->stream);
+    if (e != cudaSuccess) return cuda_status(e);
+  }
+  return FIF_OK;
+}
+
+fif_status fif_decompose_batch_host(fif_plan_t p, const float* signals, const int64_t* offsets,
+                                    int64_t batch, float* imfs, const int64_t* out_offsets,
+                                    int32_t* m, int32_t* mask_len, int32_t* n_imfs,
+                                    int32_t* sig_status, fif_imf_diag* diag) {
+  fif_status st = check_batch(p, signals, offsets, batch, imfs, out_offsets, m, mask_len, n_imfs,
+                              sig_status);
+  if (st != FIF_OK || batch == 0) return st;
+  const int K1 = p->desc.max_imfs + 1;
+  int64_t out_len = 0;
+  for (int64_t i = 0; i < batch; i++)
+    out_len = std::max(out_len, out_offsets[i] + (offsets[i + 1] - offsets[i]) * K1);
+  const size_t in_b = sizeof(float) * (size_t)offsets[batch];
+  const size_t out_b = sizeof(float) * (size_t)out_len;
+  const size_t mi_b = sizeof(int32_t) * (size_t)batch * (size_t)p->desc.max_imfs;
+  const size_t si_b = sizeof(int32_t) * (size_t)batch;
+  const size_t dg_b = diag ? sizeof(fif_imf_diag) * (size_t)batch * (size_t)K1 : 0;
+  auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
+  const size_t need = al(in_b) + al(out_b) + 2 * al(mi_b) + 2 * al(si_b) + al(dg_b);
+  if (need > p->h2d_cap) {
+    cudaFree(p->h2d_buf);
+    p->h2d_buf = nullptr;
+    p->h2d_cap = 0;
+    cudaError_t e = cudaMalloc(&p->h2d_buf, need);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return cuda_status(e);
+    }
+    p->h2d_cap = need;
+  }
+  char* base = (char*)p->h2d_buf;
+  float* d_in = (float*)base;
+  float* d_out = (float*)(base += al(in_b));
+  int32_t* d_m = (int32_t*)(base += al(out_b));
+  int32_t* d_L = (int32_t*)(base += al(mi_b));
+  int32_t* d_nimfs = (int32_t*)(base += al(mi_b));
+  int32_t* d_stat = (int32_t*)(base += al(si_b));
+  fif_imf_diag* d_diag = diag ? (fif_imf_diag*)(base += al(si_b)) : nullptr;
+  cudaStream_t s = p->stream;
+  cudaError_t e = cudaMemcpyAsync(d_in, signals, in_b, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess && p->mp.force_L && mi_b)
+    e = cudaMemcpyAsync(d_L, mask_len, mi_b, cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) return cuda_status(e);
+  st = fif_decompose_batch(p, d_in, offsets, batch, d_out, out_offsets, d_m, d_L, d_nimfs, d_stat,
+                           d_diag);
+  if (st != FIF_OK) return st;
+  e = cudaMemcpyAsync(imfs, d_out, out_b, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess && mi_b) e = cudaMemcpyAsync(m, d_m, mi_b, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess && mi_b) e = cudaMemcpyAsync(mask_len, d_L, mi_b, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(n_imfs, d_nimfs, si_b, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(sig_status, d_stat, si_b, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess && diag) e = cudaMemcpyAsync(diag, d_diag, dg_b, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  return cuda_status(e);
+}
+
+}  // extern "C"

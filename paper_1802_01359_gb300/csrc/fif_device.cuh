@@ -1,0 +1,714 @@
+// Device building blocks of the FIF path: shared-memory Stockham FFTs, the
+// m selection of eq. SD through Parseval, the spectral multiplier, and the
+// remainder update with the extrema count.  Every function here is called by
+// all threads of a CTA (it contains __syncthreads) and works on generic
+// pointers, so the fused kernel passes shared memory and the staged kernels
+// pass global scratch where they do not stage it.
+#pragma once
+
+#include <float.h>
+#include <math.h>
+
+#include "fif_internal.h"
+
+namespace fif {
+
+// ------------------------------------------------------------ complex ops
+
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+__device__ __forceinline__ float2 cconj(float2 a) { return make_float2(a.x, -a.y); }
+__device__ __forceinline__ float2 chalf(float2 a) { return make_float2(0.5f * a.x, 0.5f * a.y); }
+__device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(s * a.x, s * a.y); }
+
+// -i*a for the forward transform, +i*a for the inverse
+template <bool INV>
+__device__ __forceinline__ float2 rot_i(float2 a) {
+  return INV ? make_float2(-a.y, a.x) : make_float2(a.y, -a.x);
+}
+// exp(-i theta) * a (forward) or exp(+i theta) * a (inverse), given cos and sin of theta
+template <bool INV>
+__device__ __forceinline__ float2 rot(float2 a, float c, float s) {
+  const float ss = INV ? s : -s;
+  return make_float2(c * a.x - ss * a.y, c * a.y + ss * a.x);
+}
+
+// ------------------------------------------------- float-float arithmetic
+// A value hi + lo held in two floats (|lo| <= ulp(hi)/2), about 48 significant
+// bits on the FP32 pipe: Knuth's TwoSum and the FMA form of Dekker's
+// TwoProduct, each followed by a fast renormalisation.  The _rn intrinsics
+// are never contracted into FMAs, which would break the error-free steps.
+struct ff {
+  float hi, lo;
+};
+struct __align__(16) ffc {
+  ff re, im;
+};
+
+__device__ __forceinline__ ff ff_neg(ff a) { return ff{-a.hi, -a.lo}; }
+__device__ __forceinline__ ff ff_add(ff a, ff b) {
+  const float s = __fadd_rn(a.hi, b.hi);
+  const float bb = __fsub_rn(s, a.hi);
+  float e = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, bb)), __fsub_rn(b.hi, bb));
+  e = __fadd_rn(e, __fadd_rn(a.lo, b.lo));
+  const float hi = __fadd_rn(s, e);
+  return ff{hi, __fsub_rn(e, __fsub_rn(hi, s))};
+}
+__device__ __forceinline__ ff ff_sub(ff a, ff b) { return ff_add(a, ff_neg(b)); }
+__device__ __forceinline__ ff ff_mul(ff a, ff b) {
+  const float p = __fmul_rn(a.hi, b.hi);
+  float e = __fmaf_rn(a.hi, b.hi, -p);
+  e = __fmaf_rn(a.hi, b.lo, e);
+  e = __fmaf_rn(a.lo, b.hi, e);
+  const float hi = __fadd_rn(p, e);
+  return ff{hi, __fsub_rn(e, __fsub_rn(hi, p))};
+}
+
+__device__ __forceinline__ ffc cadd(ffc a, ffc b) { return ffc{ff_add(a.re, b.re), ff_add(a.im, b.im)}; }
+__device__ __forceinline__ ffc csub(ffc a, ffc b) { return ffc{ff_sub(a.re, b.re), ff_sub(a.im, b.im)}; }
+__device__ __forceinline__ ffc cmul(ffc a, ffc w) {
+  return ffc{ff_sub(ff_mul(a.re, w.re), ff_mul(a.im, w.im)),
+             ff_add(ff_mul(a.re, w.im), ff_mul(a.im, w.re))};
+}
+__device__ __forceinline__ ffc cconj(ffc a) { return ffc{a.re, ff_neg(a.im)}; }
+__device__ __forceinline__ ffc chalf(ffc a) {
+  return ffc{ff{0.5f * a.re.hi, 0.5f * a.re.lo}, ff{0.5f * a.im.hi, 0.5f * a.im.lo}};
+}
+__device__ __forceinline__ ffc cscale(ffc a, ff s) { return ffc{ff_mul(a.re, s), ff_mul(a.im, s)}; }
+template <bool INV>
+__device__ __forceinline__ ffc rot_i(ffc a) {
+  return INV ? ffc{ff_neg(a.im), a.re} : ffc{a.im, ff_neg(a.re)};
+}
+template <bool INV>
+__device__ __forceinline__ ffc rot(ffc a, ff c, ff s) {
+  const ff ss = INV ? s : ff_neg(s);
+  return ffc{ff_sub(ff_mul(c, a.re), ff_mul(ss, a.im)), ff_add(ff_mul(c, a.im), ff_mul(ss, a.re))};
+}
+
+// Butterfly constants for each arithmetic: cos(pi/8), sin(pi/8), sqrt(1/2),
+// sin(2 pi/3); float-float pairs are the binary32 value and the rounded rest.
+template <class Cx>
+struct Kc;
+template <>
+struct Kc<float2> {
+  __device__ static float c16() { return 0.923879532511286756f; }
+  __device__ static float s16() { return 0.382683432365089772f; }
+  __device__ static float r2() { return 0.707106781186547524f; }
+  __device__ static float h3() { return 0.866025403784438647f; }
+  __device__ static float neg(float a) { return -a; }
+};
+template <>
+struct Kc<ffc> {
+  __device__ static ff c16() { return ff{0.9238795042037964f, 2.830748968563057e-08f}; }
+  __device__ static ff s16() { return ff{0.3826834261417389f, 6.2233507236442165e-09f}; }
+  __device__ static ff r2() { return ff{0.7071067690849304f, 1.2101617485882343e-08f}; }
+  __device__ static ff h3() { return ff{0.8660253882408142f, 1.5543625053737742e-08f}; }
+  __device__ static ff neg(ff a) { return ff_neg(a); }
+};
+
+// Twiddle exp(-+2 pi i idx/n) from the plan's table (hi part, and for
+// float-float the rounded rest).
+template <class Cx, bool INV>
+__device__ __forceinline__ Cx load_tw(const FftSched& S, int idx);
+template <>
+__device__ __forceinline__ float2 load_tw<float2, false>(const FftSched& S, int idx) {
+  return __ldg(&S.tw[idx]);
+}
+template <>
+__device__ __forceinline__ float2 load_tw<float2, true>(const FftSched& S, int idx) {
+  return cconj(__ldg(&S.tw[idx]));
+}
+template <>
+__device__ __forceinline__ ffc load_tw<ffc, false>(const FftSched& S, int idx) {
+  const float2 h = __ldg(&S.tw[idx]), l = __ldg(&S.tw_lo[idx]);
+  return ffc{ff{h.x, l.x}, ff{h.y, l.y}};
+}
+template <>
+__device__ __forceinline__ ffc load_tw<ffc, true>(const FftSched& S, int idx) {
+  return cconj(load_tw<ffc, false>(S, idx));
+}
+
+// ------------------------------------------------------- small DFT kernels
+
+template <class Cx, bool INV>
+__device__ __forceinline__ void dft2(Cx* v) {
+  const Cx a = v[0];
+  v[0] = cadd(a, v[1]);
+  v[1] = csub(a, v[1]);
+}
+
+template <class Cx, bool INV>
+__device__ __forceinline__ void dft3(Cx* v) {
+  const Cx t1 = cadd(v[1], v[2]);
+  const Cx t2 = csub(v[0], chalf(t1));
+  const Cx t3 = rot_i<INV>(cscale(csub(v[1], v[2]), Kc<Cx>::h3()));
+  v[0] = cadd(v[0], t1);
+  v[1] = cadd(t2, t3);
+  v[2] = csub(t2, t3);
+}
+
+template <class Cx, bool INV>
+__device__ __forceinline__ void dft4r(Cx& x0, Cx& x1, Cx& x2, Cx& x3) {
+  const Cx t0 = cadd(x0, x2), t1 = csub(x0, x2), t2 = cadd(x1, x3), t3 = rot_i<INV>(csub(x1, x3));
+  x0 = cadd(t0, t2);
+  x2 = csub(t0, t2);
+  x1 = cadd(t1, t3);
+  x3 = csub(t1, t3);
+}
+
+template <class Cx, bool INV>
+__device__ __forceinline__ void dft4(Cx* v) {
+  dft4r<Cx, INV>(v[0], v[1], v[2], v[3]);
+}
+
+// 8 = 4 x 2: four-point DFTs over the even and odd samples, twiddle, pairs.
+template <class Cx, bool INV>
+__device__ __forceinline__ void dft8(Cx* v) {
+  Cx a0 = v[0], a1 = v[2], a2 = v[4], a3 = v[6];
+  Cx b0 = v[1], b1 = v[3], b2 = v[5], b3 = v[7];
+  dft4r<Cx, INV>(a0, a1, a2, a3);
+  dft4r<Cx, INV>(b0, b1, b2, b3);
+  const auto c = Kc<Cx>::r2();
+  b1 = rot<INV>(b1, c, c);
+  b2 = rot_i<INV>(b2);
+  b3 = rot<INV>(b3, Kc<Cx>::neg(c), c);
+  v[0] = cadd(a0, b0);
+  v[4] = csub(a0, b0);
+  v[1] = cadd(a1, b1);
+  v[5] = csub(a1, b1);
+  v[2] = cadd(a2, b2);
+  v[6] = csub(a2, b2);
+  v[3] = cadd(a3, b3);
+  v[7] = csub(a3, b3);
+}
+
+// 16 = 4 x 4: DFT4 over x[4 n1 + n2], twiddle w16^(n2 k1), DFT4 over n2.
+template <class Cx, bool INV>
+__device__ __forceinline__ void dft16(Cx* v) {
+#pragma unroll
+  for (int n2 = 0; n2 < 4; n2++) dft4r<Cx, INV>(v[n2], v[4 + n2], v[8 + n2], v[12 + n2]);
+  // v[4 k1 + n2] now holds Y[n2][k1]
+  const auto C1 = Kc<Cx>::c16(), S1 = Kc<Cx>::s16(), C2 = Kc<Cx>::r2();
+  v[5] = rot<INV>(v[5], C1, S1);
+  v[9] = rot<INV>(v[9], C2, C2);
+  v[13] = rot<INV>(v[13], S1, C1);
+  v[6] = rot<INV>(v[6], C2, C2);
+  v[10] = rot_i<INV>(v[10]);
+  v[14] = rot<INV>(v[14], Kc<Cx>::neg(C2), C2);
+  v[7] = rot<INV>(v[7], S1, C1);
+  v[11] = rot<INV>(v[11], Kc<Cx>::neg(C2), C2);
+  v[15] = rot<INV>(v[15], Kc<Cx>::neg(C1), Kc<Cx>::neg(S1));
+#pragma unroll
+  for (int k1 = 0; k1 < 4; k1++) dft4r<Cx, INV>(v[4 * k1], v[4 * k1 + 1], v[4 * k1 + 2], v[4 * k1 + 3]);
+  // v[4 k1 + k2] now holds X[k1 + 4 k2]: transpose the 4 x 4 block in registers
+  Cx t;
+  t = v[1], v[1] = v[4], v[4] = t;
+  t = v[2], v[2] = v[8], v[8] = t;
+  t = v[3], v[3] = v[12], v[12] = t;
+  t = v[6], v[6] = v[9], v[9] = t;
+  t = v[7], v[7] = v[13], v[13] = t;
+  t = v[11], v[11] = v[14], v[14] = t;
+}
+
+template <class Cx, bool INV, int R>
+__device__ __forceinline__ void butterfly(Cx* v) {
+  if (R == 2) dft2<Cx, INV>(v);
+  if (R == 3) dft3<Cx, INV>(v);
+  if (R == 4) dft4<Cx, INV>(v);
+  if (R == 8) dft8<Cx, INV>(v);
+  if (R == 16) dft16<Cx, INV>(v);
+}
+
+// ------------------------------------------------------- Stockham passes
+
+// One radix-R pass of the self-sorting (Stockham) FFT, in place: every thread
+// first loads its E/R butterflies (inputs at j + r*Nc/R), the CTA
+// synchronises, then each butterfly is twiddled by w_{Ns R}^{r (j mod Ns)},
+// transformed, and stored at (j - j mod Ns) R + j mod Ns + r Ns.
+template <class Cx, bool INV, int R, int E>
+__device__ __forceinline__ void fft_pass(Cx* buf, const FftSched& S, int Ns) {
+  constexpr int NB = E / R;
+  const int tid = threadIdx.x;
+  const int T = S.T;
+  const int stride = S.Nc / R;
+  const bool active = tid < T;
+  Cx v[E];
+  if (active) {
+#pragma unroll
+    for (int t = 0; t < NB; t++) {
+      const int j = tid + t * T;
+#pragma unroll
+      for (int r = 0; r < R; r++) v[t * R + r] = buf[j + r * stride];
+    }
+  }
+  __syncthreads();
+  if (active) {
+    const int twstep = S.n / (Ns * R);
+#pragma unroll
+    for (int t = 0; t < NB; t++) {
+      const int j = tid + t * T;
+      const int k = j % Ns;
+      if (k != 0) {
+#pragma unroll
+        for (int r = 1; r < R; r++) v[t * R + r] = cmul(v[t * R + r], load_tw<Cx, INV>(S, r * k * twstep));
+      }
+      butterfly<Cx, INV, R>(&v[t * R]);
+      const int base = (j - k) * R + k;
+#pragma unroll
+      for (int r = 0; r < R; r++) buf[base + r * Ns] = v[t * R + r];
+    }
+  }
+  __syncthreads();
+}
+
+// The one pass whose radix is not the schedule's main radix (the host emits
+// at most one such pass per transform).  Kept out of line so that its
+// register needs do not add to the main loop's.
+template <class Cx, bool INV, int E>
+__device__ __noinline__ void fft_tail_pass(Cx* buf, const FftSched& S, int Ns, int R) {
+  if constexpr (E % 8 == 0) {
+    if (R == 8) fft_pass<Cx, INV, 8, E>(buf, S, Ns);
+  }
+  if constexpr (E % 4 == 0) {
+    if (R == 4) fft_pass<Cx, INV, 4, E>(buf, S, Ns);
+  }
+  if constexpr (E % 2 == 0) {
+    if (R == 2) fft_pass<Cx, INV, 2, E>(buf, S, Ns);
+  }
+}
+
+template <int E>
+__host__ __device__ constexpr int main_radix() {
+  return E % 16 == 0 ? 16 : E % 8 == 0 ? 8 : E % 4 == 0 ? 4 : E % 2 == 0 ? 2 : 3;
+}
+
+// Complex FFT of S.Nc points in buf (unnormalised).  Forward: exp(-2 pi i jk/Nc).
+// Every radix of the schedule divides E; all but at most one pass use the
+// main radix (largest power of two dividing E, at most 16) or radix 3.
+template <class Cx, bool INV, int E>
+__device__ __forceinline__ void fft_inplace(Cx* buf, const FftSched& S) {
+  constexpr int RM = main_radix<E>();
+  int Ns = 1;
+#pragma unroll 1
+  for (int p = 0; p < S.npass; p++) {
+    const int R = S.radix[p];
+    if (R == RM) {
+      fft_pass<Cx, INV, RM, E>(buf, S, Ns);
+    } else if (E % 3 == 0 && R == 3) {
+      if constexpr (E % 3 == 0 && RM != 3) fft_pass<Cx, INV, 3, E>(buf, S, Ns);
+    } else {
+      fft_tail_pass<Cx, INV, E>(buf, S, Ns, R);
+    }
+    Ns *= R;
+  }
+}
+
+// ------------------------------------------------------------ reductions
+
+struct RedScratch {
+  double d[64];
+};
+
+template <typename T, typename Op>
+__device__ __forceinline__ T warp_reduce(T v, Op op) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = op(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+// Block-wide reduction of two values of type T (float or double) with op;
+// every thread gets the result.  scratch holds >= 64 doubles.
+template <typename T, typename Op>
+__device__ __forceinline__ void block_reduce2(T& a, T& b, Op op, T ident, RedScratch* scratch) {
+  a = warp_reduce(a, op);
+  b = warp_reduce(b, op);
+  T* s = reinterpret_cast<T*>(scratch->d);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  __syncthreads();
+  if (lane == 0) {
+    s[2 * wid] = a;
+    s[2 * wid + 1] = b;
+  }
+  __syncthreads();
+  T x = lane < nw ? s[2 * lane] : ident;
+  T y = lane < nw ? s[2 * lane + 1] : ident;
+  x = warp_reduce(x, op);
+  y = warp_reduce(y, op);
+  a = x;
+  b = y;
+}
+
+struct OpAdd {
+  template <typename T>
+  __device__ __forceinline__ T operator()(T a, T b) const { return a + b; }
+};
+struct OpMax {
+  template <typename T>
+  __device__ __forceinline__ T operator()(T a, T b) const { return a > b ? a : b; }
+};
+
+// ------------------------------------------------------ real transforms
+
+// Forward real FFT in float-float arithmetic, rounded once per bin.  An FP32
+// forward transform leaves round-off of the order 2^-24 ||s|| in every bin;
+// the bins an IMF keeps can hold far less energy than s, so that error
+// would dominate the IMF.  Every later step errs relative to the IMF itself.
+//   x    n real samples (global)
+//   zf   float-float work array of Nc complex points (16 Nc bytes); it may
+//        overlay rem and the float work array of the caller, but must not
+//        overlap spec[0..P) in its first 16 P bytes
+//   spec receives the n/2+1 (even n) or (n+1)/2 (odd n) bins, rounded
+//   rem  receives x (written after the transform)
+// Returns max |x| (every thread), or -1 if x holds a NaN or Inf.
+template <int E>
+__device__ float forward_real(const float* __restrict__ x, float* rem, ffc* zf, float2* spec,
+                              const FftSched& S, RedScratch* red) {
+  const int tid = threadIdx.x, nt = blockDim.x, n = S.n;
+  float amax = 0.f;
+  int bad = 0;
+  if (!S.odd) {
+    for (int t = tid; t < S.Nc; t += nt) {
+      const float a = x[2 * t], b = x[2 * t + 1];
+      zf[t] = ffc{ff{a, 0.f}, ff{b, 0.f}};
+      amax = fmaxf(amax, fmaxf(fabsf(a), fabsf(b)));
+      bad |= !isfinite(a) || !isfinite(b);
+    }
+  } else {
+    for (int t = tid; t < n; t += nt) {
+      const float a = x[t];
+      zf[t] = ffc{ff{a, 0.f}, ff{0.f, 0.f}};
+      amax = fmaxf(amax, fabsf(a));
+      bad |= !isfinite(a);
+    }
+  }
+  bad = __syncthreads_or(bad);
+  float dummy = 0.f;
+  block_reduce2(amax, dummy, OpMax(), 0.f, red);
+  if (bad) return -1.f;
+  fft_inplace<ffc, false, E>(zf, S);
+  if (!S.odd) {
+    // X_k = E + W^k O, X_{Nc-k} = conj(E - W^k O),
+    // E = (Z_k + conj Z_{Nc-k})/2, O = -i (Z_k - conj Z_{Nc-k})/2, W = exp(-2 pi i/n)
+    const int Nc = S.Nc;
+    for (int k = tid; k <= Nc / 2; k += nt) {
+      const ffc zk = zf[k];
+      const ffc zc = cconj(zf[k == 0 ? 0 : Nc - k]);
+      const ffc e = chalf(cadd(zk, zc));
+      const ffc o = rot_i<false>(chalf(csub(zk, zc)));
+      const ffc wo = cmul(load_tw<ffc, false>(S, k), o);
+      const ffc xk = cadd(e, wo);
+      const ffc xc = cconj(csub(e, wo));
+      zf[k] = xk;
+      if (k == 0)
+        spec[Nc] = make_float2(xc.re.hi, xc.im.hi);
+      else
+        zf[Nc - k] = xc;
+    }
+    __syncthreads();
+    for (int k = tid; k < Nc; k += nt) spec[k] = make_float2(zf[k].re.hi, zf[k].im.hi);
+  } else {
+    for (int k = tid; k < S.P; k += nt) spec[k] = make_float2(zf[k].re.hi, zf[k].im.hi);
+  }
+  __syncthreads();
+  for (int i = tid; i < n; i += nt) rem[i] = x[i];
+  __syncthreads();
+  return amax;
+}
+
+// Inverse real FFT of the bins in work[0..P) (in place); afterwards the time
+// sample t is  work[t/2].x or .y (even n)  or  work[t].x (odd n), times n.
+template <int E>
+__device__ void inverse_real(float2* work, const FftSched& S) {
+  const int tid = threadIdx.x, nt = blockDim.x;
+  if (!S.odd) {
+    // Z_k = F + i W^-k G, Z_{Nc-k} = conj(F - i W^-k G),
+    // F = X_k + conj X_{Nc-k}, G = X_k - conj X_{Nc-k}
+    const int Nc = S.Nc;
+    for (int k = tid; k <= Nc / 2; k += nt) {
+      const float2 xk = work[k];
+      const float2 xc = work[Nc - k];
+      const float2 f = make_float2(xk.x + xc.x, xk.y - xc.y);
+      const float2 g = make_float2(xk.x - xc.x, xk.y + xc.y);
+      const float2 wg = cmul(cconj(__ldg(&S.tw[k])), g);
+      const float2 iwg = make_float2(-wg.y, wg.x);
+      work[k] = cadd(f, iwg);
+      if (k != 0) work[Nc - k] = cconj(csub(f, iwg));
+    }
+  } else {
+    const int n = S.n;
+    for (int k = 1 + tid; k < S.P; k += nt) work[n - k] = cconj(work[k]);
+  }
+  __syncthreads();
+  fft_inplace<float2, true, E>(work, S);
+}
+
+// ---------------------------------------------------------- window table
+
+__device__ __forceinline__ const float2* wrow(const FftSched& S, int L) {
+  return S.wtab + (size_t)(L - 1) * (size_t)S.P;
+}
+
+__device__ __forceinline__ float parseval_weight(const FftSched& S, int k) {
+  return (k == 0 || (!S.odd && 2 * k == S.n)) ? 1.f : 2.f;
+}
+
+// w_hat_k in binary64 from the sine table (exact integer argument reduction).
+__device__ __forceinline__ double what64(const FftSched& S, int L, int k) {
+  if (k == 0) return 1.0;
+  const int n = S.n;
+  long long t = ((long long)k * (long long)L) % n;
+  if (t > n - t) t = n - t;
+  const double num = S.sin64[t];
+  const double den = (double)L * S.sin64[k];
+  double w = (num / den) * (num / den);
+  return w > 1.0 ? 1.0 : (w < 0.0 ? 0.0 : w);
+}
+
+// --------------------------------------------------------- m selection
+
+struct MSelState {
+  float sc;      // 1 / max |component| of the spectrum
+  float hlmax;   // max log2(1 - w_hat_k) over bins with energy
+  int flags;
+};
+
+// SD_j in binary64 (Parseval, eq. SD), log-domain normalised so that no
+// weight under- or overflows: weight_k = c_k |r_k|^2 (1 - w_k)^{2(j-1)}.
+static __device__ double exact_sd(const float2* spec, const FftSched& S, int L, int j, RedScratch* red) {
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const double inv_ln2 = 1.4426950408889634;
+  double M = -INFINITY, dummy = -INFINITY;
+  for (int k = tid; k < S.P; k += nt) {
+    const float2 z = spec[k];
+    const double q = (double)parseval_weight(S, k) * ((double)z.x * z.x + (double)z.y * z.y);
+    if (q > 0.0) {
+      double lw = log2(q);
+      if (j > 1) lw += 2.0 * (j - 1) * log1p(-what64(S, L, k)) * inv_ln2;
+      M = fmax(M, lw);
+    }
+  }
+  block_reduce2(M, dummy, OpMax(), (double)-INFINITY, red);
+  double num = 0.0, den = 0.0;
+  if (M > -INFINITY) {
+    for (int k = tid; k < S.P; k += nt) {
+      const float2 z = spec[k];
+      const double q = (double)parseval_weight(S, k) * ((double)z.x * z.x + (double)z.y * z.y);
+      if (q > 0.0) {
+        const double w = what64(S, L, k);
+        double lw = log2(q);
+        if (j > 1) lw += 2.0 * (j - 1) * log1p(-w) * inv_ln2;
+        const double e = exp2(lw - M);
+        den += e;
+        num += e * w * w;
+      }
+    }
+  }
+  block_reduce2(num, den, OpAdd(), 0.0, red);
+  return den > 0.0 ? sqrt(num / den) : 0.0;
+}
+
+// Decide SD_j < delta.  First an FP32 evaluation whose relative error on
+// SD_j^2 is bounded (see margin below); inside the error band, the decision
+// is re-taken on the binary64 value.
+static __device__ bool sd_below(const float2* spec, const FftSched& S, const float2* row, int L, int j,
+                         const MethodParams& mp, MSelState& st, RedScratch* red) {
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const float e2 = 2.f * (float)(j - 1);
+  float num = 0.f, den = 0.f;
+  for (int k = tid; k < S.P; k += nt) {
+    const float2 z = spec[k];
+    const float2 tv = __ldg(&row[k]);
+    const float re = z.x * st.sc, im = z.y * st.sc;
+    const float q = parseval_weight(S, k) * fmaf(re, re, im * im);
+    const float w = (j == 1) ? 1.f : exp2f(e2 * (tv.x - st.hlmax));
+    const float qw = q * w;
+    den += qw;
+    num = fmaf(qw, tv.y * tv.y, num);
+  }
+  block_reduce2(num, den, OpAdd(), 0.f, red);
+  // Error bound of the FP32 value of SD_j^2 relative to the binary64 value on
+  // the same spectrum (u = 2^-24): table rounding of log2(1-w) and of the
+  // subtraction/multiplication in the exponent (<= ln2 u (300 + 4 (j-1)
+  // |hlmax|) for every weight above 2^-150) plus 2 ulp of exp2f per weight,
+  // 3u on w^2, 2u on |r|^2, sequential plus tree summation of the positive
+  // terms, one division.  The band is four times that bound.
+  const float u = 5.9604645e-8f;
+  const float per_thread = (float)((S.P + nt - 1) / nt);
+  const float werr = 0.6931472f * u * (300.f + 4.f * (float)(j - 1) * fabsf(st.hlmax)) + 4.f * u;
+  const float serr = (per_thread + 12.f) * u;
+  const float margin = 4.f * (2.f * werr + 2.f * serr + 8.f * u);
+  const float d2 = (float)(mp.delta * mp.delta);
+  const float ratio = num / den;
+  if (den > 8.27e-25f && ratio == ratio) {  // 2^-80: no weight above the noise floor was lost
+    if (ratio <= d2 * (1.f - margin)) return true;
+    if (ratio >= d2 * (1.f + margin)) return false;
+  }
+  const double sd = exact_sd(spec, S, L, j, red);
+  st.flags |= FIF_FLAG_FP64_TIEBREAK;
+  if (fabs(sd - mp.delta) <= 1e-6 * mp.delta) st.flags |= FIF_FLAG_NEAR_DELTA_TIE;
+  return sd < mp.delta;
+}
+
+// m = first j in [1, max_inner] with SD_j < delta, else max_inner (eq. SD,
+// Sec. 4).  SD_j is non-increasing in j (raising j reweights towards bins
+// with small w_hat, where w_hat^2 is small), so the first crossing is found by
+// testing j = max_inner, then bisecting.
+static __device__ int select_m(const float2* spec, const FftSched& S, int L, const MethodParams& mp,
+                        int& flags, RedScratch* red) {
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const float2* row = wrow(S, L);
+  float amax = 0.f, hlmax = -INFINITY;
+  for (int k = tid; k < S.P; k += nt) {
+    const float2 z = spec[k];
+    const float a = fmaxf(fabsf(z.x), fabsf(z.y));
+    amax = fmaxf(amax, a);
+    if (a > 0.f) hlmax = fmaxf(hlmax, __ldg(&row[k]).x);
+  }
+  block_reduce2(amax, hlmax, OpMax(), -INFINITY, red);
+  MSelState st;
+  st.sc = amax > 0.f ? 1.f / amax : 1.f;
+  st.hlmax = hlmax > -INFINITY ? hlmax : 0.f;
+  st.flags = 0;
+  int m;
+  const int jmax = mp.max_inner;
+  if (!sd_below(spec, S, row, L, jmax, mp, st, red)) {
+    m = jmax;
+    st.flags |= FIF_FLAG_MAX_INNER_HIT;
+  } else {
+    int lo = 0, hi = jmax;
+    while (hi - lo > 1) {
+      const int mid = lo + (hi - lo) / 2;
+      if (sd_below(spec, S, row, L, mid, mp, st, red))
+        hi = mid;
+      else
+        lo = mid;
+    }
+    m = hi;
+  }
+  flags |= st.flags;
+  return m;
+}
+
+// g = (1 - w_hat)^m = 2^(m log2(1 - w_hat)) and 1 - g; 1 - g from expm1 when
+// g is close to 1, where 1 - g would cancel.
+__device__ __forceinline__ void multiplier(int m, float hl, float& g, float& omg) {
+  const float e = (float)m * hl;
+  g = exp2f(e);
+  omg = e > -1.f ? -expm1f(e * 0.693147180559945309f) : 1.f - g;
+}
+
+// IMF spectrum work = (1 - w_hat)^m r_hat (eq. One step_algo) and the
+// spectral remainder update r_hat <- r_hat - IMF_hat = (1 - g) r_hat
+// (Algorithm 2: s = s - s_m).
+static __device__ void apply_multiplier(float2* spec, float2* work, const FftSched& S, int L, int m) {
+  const float2* row = wrow(S, L);
+  for (int k = threadIdx.x; k < S.P; k += blockDim.x) {
+    const float2 z = spec[k];
+    float g, omg;
+    multiplier(m, __ldg(&row[k]).x, g, omg);
+    work[k] = make_float2(g * z.x, g * z.y);
+    spec[k] = make_float2(omg * z.x, omg * z.y);
+  }
+  __syncthreads();
+}
+
+// Time-domain epilogue of one IMF: scale the inverse transform by 1/n, store
+// the IMF row, subtract it from the remainder.  Returns ||IMF||_inf.
+static __device__ float store_imf_update_rem(const float2* work, float* rem, float* out_row,
+                                      const FftSched& S, RedScratch* red) {
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const float inv_n = 1.f / (float)S.n;
+  float imax = 0.f;
+  if (!S.odd) {
+    for (int t = tid; t < S.Nc; t += nt) {
+      const float2 z = work[t];
+      const float a = z.x * inv_n, b = z.y * inv_n;
+      out_row[2 * t] = a;
+      out_row[2 * t + 1] = b;
+      rem[2 * t] -= a;
+      rem[2 * t + 1] -= b;
+      imax = fmaxf(imax, fmaxf(fabsf(a), fabsf(b)));
+    }
+  } else {
+    for (int t = tid; t < S.n; t += nt) {
+      const float a = work[t].x * inv_n;
+      out_row[t] = a;
+      rem[t] -= a;
+      imax = fmaxf(imax, fabsf(a));
+    }
+  }
+  float dummy = 0.f;
+  block_reduce2(imax, dummy, OpMax(), 0.f, red);
+  return imax;
+}
+
+struct ExtremaInfo {
+  int k;
+  int zc;
+  int tie;
+  float rmax;
+};
+
+// Periodic extrema count (index i with d_{i-1} d_i < 0, d_i = r_{i+1} - r_i),
+// zero crossings, and whether the count could change under a perturbation of
+// r of tau/2 (some |d_i| <= tau whose flip would add or remove a pair).
+static __device__ ExtremaInfo count_extrema(const float* rem, int n, float tau, RedScratch* red) {
+  const int tid = threadIdx.x, nt = blockDim.x;
+  int ext = 0, zc = 0, tie = 0;
+  float rmax = 0.f;
+  for (int i = tid; i < n; i += nt) {
+    const int im1 = i == 0 ? n - 1 : i - 1;
+    const int ip1 = i + 1 == n ? 0 : i + 1;
+    const int ip2 = ip1 + 1 == n ? 0 : ip1 + 1;
+    const float a = rem[im1], b = rem[i], c = rem[ip1], d = rem[ip2];
+    const float dm = b - a, d0 = c - b, dp = d - c;
+    ext += (dm > 0.f && d0 < 0.f) || (dm < 0.f && d0 > 0.f);
+    zc += (b > 0.f && c < 0.f) || (b < 0.f && c > 0.f);
+    tie |= fabsf(d0) <= tau && (fabsf(dm) <= tau || fabsf(dp) <= tau || ((dm > 0.f) == (dp > 0.f)));
+    rmax = fmaxf(rmax, fabsf(b));
+  }
+  tie = __syncthreads_or(tie);
+  float fe = (float)ext, fz = (float)zc;  // exact: counts < 2^24
+  block_reduce2(fe, fz, OpAdd(), 0.f, red);
+  float dummy = 0.f;
+  block_reduce2(rmax, dummy, OpMax(), 0.f, red);
+  ExtremaInfo e;
+  e.k = (int)fe;
+  e.zc = (int)fz;
+  e.tie = tie;
+  e.rmax = rmax;
+  return e;
+}
+
+// Outer-loop test before IMF K (Algorithm 2 "while #extrema >= 2", the
+// max_imfs cap, the window limit 2L-1 <= n).  Returns 0 and sets L to
+// continue, else the stop reason.  Same value in every thread.
+__device__ __forceinline__ int outer_test(int k, int K, int n, const MethodParams& mp,
+                                          const int32_t* forced_L, int& L, int& flags) {
+  if (mp.force_L) {
+    if (K == mp.max_imfs) return FIF_STOP_MAX_IMFS;
+    L = forced_L[K];
+    if (L <= 0) return FIF_STOP_FORCED_END;
+    if (2LL * L - 1 > n) return FIF_STOP_MASK;
+    return 0;
+  }
+  if (k < 2) return FIF_STOP_EXTREMA;
+  double t = mp.nu * (double)n;
+  t = t / (double)k;
+  L = mp.mask_scale * (int)floor(t);
+  if (L < 2) {
+    L = 2;
+    flags |= FIF_FLAG_L_CLAMPED;
+  }
+  if (2LL * L - 1 > n) return FIF_STOP_MASK;
+  if (K == mp.max_imfs) return FIF_STOP_MAX_IMFS;
+  return 0;
+}
+
+// Perturbation threshold of the extrema tie test: 2^-17 max|s|.
+__device__ __forceinline__ float tie_tau(float smax) { return smax * 7.62939453125e-06f; }
+
+}  // namespace fif

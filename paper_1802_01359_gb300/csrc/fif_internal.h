@@ -1,0 +1,103 @@
+// Internal definitions shared by the host side and the kernels of libfif.so.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "fif.h"
+
+namespace fif {
+
+constexpr int kMaxPass = 24;     // radix passes per FFT
+constexpr int kEMax = 27;        // complex elements a thread holds during one FFT pass
+constexpr int kMaxImfs = 64;
+
+// FFT and table schedule for one signal length n = 2^a 3^b.
+//   even n: the real transform is a complex FFT of Nc = n/2 points on
+//           z_t = x_{2t} + i x_{2t+1}, plus an O(n) split step;
+//   odd n:  a complex FFT of Nc = n points on the real data.
+// Each FFT pass of radix R runs E/R butterflies per thread on T = Nc/E threads.
+struct FftSched {
+  int n;
+  int Nc;
+  int odd;
+  int P;                       // spectrum bins kept: n/2+1 (even) or (n+1)/2 (odd)
+  int E;
+  int T;
+  int npass;
+  int radix[kMaxPass];
+  int Lmax;                    // largest L with 2L-1 <= n
+  const float2* tw;            // [n]  exp(-2 pi i t/n), rounded from binary64
+  const float2* tw_lo;         // [n]  binary64 value minus tw, rounded (float-float twiddles)
+  const float2* wtab;          // [Lmax * P]  row L-1: {log2(1 - w_hat_k), w_hat_k}
+  const double* sin64;         // [n/2 + 1]  sin(pi t/n) in binary64
+};
+
+// Method parameters as the kernels see them.
+struct MethodParams {
+  double nu;
+  double delta;
+  int mask_scale;
+  int max_inner;
+  int max_imfs;
+  int force_L;
+};
+
+// One signal of a batch launch.
+struct SigDesc {
+  int64_t in_off;
+  int64_t out_off;
+  int sched;                   // index into the schedule array
+  int n;
+  int idx;                     // signal index in the caller's batch (output row)
+  int pad;
+};
+
+struct Outputs {
+  float* imfs;
+  int32_t* m;
+  int32_t* mask_len;
+  int32_t* n_imfs;
+  int32_t* sig_status;
+  fif_imf_diag* diag;
+};
+
+// Shared-memory layout of the fused kernel after a 1 KiB header: the
+// time-domain remainder (n floats, padded to 16 bytes), the complex work array
+// (Nc+1 points for even n, n for odd n) and the spectrum (P points).  The
+// float-float forward transform (16 bytes per point, Nc points) overlays the
+// first two regions (and, for odd n, the start of the third, which it does
+// not read back).
+__host__ __device__ inline size_t rem_bytes(const FftSched& s) { return ((size_t)s.n * sizeof(float) + 15) & ~(size_t)15; }
+__host__ __device__ inline size_t work_points(const FftSched& s) { return (size_t)(s.odd ? s.n : s.Nc + 1); }
+inline size_t fused_smem_bytes(const FftSched& s) {
+  return 1024 + rem_bytes(s) + (work_points(s) + (size_t)s.P) * sizeof(float2);
+}
+
+inline int sched_threads(const FftSched& s) {
+  int t = s.T < 128 ? 128 : s.T;
+  if (s.n <= 256 && t > 64) t = 64;
+  return (t + 31) & ~31;
+}
+
+// Kernel launchers (fif_fused.cu, fif_staged.cu, fif_tables.cu).
+cudaError_t launch_fused(int E, const SigDesc* d_sigs, int nsig, const FftSched* d_scheds,
+                         int smem_bytes, int threads, int grid, const MethodParams& mp,
+                         const float* signals, const Outputs& out, int* d_counter,
+                         cudaStream_t st);
+int fused_blocks_per_sm(int E, int smem_bytes, int threads);
+
+struct StagedScratch {
+  float2* spec;   // [P]
+  float2* work;   // [max(Nc+1, n)]
+  float* rem;     // [n]
+  int* state;     // per-signal loop state
+};
+cudaError_t launch_staged(const FftSched& s, const FftSched* d_sched, const MethodParams& mp,
+                          const float* signal, const Outputs& out, const StagedScratch& scr,
+                          cudaStream_t st);
+
+cudaError_t build_tables(int n, int P, int Lmax, float2* tw, float2* tw_lo, float2* wtab,
+                         double* sin64, cudaStream_t st);
+
+}  // namespace fif

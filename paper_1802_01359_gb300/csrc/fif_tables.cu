@@ -1,0 +1,60 @@
+// Plan-time tables for one signal length n, computed in binary64 on the GPU
+// and rounded once:
+//   tw[t]     = exp(-2 pi i t/n), t = 0..n-1             (FFT twiddles, float2)
+//   tw_lo[t]  = exp(-2 pi i t/n) - tw[t], rounded          (float-float twiddles)
+//   sin64[t]  = sin(pi t/n), t = 0..n/2                  (binary64 tie-break path)
+//   wtab[(L-1) P + k] = { log2(1 - w_hat_k(L)), w_hat_k(L) },  L = 1..Lmax, k = 0..P-1
+// with w_hat_k(L) = [sin(pi k L/n) / (L sin(pi k/n))]^2, w_hat_0 = 1: the
+// eigenvalues of the circulant built from the sampled triangle (eq. Lambdas,
+// eq. eig2; the taps are the autocorrelation of a length-L box).  The paper
+// suggests storing the window's eigenvalues for every support length ahead of
+// time (end of Sec. 3 and Sec. 4); this is that table.
+#include "fif_internal.h"
+
+namespace fif {
+
+__global__ void twiddle_kernel(float2* tw, float2* tw_lo, double* sin64, int n) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < n) {
+    double s, c;
+    sincospi(2.0 * (double)t / (double)n, &s, &c);
+    const float ch = (float)c, sh = (float)(-s);
+    tw[t] = make_float2(ch, sh);
+    tw_lo[t] = make_float2((float)(c - (double)ch), (float)(-s - (double)sh));
+  }
+  if (t <= n / 2) sin64[t] = sinpi((double)t / (double)n);
+}
+
+__global__ void window_kernel(float2* wtab, int n, int P, int Lmax) {
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long total = (long long)Lmax * P;
+  if (idx >= total) return;
+  const int L = (int)(idx / P) + 1;
+  const int k = (int)(idx % P);
+  double w;
+  if (k == 0) {
+    w = 1.0;
+  } else {
+    long long t = ((long long)k * (long long)L) % n;
+    if (t > n - t) t = n - t;
+    const double num = sinpi((double)t / (double)n);
+    const double den = (double)L * sinpi((double)k / (double)n);
+    w = (num / den) * (num / den);
+    w = w > 1.0 ? 1.0 : (w < 0.0 ? 0.0 : w);
+  }
+  const double hl = log1p(-w) * 1.4426950408889634;  // log2(1 - w); -inf at w = 1
+  wtab[idx] = make_float2((float)hl, (float)w);
+}
+
+cudaError_t build_tables(int n, int P, int Lmax, float2* tw, float2* tw_lo, float2* wtab,
+                         double* sin64, cudaStream_t st) {
+  twiddle_kernel<<<(n + 255) / 256, 256, 0, st>>>(tw, tw_lo, sin64, n);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const long long total = (long long)Lmax * P;
+  const long long blocks = (total + 255) / 256;
+  window_kernel<<<(unsigned)blocks, 256, 0, st>>>(wtab, n, P, Lmax);
+  return cudaGetLastError();
+}
+
+}  // namespace fif

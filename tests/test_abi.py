@@ -1,0 +1,94 @@
+"""Host-side checks of the C ABI library (no GPU needed, no kernel launched)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_1802_01359_gb300 import build, fif
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build.build()
+    return fif.load_library()
+
+
+def declared_functions():
+    text = open(os.path.join(ROOT, "include", "fif.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(fif_[a-z_0-9]+)\s*\(", text)))
+
+
+def test_header_declares_the_binding_exports():
+    assert declared_functions() == sorted(fif.EXPORTS)
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+
+
+def test_status_strings(lib):
+    for code in range(6):
+        s = fif.status_string(code)
+        assert s.startswith("FIF_")
+    assert "unknown" in fif.status_string(99)
+
+
+def _desc(**kw):
+    d = dict(window=0, nu=1.6, mask_scale=1, delta=1e-3, max_inner=200, max_imfs=10, precision=0,
+             max_n=4096, flags=0)
+    d.update(kw)
+    return fif.PlanDesc(d["window"], d["nu"], d["mask_scale"], d["delta"], d["max_inner"],
+                        d["max_imfs"], d["precision"], d["max_n"], d["flags"])
+
+
+@pytest.mark.parametrize("bad", [dict(delta=0.0), dict(delta=-1.0), dict(max_inner=0),
+                                 dict(max_imfs=-1), dict(max_imfs=65), dict(max_n=3),
+                                 dict(max_n=(1 << 24) + 1), dict(window=7), dict(mask_scale=0),
+                                 dict(mask_scale=3), dict(nu=0.0), dict(flags=8),
+                                 dict(delta=float("nan"))])
+def test_plan_descriptor_validation(lib, bad):
+    """Invalid descriptors are rejected before any CUDA call."""
+    h = ctypes.c_void_p()
+    rc = lib.fif_plan_create(ctypes.byref(h), ctypes.byref(_desc(**bad)), None)
+    assert rc == fif.FIF_EINVAL and not h.value
+
+
+def test_null_arguments(lib):
+    assert lib.fif_plan_create(None, ctypes.byref(_desc()), None) == fif.FIF_EINVAL
+    h = ctypes.c_void_p()
+    assert lib.fif_plan_create(ctypes.byref(h), None, None) == fif.FIF_EINVAL
+    assert lib.fif_plan_destroy(None) == fif.FIF_OK
+    assert lib.fif_plan_set_stream(None, None) == fif.FIF_EINVAL
+    assert lib.fif_plan_prepare(None, None, 0) == fif.FIF_EINVAL
+    assert lib.fif_decompose(None, None, 0, None, None, None, None, None, None) == fif.FIF_EINVAL
+    assert lib.fif_decompose_batch(None, None, None, 1, None, None, None, None, None, None,
+                                   None) == fif.FIF_EINVAL
+    assert lib.fif_decompose_batch_host(None, None, None, 1, None, None, None, None, None, None,
+                                        None) == fif.FIF_EINVAL
+
+
+def test_split_bf16_precision_not_implemented(lib):
+    h = ctypes.c_void_p()
+    assert lib.fif_plan_create(ctypes.byref(h), ctypes.byref(_desc(precision=1)), None) == \
+        fif.FIF_EUNSUPPORTED
+
+
+def test_binding_fails_loudly_without_library(tmp_path):
+    saved = fif._lib
+    fif._lib = None
+    try:
+        with pytest.raises(RuntimeError, match="no CPU fallback"):
+            fif.load_library(str(tmp_path / "missing.so"))
+    finally:
+        fif._lib = saved
+
+
+def test_out_layout():
+    import numpy as np
+    assert fif.out_layout([4, 6, 8], 2).tolist() == [0, 12, 30]
+    assert np.array_equal(fif.out_layout([], 3), np.zeros(0, dtype=np.int64))

@@ -1,0 +1,214 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle."""
+import math
+
+import numpy as np
+import pytest
+
+import parity
+from paper_1802_01359_gb300 import fif, signals
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def dev():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1802_01359_gb300 import build
+    build.build()
+    return torch.device("cuda:0")
+
+
+def _batch(plan, sigs, dev, diag=True):
+    lens = np.array([s.size for s in sigs], dtype=np.int64)
+    offs = np.zeros(lens.size + 1, dtype=np.int64)
+    offs[1:] = np.cumsum(lens)
+    x = torch.from_numpy(np.concatenate(sigs).astype(np.float32)).to(dev)
+    res = plan.decompose_batch(x, offs, diag=diag)
+    torch.cuda.synchronize()
+    return res
+
+
+def test_single_4096_both_paths(dev, oracle_mod):
+    s = signals.single_4096()
+    ref = oracle_mod.direct(s.astype(np.float64))
+    refA = oracle_mod.iterative(s.astype(np.float64))
+    assert refA["m"].tolist() == ref["m"].tolist() and refA["L"].tolist() == ref["L"].tolist()
+    with fif.Plan(max_n=4096) as plan:
+        res = _batch(plan, [s], dev)
+        rep = parity.compare(res.signal(0), ref)
+        assert rep["diverged_at"] is None and rep["n_imfs"] == 10
+        one = plan.decompose(torch.from_numpy(s).to(dev), diag=True)
+        rep2 = parity.compare(one, ref)
+        assert rep2["diverged_at"] is None
+        # tier A (time-domain iteration) too
+        parity.compare(one, refA)
+        # the staged and fused paths run the same arithmetic
+        a = res.signal(0).imfs.cpu().numpy()
+        b = one.imfs.cpu().numpy()
+        assert np.abs(a - b).max() <= 1e-6 * np.abs(s).max()
+
+
+def test_pure_tone_closed_form(dev, oracle_mod):
+    n, k0, phi = 4096, 8, 0.3
+    j = np.arange(n)
+    s = np.cos(2 * np.pi * k0 * j / n + phi).astype(np.float32)
+    ref = oracle_mod.direct(s.astype(np.float64), max_imfs=1)
+    with fif.Plan(max_n=n, max_imfs=1) as plan:
+        d = _batch(plan, [s], dev).signal(0)
+    assert d.n_imfs == 1 and int(d.mask_len[0]) == 409 and int(d.m[0]) == 200
+    # parity with the oracle on the same float32 input
+    parity.compare(d, ref)
+    # the closed form (1 - w_hat_k0)^200 s holds up to the float32 rounding of the
+    # input, whose spectrum the IMF passes on almost unchanged
+    lam = oracle_mod.window_spectrum(n, 409)[k0]
+    scale = (1 - lam) ** 200
+    imf = d.imfs[0].cpu().numpy().astype(np.float64)
+    assert np.linalg.norm(imf - scale * s) < 1e-7 * np.linalg.norm(s)
+
+
+def test_interior_m_forced_schedule(dev, oracle_mod):
+    """n=64, L=8: SD_j first below 1e-3 at j=13 (closed form, see the oracle pins)."""
+    n = 64
+    j = np.arange(n)
+    s = (np.cos(2 * np.pi * 8 * j / n) + np.cos(2 * np.pi * 4 * j / n)).astype(np.float32)
+    ref = oracle_mod.direct(s.astype(np.float64), force_L=[8], max_imfs=1)
+    assert ref["m"][0] == 13
+    with fif.Plan(max_n=n, max_imfs=1, force_L=True) as plan:
+        x = torch.from_numpy(s).to(dev)
+        offs = np.array([0, n], dtype=np.int64)
+        out = plan.alloc_batch_outputs([n], dev, diag=True)
+        out.mask_len[0, 0] = 8
+        plan.decompose_batch(x, offs, out=out)
+        torch.cuda.synchronize()
+        d = out.signal(0)
+        assert int(d.m[0]) == 13 and d.n_imfs == 1 and d.stop == fif.STOP_MAX_IMFS
+        parity.compare(d, ref)
+        one = plan.decompose(x, mask_len=[8], diag=True)
+        assert int(one.m[0]) == 13
+        parity.compare(one, ref)
+
+
+SMALL_LENGTHS = [4, 6, 8, 12, 16, 18, 24, 27, 32, 36, 48, 54, 64, 81, 96, 128, 162, 243, 256, 384,
+                 486, 512, 729, 768, 1024, 1152, 1536, 2048, 2187, 2304, 3072, 4096, 4608, 6144,
+                 6561, 8192, 9216, 12288, 13824, 16384]
+
+
+@pytest.mark.parametrize("delta", [1e-3, 2e-2])
+def test_mixed_lengths_batch(dev, oracle_mod, delta):
+    """Every supported length class (even and odd, 2^a 3^b) in one batch call."""
+    sigs = [signals.component_signal(50, i, n) for i, n in enumerate(SMALL_LENGTHS)]
+    with fif.Plan(max_n=16384, delta=delta, max_imfs=6) as plan:
+        res = _batch(plan, sigs, dev)
+        for i, s in enumerate(sigs):
+            ref = oracle_mod.direct(s.astype(np.float64), delta=delta, max_imfs=6)
+            parity.compare(res.signal(i), ref)
+
+
+def test_interior_m_cases_random(dev, oracle_mod):
+    """Signals and deltas chosen so that m lands strictly inside [1, max_inner]."""
+    sigs = [signals.component_signal(51, i, 1024) for i in range(12)]
+    ms = []
+    with fif.Plan(max_n=1024, delta=3e-2, max_inner=100, max_imfs=5) as plan:
+        res = _batch(plan, sigs, dev)
+        for i, s in enumerate(sigs):
+            ref = oracle_mod.direct(s.astype(np.float64), delta=3e-2, max_inner=100, max_imfs=5)
+            rep = parity.compare(res.signal(i), ref)
+            ms += list(ref["m"][:len(rep["errors"])])
+    assert any(1 < m < 100 for m in ms)
+
+
+def test_fp64_tiebreak_path(dev, oracle_mod):
+    """delta placed within the FP32 screen's error band of SD_m: the decision must be
+    re-taken in binary64 and still agree with the oracle."""
+    s = signals.component_signal(52, 3, 1024)
+    base = oracle_mod.direct(s.astype(np.float64), delta=3e-2, max_inner=100, max_imfs=1)
+    m0 = int(base["m"][0])
+    assert 1 < m0 < 100
+    delta = float(base["sd_m"][0]) * (1 + 2e-5)       # SD_m just below delta
+    ref = oracle_mod.direct(s.astype(np.float64), delta=delta, max_inner=100, max_imfs=1)
+    assert int(ref["m"][0]) == m0
+    with fif.Plan(max_n=1024, delta=delta, max_inner=100, max_imfs=1) as plan:
+        d = _batch(plan, [s], dev).signal(0)
+    assert d.status & fif.FLAG_FP64_TIEBREAK
+    parity.compare(d, ref)
+
+
+def test_degenerate_inputs(dev):
+    n = 256
+    cases = [np.zeros(n, np.float32), np.full(n, 3.25, np.float32),
+             np.cos(2 * np.pi * np.arange(n) / n).astype(np.float32)]
+    nanv = np.ones(n, np.float32)
+    nanv[17] = np.nan
+    infv = np.ones(n, np.float32)
+    infv[3] = np.inf
+    cases += [nanv, infv]
+    with fif.Plan(max_n=n) as plan:
+        res = _batch(plan, cases, dev)
+        stops = [res.signal(i).stop for i in range(len(cases))]
+        assert stops == [fif.STOP_EXTREMA, fif.STOP_EXTREMA, fif.STOP_MASK, fif.STOP_NONFINITE,
+                         fif.STOP_NONFINITE]
+        for i in range(len(cases)):
+            d = res.signal(i)
+            assert d.n_imfs == 0
+            row = d.imfs[0].cpu().numpy()
+            assert np.array_equal(row, cases[i], equal_nan=True)
+    with fif.Plan(max_n=n, max_imfs=0) as plan:
+        d = _batch(plan, [signals.component_signal(53, 0, n)], dev).signal(0)
+        assert d.n_imfs == 0 and d.stop == fif.STOP_MAX_IMFS
+
+
+def test_invalid_calls_return_errors(dev):
+    with fif.Plan(max_n=1024) as plan:
+        x = torch.zeros(2048, device=dev)
+        with pytest.raises(fif.FifError) as e:
+            plan.decompose_batch(x, np.array([0, 2048]))           # above max_n
+        assert e.value.code == fif.FIF_EUNSUPPORTED
+        with pytest.raises(fif.FifError) as e:
+            plan.decompose_batch(x, np.array([0, 1000]))           # not 2^a 3^b
+        assert e.value.code == fif.FIF_EUNSUPPORTED
+        with pytest.raises(fif.FifError) as e:
+            plan.decompose_batch(x, np.array([0, 2]))              # too short
+        assert e.value.code == fif.FIF_EINVAL
+        with pytest.raises(fif.FifError):
+            plan.decompose(torch.zeros(1000, device=dev))
+
+
+def test_host_entry_point_matches_device_batch(dev):
+    sigs = [signals.component_signal(54, i, n) for i, n in enumerate([512, 2048, 729, 4096])]
+    lens = np.array([s.size for s in sigs])
+    offs = np.concatenate([[0], np.cumsum(lens)]).astype(np.int64)
+    flat = np.concatenate(sigs)
+    with fif.Plan(max_n=4096) as plan:
+        dres = _batch(plan, sigs, dev)
+        hres = plan.decompose_batch_host(flat, offs, diag=True)
+    assert np.array_equal(hres.imfs, dres.imfs.cpu().numpy())
+    assert np.array_equal(hres.m, dres.m.cpu().numpy())
+    assert np.array_equal(hres.n_imfs, dres.n_imfs.cpu().numpy())
+    assert np.array_equal(hres.status, dres.status.cpu().numpy())
+
+
+def test_full_size_batch_sampled(dev, oracle_mod):
+    """1024 x 16384 in the launch configuration the benchmark times; sampled signals
+    against the oracle, every signal against the reconstruction identity."""
+    B, n = 1024, 16384
+    data, offs = signals.batch(signals.W_BATCH_16384, B, n)
+    x = torch.from_numpy(data).to(dev)
+    with fif.Plan(max_n=n) as plan:
+        res = plan.decompose_batch(x, offs, diag=True)
+        torch.cuda.synchronize()
+        nim = res.n_imfs.cpu().numpy()
+        st = res.status.cpu().numpy()
+        assert ((st & 0xFF) > 0).all()
+        imfs = res.imfs.view(B, -1, n)
+        # sum of all rows (IMFs + remainder) reconstructs the input (Algorithm 1 telescopes)
+        rows = torch.arange(imfs.shape[1], device=dev)[None, :, None]
+        mask = rows <= res.n_imfs.to(torch.int64)[:, None, None]
+        recon = torch.where(mask, imfs.double(), torch.zeros((), dtype=torch.float64, device=dev)).sum(1)
+        err = (recon - x.view(B, n).double()).abs().max().item()
+        assert err < 1e-5 * x.abs().max().item()
+        for i in (0, 1, 77, 512, 1023):
+            ref = oracle_mod.direct(data[offs[i]:offs[i + 1]].astype(np.float64))
+            parity.compare(res.signal(i), ref)
