@@ -173,19 +173,26 @@ def parity_summary(res_gpu, refs, idx):
 
 
 def run_reference(args, rank, world):
-    """Reference arm: the FP64 oracle on the host cores, on bounded samples of the workload."""
+    """Reference arm: the FP64 oracle on the host cores, on bounded samples of the workload.
+    The per-step sample is sized from a warm-up step so that the K timed steps take
+    about a minute in total."""
     if rank != 0:
         return
     from paper_1802_01359_gb300 import signals
     threads = os.cpu_count() or 1
-    per_step = max(threads, 16)
-    data, offs = signals.batch(signals.W_BATCH_16384, per_step, N)
-    idx = list(range(per_step))
+    pool = 4 * threads
+    data, offs = signals.batch(signals.W_BATCH_16384, pool, N)
+    t_warm = None
     for _ in range(args.warmup):
-        oracle_sample(data, offs, idx[:threads], threads)
+        _, dt = oracle_sample(data, offs, list(range(threads)), threads)
+        t_warm = dt if t_warm is None else min(t_warm, dt)
+    per_step = int(threads * 60.0 / (max(args.steps, 1) * t_warm))
+    per_step = max(1, min(pool, per_step))
+    idx = list(range(per_step))
+    used = min(threads, per_step)
     t = 0.0
     for _ in range(args.steps):
-        _, dt = oracle_sample(data, offs, idx, threads)
+        _, dt = oracle_sample(data, offs, idx, used)
         t += dt
     value = per_step * N * args.steps / t
     line = {
@@ -194,7 +201,7 @@ def run_reference(args, rank, world):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic", "config": {"workload": WORKLOAD, "batch": BATCH, "n": N,
                                         "step_sample_signals": per_step},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": used, "kind": "oracle",
                          "sample": f"{per_step} signals of the workload per step, FP64 direct "
                                    "method (tier B), one signal per thread"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -205,7 +212,7 @@ def run_reference(args, rank, world):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="fif")
     ap.add_argument("--cpu-sample", type=int, default=48)
