@@ -68,7 +68,8 @@ def build(force: bool = False, verbose: bool = False) -> str:
         for log in ex.map(compile_one, todo):
             if verbose and log:
                 print(log)
-    if todo or not os.path.exists(LIB):
+    if todo or not os.path.exists(LIB) or any(os.path.getmtime(o) > os.path.getmtime(LIB)
+                                               for o in objs):
         tmp = LIB + f".tmp{os.getpid()}"
         cmd = [nvcc] + ARCH + ["-shared", "-cudart", "static", "-o", tmp] + objs
         r = subprocess.run(cmd, capture_output=True, text=True)

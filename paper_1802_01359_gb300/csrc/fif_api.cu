@@ -96,7 +96,9 @@ bool make_fft_plan(int Nc, FftSched& s) {
   return false;
 }
 
-bool make_sched(int64_t n64, FftSched& s) {
+// smem_limit: shared memory per block the fused kernel may use; the folded
+// twiddle table goes to shared memory when it fits under that limit.
+bool make_sched(int64_t n64, FftSched& s, int smem_limit = 0) {
   if (n64 < 4 || n64 > (1 << 24) || !is_smooth(n64)) return false;
   const int n = (int)n64;
   memset(&s, 0, sizeof(s));
@@ -105,6 +107,10 @@ bool make_sched(int64_t n64, FftSched& s) {
   s.Nc = s.odd ? n : n / 2;
   s.P = s.odd ? (n + 1) / 2 : n / 2 + 1;
   s.Lmax = (n + 1) / 2;
+  s.tw_fold = n % 8 == 0 ? 3 : n % 4 == 0 ? 2 : n % 2 == 0 ? 1 : 0;
+  s.tw_entries = s.tw_fold == 0 ? n : (n >> s.tw_fold) + 1;
+  s.tw_shared = 1;
+  if (smem_limit > 0 && fused_smem_bytes(s) > (size_t)smem_limit) s.tw_shared = 0;
   return make_fft_plan(s.Nc, s);
 }
 
@@ -127,7 +133,8 @@ bool fused_fits(const FftSched& s, int smem_optin) {
 }
 
 bool staged_fits(const FftSched& s, int smem_optin) {
-  const size_t work = work_points(s) * sizeof(float2);
+  const size_t work = ((work_points(s) + 1) & ~(size_t)1) * sizeof(float2) +
+                      (size_t)s.tw_entries * sizeof(float2);
   const size_t ffb = (size_t)s.Nc * 16;
   return (work > ffb ? work : ffb) + 1024 <= (size_t)smem_optin;
 }
@@ -139,7 +146,7 @@ fif_status get_tables(fif_plan_t p, int64_t n, LengthTables** out) {
     return FIF_OK;
   }
   LengthTables t;
-  if (!make_sched(n, t.sched)) return FIF_EUNSUPPORTED;
+  if (!make_sched(n, t.sched, p->smem_optin)) return FIF_EUNSUPPORTED;
   const FftSched& s = t.sched;
   cudaError_t e = cudaMalloc(&t.tw, sizeof(float2) * (size_t)s.n);
   if (e == cudaSuccess) e = cudaMalloc(&t.tw_lo, sizeof(float2) * (size_t)s.n);
@@ -272,7 +279,7 @@ int64_t fif_fused_max_n(void) {
   for (int64_t p3 = 1; p3 <= (1 << 24); p3 *= 3) {
     for (int64_t n = p3; n <= (1 << 24); n *= 2) {
       FftSched s;
-      if (n > best && make_sched(n, s) && fused_fits(s, optin)) best = n;
+      if (n > best && make_sched(n, s, optin) && fused_fits(s, optin)) best = n;
     }
   }
   return best;
@@ -377,7 +384,7 @@ static fif_status check_batch(fif_plan_t p, const float* signals, const int64_t*
     if (n < 4 || out_offsets[i] < 0) return FIF_EINVAL;
     if (n > p->desc.max_n || !is_smooth(n)) return FIF_EUNSUPPORTED;
     FftSched s;
-    if (!make_sched(n, s) || !fused_fits(s, p->smem_optin)) return FIF_EUNSUPPORTED;
+    if (!make_sched(n, s, p->smem_optin) || !fused_fits(s, p->smem_optin)) return FIF_EUNSUPPORTED;
   }
   return FIF_OK;
 }

@@ -8,6 +8,7 @@
 
 #include <float.h>
 #include <math.h>
+#include <stdint.h>
 
 #include "fif_internal.h"
 
@@ -224,12 +225,105 @@ __device__ __forceinline__ void butterfly(Cx* v) {
 
 // ------------------------------------------------------- Stockham passes
 
+// Where the FP32 passes take their twiddles from: a folded shared-memory
+// table Q[u] = (cos 2 pi u/n, sin 2 pi u/n), u = 0 .. n/2^fold (fold 3 uses the
+// octant symmetry, 2 the quarter-wave, 1 the half-wave), or the global table.
+struct TwSrc {
+  const float2* q;   // shared table or nullptr
+  const float2* g;   // global table exp(-2 pi i t/n)
+  int n;
+  int fold;
+};
+
+// exp(-2 pi i t/n), 0 <= t < n
+__device__ __forceinline__ float2 tw_value(const TwSrc& ts, int t) {
+  if (!ts.q) return __ldg(&ts.g[t]);
+  const int n = ts.n;
+  if (ts.fold >= 2) {
+    const int quarter = n >> 2;
+    const int qd = (t >= quarter) + (t >= 2 * quarter) + (t >= 3 * quarter);
+    const int u = t - qd * quarter;
+    const bool sw = ts.fold == 3 && u > (n >> 3);
+    const float2 v = ts.q[sw ? quarter - u : u];
+    const float c = sw ? v.y : v.x, s = sw ? v.x : v.y;
+    // exp(-i (qd pi/2 + phi)) with cos phi = c, sin phi = s
+    const float a = (qd & 1) ? s : c, b = (qd & 1) ? c : s;
+    return make_float2((qd == 1 || qd == 2) ? -a : a, qd < 2 ? -b : b);
+  }
+  if (ts.fold == 1) {
+    const int half = n >> 1;
+    const bool h = t >= half;
+    const float2 v = ts.q[h ? t - half : t];
+    return h ? make_float2(-v.x, v.y) : make_float2(v.x, -v.y);
+  }
+  const float2 v = ts.q[t];
+  return make_float2(v.x, -v.y);
+}
+
+template <bool INV>
+__device__ __forceinline__ float2 tw_dir(const TwSrc& ts, int t) {
+  const float2 w = tw_value(ts, t);
+  return INV ? cconj(w) : w;
+}
+
+// Multiply v[1..R-1] by w^r, w = exp(-+2 pi i b/n): w, w^2, w^4, w^8 are looked
+// up, the other powers are products of at most three of them.
+template <bool INV, int R>
+__device__ __forceinline__ void apply_twiddles(float2* v, const TwSrc& ts, int b) {
+  const float2 w1 = tw_dir<INV>(ts, b);
+  if (R == 2) {
+    v[1] = cmul(v[1], w1);
+    return;
+  }
+  const float2 w2 = tw_dir<INV>(ts, 2 * b);
+  v[1] = cmul(v[1], w1);
+  v[2] = cmul(v[2], w2);
+  if (R == 3) return;
+  const float2 w3 = cmul(w2, w1);
+  v[3] = cmul(v[3], w3);
+  if (R == 4) return;
+  const float2 w4 = tw_dir<INV>(ts, 4 * b);
+  v[4] = cmul(v[4], w4);
+  v[5] = cmul(v[5], cmul(w4, w1));
+  v[6] = cmul(v[6], cmul(w4, w2));
+  const float2 w7 = cmul(w4, w3);
+  v[7] = cmul(v[7], w7);
+  if (R == 8) return;
+  const float2 w8 = tw_dir<INV>(ts, 8 * b);
+  v[8] = cmul(v[8], w8);
+  v[9] = cmul(v[9], cmul(w8, w1));
+  v[10] = cmul(v[10], cmul(w8, w2));
+  v[11] = cmul(v[11], cmul(w8, w3));
+  v[12] = cmul(v[12], cmul(w8, w4));
+  v[13] = cmul(v[13], cmul(w8, cmul(w4, w1)));
+  v[14] = cmul(v[14], cmul(w8, cmul(w4, w2)));
+  v[15] = cmul(v[15], cmul(w8, w7));
+}
+
+template <bool INV, int R>
+__device__ __forceinline__ void apply_twiddles(ffc* v, const FftSched& S, int b) {
+#pragma unroll
+  for (int r = 1; r < R; r++) v[r] = cmul(v[r], load_tw<ffc, INV>(S, r * b));
+}
+
+template <class Cx>
+struct TwArg;
+template <>
+struct TwArg<float2> {
+  using type = TwSrc;
+};
+template <>
+struct TwArg<ffc> {
+  using type = FftSched;
+};
+
 // One radix-R pass of the self-sorting (Stockham) FFT, in place: every thread
 // first loads its E/R butterflies (inputs at j + r*Nc/R), the CTA
 // synchronises, then each butterfly is twiddled by w_{Ns R}^{r (j mod Ns)},
 // transformed, and stored at (j - j mod Ns) R + j mod Ns + r Ns.
 template <class Cx, bool INV, int R, int E>
-__device__ __forceinline__ void fft_pass(Cx* buf, const FftSched& S, int Ns) {
+__device__ __forceinline__ void fft_pass(Cx* buf, const FftSched& S,
+                                         const typename TwArg<Cx>::type& tws, int Ns) {
   constexpr int NB = E / R;
   const int tid = threadIdx.x;
   const int T = S.T;
@@ -251,10 +345,7 @@ __device__ __forceinline__ void fft_pass(Cx* buf, const FftSched& S, int Ns) {
     for (int t = 0; t < NB; t++) {
       const int j = tid + t * T;
       const int k = j % Ns;
-      if (k != 0) {
-#pragma unroll
-        for (int r = 1; r < R; r++) v[t * R + r] = cmul(v[t * R + r], load_tw<Cx, INV>(S, r * k * twstep));
-      }
+      if (k != 0) apply_twiddles<INV, R>(&v[t * R], tws, k * twstep);
       butterfly<Cx, INV, R>(&v[t * R]);
       const int base = (j - k) * R + k;
 #pragma unroll
@@ -268,15 +359,16 @@ __device__ __forceinline__ void fft_pass(Cx* buf, const FftSched& S, int Ns) {
 // at most one such pass per transform).  Kept out of line so that its
 // register needs do not add to the main loop's.
 template <class Cx, bool INV, int E>
-__device__ __noinline__ void fft_tail_pass(Cx* buf, const FftSched& S, int Ns, int R) {
+__device__ __noinline__ void fft_tail_pass(Cx* buf, const FftSched& S,
+                                           const typename TwArg<Cx>::type& tws, int Ns, int R) {
   if constexpr (E % 8 == 0) {
-    if (R == 8) fft_pass<Cx, INV, 8, E>(buf, S, Ns);
+    if (R == 8) fft_pass<Cx, INV, 8, E>(buf, S, tws, Ns);
   }
   if constexpr (E % 4 == 0) {
-    if (R == 4) fft_pass<Cx, INV, 4, E>(buf, S, Ns);
+    if (R == 4) fft_pass<Cx, INV, 4, E>(buf, S, tws, Ns);
   }
   if constexpr (E % 2 == 0) {
-    if (R == 2) fft_pass<Cx, INV, 2, E>(buf, S, Ns);
+    if (R == 2) fft_pass<Cx, INV, 2, E>(buf, S, tws, Ns);
   }
 }
 
@@ -289,18 +381,19 @@ __host__ __device__ constexpr int main_radix() {
 // Every radix of the schedule divides E; all but at most one pass use the
 // main radix (largest power of two dividing E, at most 16) or radix 3.
 template <class Cx, bool INV, int E>
-__device__ __forceinline__ void fft_inplace(Cx* buf, const FftSched& S) {
+__device__ __forceinline__ void fft_inplace(Cx* buf, const FftSched& S,
+                                            const typename TwArg<Cx>::type& tws) {
   constexpr int RM = main_radix<E>();
   int Ns = 1;
 #pragma unroll 1
   for (int p = 0; p < S.npass; p++) {
     const int R = S.radix[p];
     if (R == RM) {
-      fft_pass<Cx, INV, RM, E>(buf, S, Ns);
+      fft_pass<Cx, INV, RM, E>(buf, S, tws, Ns);
     } else if (E % 3 == 0 && R == 3) {
-      if constexpr (E % 3 == 0 && RM != 3) fft_pass<Cx, INV, 3, E>(buf, S, Ns);
+      if constexpr (E % 3 == 0 && RM != 3) fft_pass<Cx, INV, 3, E>(buf, S, tws, Ns);
     } else {
-      fft_tail_pass<Cx, INV, E>(buf, S, Ns, R);
+      fft_tail_pass<Cx, INV, E>(buf, S, tws, Ns, R);
     }
     Ns *= R;
   }
@@ -388,7 +481,7 @@ __device__ float forward_real(const float* __restrict__ x, float* rem, ffc* zf, 
   float dummy = 0.f;
   block_reduce2(amax, dummy, OpMax(), 0.f, red);
   if (bad) return -1.f;
-  fft_inplace<ffc, false, E>(zf, S);
+  fft_inplace<ffc, false, E>(zf, S, S);
   if (!S.odd) {
     // X_k = E + W^k O, X_{Nc-k} = conj(E - W^k O),
     // E = (Z_k + conj Z_{Nc-k})/2, O = -i (Z_k - conj Z_{Nc-k})/2, W = exp(-2 pi i/n)
@@ -421,7 +514,7 @@ __device__ float forward_real(const float* __restrict__ x, float* rem, ffc* zf, 
 // Inverse real FFT of the bins in work[0..P) (in place); afterwards the time
 // sample t is  work[t/2].x or .y (even n)  or  work[t].x (odd n), times n.
 template <int E>
-__device__ void inverse_real(float2* work, const FftSched& S) {
+__device__ void inverse_real(float2* work, const FftSched& S, const TwSrc& ts) {
   const int tid = threadIdx.x, nt = blockDim.x;
   if (!S.odd) {
     // Z_k = F + i W^-k G, Z_{Nc-k} = conj(F - i W^-k G),
@@ -432,7 +525,7 @@ __device__ void inverse_real(float2* work, const FftSched& S) {
       const float2 xc = work[Nc - k];
       const float2 f = make_float2(xk.x + xc.x, xk.y - xc.y);
       const float2 g = make_float2(xk.x - xc.x, xk.y + xc.y);
-      const float2 wg = cmul(cconj(__ldg(&S.tw[k])), g);
+      const float2 wg = cmul(cconj(tw_value(ts, k)), g);
       const float2 iwg = make_float2(-wg.y, wg.x);
       work[k] = cadd(f, iwg);
       if (k != 0) work[Nc - k] = cconj(csub(f, iwg));
@@ -442,7 +535,7 @@ __device__ void inverse_real(float2* work, const FftSched& S) {
     for (int k = 1 + tid; k < S.P; k += nt) work[n - k] = cconj(work[k]);
   }
   __syncthreads();
-  fft_inplace<float2, true, E>(work, S);
+  fft_inplace<float2, true, E>(work, S, ts);
 }
 
 // ---------------------------------------------------------- window table
@@ -470,10 +563,19 @@ __device__ __forceinline__ double what64(const FftSched& S, int L, int k) {
 // --------------------------------------------------------- m selection
 
 struct MSelState {
-  float sc;      // 1 / max |component| of the spectrum
+  float sc;      // power-of-two scale of the spectrum (|sc r_k| <= 1 for every k)
   float hlmax;   // max log2(1 - w_hat_k) over bins with energy
   int flags;
 };
+
+// Power of two sc with n * smax * sc <= 1: bounds every bin |r_k| <= n max|s|.
+__device__ __forceinline__ float spectrum_scale(int n, float smax) {
+  const float b = (float)n * smax;
+  if (!(b > 0.f)) return 1.f;
+  int e;
+  frexpf(b, &e);  // b < 2^e
+  return ldexpf(1.f, -e);
+}
 
 // SD_j in binary64 (Parseval, eq. SD), log-domain normalised so that no
 // weight under- or overflows: weight_k = c_k |r_k|^2 (1 - w_k)^{2(j-1)}.
@@ -510,9 +612,42 @@ static __device__ double exact_sd(const float2* spec, const FftSched& S, int L, 
   return den > 0.0 ? sqrt(num / den) : 0.0;
 }
 
-// Decide SD_j < delta.  First an FP32 evaluation whose relative error on
-// SD_j^2 is bounded (see margin below); inside the error band, the decision
-// is re-taken on the binary64 value.
+// Error band of the FP32 value of SD_j^2 relative to the binary64 value on
+// the same spectrum (u = 2^-24): table rounding of log2(1-w) and of the
+// subtraction/multiplication in the exponent (<= ln2 u (300 + 4 (j-1)
+// |hlmax|) for every weight above 2^-150) plus 2 ulp of exp2f per weight,
+// 3u on w^2, 2u on |r|^2, sequential plus tree summation of the positive
+// terms, one division.  The band is four times that bound.
+// The one-pass evaluation (online) also rescales partial sums by exp2f of
+// exponent differences, at most once per term per thread and once per
+// reduction level: another 2 ulp per rescale on the weights.
+__device__ __forceinline__ float screen_margin(const FftSched& S, int j, float hlmax, bool online) {
+  const float u = 5.9604645e-8f;
+  const float per_thread = (float)((S.P + (int)blockDim.x - 1) / (int)blockDim.x);
+  float werr = 0.6931472f * u * (300.f + 4.f * (float)(j - 1) * fabsf(hlmax)) + 4.f * u;
+  if (online) werr += 4.f * u * (per_thread + 10.f);
+  const float serr = (per_thread + 12.f) * u;
+  return 4.f * (2.f * werr + 2.f * serr + 8.f * u);
+}
+
+// Take the decision SD_j < delta from the FP32 ratio num/den if it lies
+// outside the error band, else re-take it on the binary64 value.
+static __device__ bool decide_sd(float num, float den, const float2* spec, const FftSched& S, int L, int j,
+                          const MethodParams& mp, MSelState& st, bool online, RedScratch* red) {
+  const float margin = screen_margin(S, j, st.hlmax, online);
+  const float d2 = (float)(mp.delta * mp.delta);
+  const float ratio = num / den;
+  if (den > 8.27e-25f && ratio == ratio) {  // 2^-80: no weight above the noise floor was lost
+    if (ratio <= d2 * (1.f - margin)) return true;
+    if (ratio >= d2 * (1.f + margin)) return false;
+  }
+  const double sd = exact_sd(spec, S, L, j, red);
+  st.flags |= FIF_FLAG_FP64_TIEBREAK;
+  if (fabs(sd - mp.delta) <= 1e-6 * mp.delta) st.flags |= FIF_FLAG_NEAR_DELTA_TIE;
+  return sd < mp.delta;
+}
+
+// FP32 screen of SD_j with known hlmax: weights exp2(2(j-1)(log2(1-w_k) - hlmax)).
 static __device__ bool sd_below(const float2* spec, const FftSched& S, const float2* row, int L, int j,
                          const MethodParams& mp, MSelState& st, RedScratch* red) {
   const int tid = threadIdx.x, nt = blockDim.x;
@@ -529,27 +664,85 @@ static __device__ bool sd_below(const float2* spec, const FftSched& S, const flo
     num = fmaf(qw, tv.y * tv.y, num);
   }
   block_reduce2(num, den, OpAdd(), 0.f, red);
-  // Error bound of the FP32 value of SD_j^2 relative to the binary64 value on
-  // the same spectrum (u = 2^-24): table rounding of log2(1-w) and of the
-  // subtraction/multiplication in the exponent (<= ln2 u (300 + 4 (j-1)
-  // |hlmax|) for every weight above 2^-150) plus 2 ulp of exp2f per weight,
-  // 3u on w^2, 2u on |r|^2, sequential plus tree summation of the positive
-  // terms, one division.  The band is four times that bound.
-  const float u = 5.9604645e-8f;
-  const float per_thread = (float)((S.P + nt - 1) / nt);
-  const float werr = 0.6931472f * u * (300.f + 4.f * (float)(j - 1) * fabsf(st.hlmax)) + 4.f * u;
-  const float serr = (per_thread + 12.f) * u;
-  const float margin = 4.f * (2.f * werr + 2.f * serr + 8.f * u);
-  const float d2 = (float)(mp.delta * mp.delta);
-  const float ratio = num / den;
-  if (den > 8.27e-25f && ratio == ratio) {  // 2^-80: no weight above the noise floor was lost
-    if (ratio <= d2 * (1.f - margin)) return true;
-    if (ratio >= d2 * (1.f + margin)) return false;
+  return decide_sd(num, den, spec, S, L, j, mp, st, false, red);
+}
+
+struct Online {
+  float M, num, den;
+};
+
+__device__ __forceinline__ Online online_merge(Online a, Online b) {
+  if (a.M < b.M) {
+    const Online t = a;
+    a = b;
+    b = t;
   }
-  const double sd = exact_sd(spec, S, L, j, red);
-  st.flags |= FIF_FLAG_FP64_TIEBREAK;
-  if (fabs(sd - mp.delta) <= 1e-6 * mp.delta) st.flags |= FIF_FLAG_NEAR_DELTA_TIE;
-  return sd < mp.delta;
+  if (b.M == -INFINITY) return a;
+  const float s = exp2f(b.M - a.M);
+  return Online{a.M, fmaf(b.num, s, a.num), fmaf(b.den, s, a.den)};
+}
+
+// The first evaluation (j = max_inner) in one pass: the normalising maximum of
+// the exponents is found on the fly, rescaling the running sums when it grows
+// (the combination is exact up to the rounding of exp2f and the products).
+// Sets st.hlmax for the evaluations that may follow.
+static __device__ bool sd_below_first(const float2* spec, const FftSched& S, const float2* row, int L,
+                               int j, const MethodParams& mp, MSelState& st, RedScratch* red) {
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const float e2 = 2.f * (float)(j - 1);
+  Online o{-INFINITY, 0.f, 0.f};
+  float hlmax = -INFINITY;
+  for (int k = tid; k < S.P; k += nt) {
+    const float2 z = spec[k];
+    if (z.x == 0.f && z.y == 0.f) continue;
+    const float2 tv = __ldg(&row[k]);
+    const float re = z.x * st.sc, im = z.y * st.sc;
+    const float q = parseval_weight(S, k) * fmaf(re, re, im * im);
+    hlmax = fmaxf(hlmax, tv.x);
+    const float e = (j == 1) ? 0.f : e2 * tv.x;
+    if (e == -INFINITY) continue;  // w_hat = 1 (the DC bin): weight 0 for j > 1
+    if (e > o.M) {
+      const float s = exp2f(o.M - e);  // 0 when o.M = -inf
+      o.num *= s;
+      o.den *= s;
+      o.M = e;
+    }
+    const float qw = q * exp2f(e - o.M);
+    o.den += qw;
+    o.num = fmaf(qw, tv.y * tv.y, o.num);
+  }
+  // block-wide merge of (M, num, den) and max of hlmax
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    Online b{__shfl_xor_sync(0xffffffffu, o.M, off), __shfl_xor_sync(0xffffffffu, o.num, off),
+             __shfl_xor_sync(0xffffffffu, o.den, off)};
+    o = online_merge(o, b);
+    hlmax = fmaxf(hlmax, __shfl_xor_sync(0xffffffffu, hlmax, off));
+  }
+  float* s = reinterpret_cast<float*>(red->d);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  __syncthreads();
+  if (lane == 0) {
+    s[4 * wid] = o.M;
+    s[4 * wid + 1] = o.num;
+    s[4 * wid + 2] = o.den;
+    s[4 * wid + 3] = hlmax;
+  }
+  __syncthreads();
+  Online r = lane < nw ? Online{s[4 * lane], s[4 * lane + 1], s[4 * lane + 2]}
+                       : Online{-INFINITY, 0.f, 0.f};
+  float hm = lane < nw ? s[4 * lane + 3] : -INFINITY;
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    Online b{__shfl_xor_sync(0xffffffffu, r.M, off), __shfl_xor_sync(0xffffffffu, r.num, off),
+             __shfl_xor_sync(0xffffffffu, r.den, off)};
+    r = online_merge(r, b);
+    hm = fmaxf(hm, __shfl_xor_sync(0xffffffffu, hm, off));
+  }
+  st.hlmax = hm > -INFINITY ? hm : 0.f;
+  // bring the sums to the same normalisation as sd_below: exponent e2 (hl - hlmax)
+  const float shift = (j == 1 || r.M == -INFINITY) ? 1.f : exp2f(r.M - e2 * st.hlmax);
+  return decide_sd(r.num * shift, r.den * shift, spec, S, L, j, mp, st, true, red);
 }
 
 // m = first j in [1, max_inner] with SD_j < delta, else max_inner (eq. SD,
@@ -557,24 +750,15 @@ static __device__ bool sd_below(const float2* spec, const FftSched& S, const flo
 // with small w_hat, where w_hat^2 is small), so the first crossing is found by
 // testing j = max_inner, then bisecting.
 static __device__ int select_m(const float2* spec, const FftSched& S, int L, const MethodParams& mp,
-                        int& flags, RedScratch* red) {
-  const int tid = threadIdx.x, nt = blockDim.x;
+                               float sc, int& flags, RedScratch* red) {
   const float2* row = wrow(S, L);
-  float amax = 0.f, hlmax = -INFINITY;
-  for (int k = tid; k < S.P; k += nt) {
-    const float2 z = spec[k];
-    const float a = fmaxf(fabsf(z.x), fabsf(z.y));
-    amax = fmaxf(amax, a);
-    if (a > 0.f) hlmax = fmaxf(hlmax, __ldg(&row[k]).x);
-  }
-  block_reduce2(amax, hlmax, OpMax(), -INFINITY, red);
   MSelState st;
-  st.sc = amax > 0.f ? 1.f / amax : 1.f;
-  st.hlmax = hlmax > -INFINITY ? hlmax : 0.f;
+  st.sc = sc;
+  st.hlmax = 0.f;
   st.flags = 0;
   int m;
   const int jmax = mp.max_inner;
-  if (!sd_below(spec, S, row, L, jmax, mp, st, red)) {
+  if (!sd_below_first(spec, S, row, L, jmax, mp, st, red)) {
     m = jmax;
     st.flags |= FIF_FLAG_MAX_INNER_HIT;
   } else {
@@ -643,6 +827,93 @@ static __device__ float store_imf_update_rem(const float2* work, float* rem, flo
   float dummy = 0.f;
   block_reduce2(imax, dummy, OpMax(), 0.f, red);
   return imax;
+}
+
+struct EpiOut {
+  float imax;   // ||IMF||_inf
+  int k;        // extrema of the new remainder
+  int zc;       // zero crossings of the new remainder
+  int tie;      // extrema tie (see count_extrema)
+  float rmax;   // ||r||_inf of the new remainder
+};
+
+// Extrema, zero-crossing and tie terms owned by the sample pair (2t, 2t+1),
+// given r[2t-1 .. 2t+3]: samples 2t and 2t+1, differences d_2t and d_2t+1,
+// crossings (2t, 2t+1) and (2t+1, 2t+2).  Same definitions as count_extrema.
+__device__ __forceinline__ void pair_terms(float rm1, float r0, float r1, float r2, float r3,
+                                           float tau, int& ext, int& zc, int& tie) {
+  const float dm1 = r0 - rm1, d0 = r1 - r0, d1 = r2 - r1, d2 = r3 - r2;
+  ext += (dm1 > 0.f && d0 < 0.f) || (dm1 < 0.f && d0 > 0.f);
+  ext += (d0 > 0.f && d1 < 0.f) || (d0 < 0.f && d1 > 0.f);
+  zc += (r0 > 0.f && r1 < 0.f) || (r0 < 0.f && r1 > 0.f);
+  zc += (r1 > 0.f && r2 < 0.f) || (r1 < 0.f && r2 > 0.f);
+  tie |= fabsf(d0) <= tau && (fabsf(dm1) <= tau || fabsf(d1) <= tau || ((dm1 > 0.f) == (d1 > 0.f)));
+  tie |= fabsf(d1) <= tau && (fabsf(d0) <= tau || fabsf(d2) <= tau || ((d0 > 0.f) == (d2 > 0.f)));
+}
+
+// Time-domain epilogue of one IMF (even n) fused with the extrema count of
+// the new remainder.  Pass 1: the thread of point t (samples 2t, 2t+1) scales
+// the inverse transform by 1/n, stores the IMF row, writes r <- r - IMF, and
+// takes the terms of its pair from its neighbours' new values by warp
+// shuffles.  Pass 2 (after a barrier): the pairs at the edges of each block
+// of 32 points (and the last pair) take their terms from memory.
+static __device__ EpiOut epilogue_extrema_even(const float2* work, float* rem, float* out_row,
+                                               const FftSched& S, float tau, RedScratch* red) {
+  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31;
+  const int Nc = S.Nc, n = S.n;
+  const float inv_n = 1.f / (float)n;
+  const bool vec = (reinterpret_cast<uintptr_t>(out_row) & 7) == 0;
+  float imax = 0.f, rmax = 0.f;
+  int ext = 0, zc = 0, tie = 0;
+  for (int base = tid - lane; base < Nc; base += nt) {
+    const int t = base + lane;
+    const bool act = t < Nc;
+    float ra = 0.f, rb = 0.f;
+    if (act) {
+      const float2 z = work[t];
+      const float a = z.x * inv_n, b = z.y * inv_n;
+      if (vec) {
+        *reinterpret_cast<float2*>(out_row + 2 * t) = make_float2(a, b);
+      } else {
+        out_row[2 * t] = a;
+        out_row[2 * t + 1] = b;
+      }
+      ra = rem[2 * t] - a;
+      rb = rem[2 * t + 1] - b;
+      rem[2 * t] = ra;
+      rem[2 * t + 1] = rb;
+      imax = fmaxf(imax, fmaxf(fabsf(a), fabsf(b)));
+      rmax = fmaxf(rmax, fmaxf(fabsf(ra), fabsf(rb)));
+    }
+    const float p_rb = __shfl_up_sync(0xffffffffu, rb, 1);
+    const float n_ra = __shfl_down_sync(0xffffffffu, ra, 1);
+    const float n_rb = __shfl_down_sync(0xffffffffu, rb, 1);
+    if (act && lane != 0 && lane != 31 && t != Nc - 1) pair_terms(p_rb, ra, rb, n_ra, n_rb, tau, ext, zc, tie);
+  }
+  __syncthreads();
+  const int nblk = (Nc + 31) >> 5;
+  for (int i = tid; i < 2 * nblk; i += nt) {
+    const int b0 = (i >> 1) << 5;
+    const int t = (i & 1) ? min(b0 + 31, Nc - 1) : b0;
+    if ((i & 1) && t == b0) continue;
+    const int s0 = 2 * t;
+    const float rm1 = rem[s0 == 0 ? n - 1 : s0 - 1];
+    const float r0 = rem[s0], r1 = rem[s0 + 1];
+    const float r2 = rem[s0 + 2 >= n ? s0 + 2 - n : s0 + 2];
+    const float r3 = rem[s0 + 3 >= n ? s0 + 3 - n : s0 + 3];
+    pair_terms(rm1, r0, r1, r2, r3, tau, ext, zc, tie);
+  }
+  tie = __syncthreads_or(tie);
+  float fe = (float)ext, fz = (float)zc;  // exact: counts < 2^24
+  block_reduce2(fe, fz, OpAdd(), 0.f, red);
+  block_reduce2(imax, rmax, OpMax(), 0.f, red);
+  EpiOut o;
+  o.imax = imax;
+  o.k = (int)fe;
+  o.zc = (int)fz;
+  o.tie = tie;
+  o.rmax = rmax;
+  return o;
 }
 
 struct ExtremaInfo {

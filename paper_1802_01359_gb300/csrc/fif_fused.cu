@@ -19,7 +19,7 @@ template <int E>
 __device__ void decompose_resident(const FftSched& S, const SigDesc& d, int sig,
                                    const MethodParams& mp, const float* __restrict__ signals,
                                    const Outputs& out, float2* spec, float2* work, float* rem,
-                                   ffc* zf, RedScratch* red) {
+                                   ffc* zf, float2* smtw, RedScratch* red) {
   const int n = S.n, tid = threadIdx.x, nt = blockDim.x;
   const float* x = signals + d.in_off;
   float* orow = out.imfs + d.out_off;
@@ -27,6 +27,13 @@ __device__ void decompose_resident(const FftSched& S, const SigDesc& d, int sig,
   int32_t* L_io = out.mask_len + (size_t)sig * mp.max_imfs;
   fif_imf_diag* dg = out.diag ? out.diag + (size_t)sig * (mp.max_imfs + 1) : nullptr;
 
+  if (smtw) {
+    for (int u = tid; u < S.tw_entries; u += nt) {
+      const float2 w = __ldg(&S.tw[u]);
+      smtw[u] = make_float2(w.x, -w.y);
+    }
+  }
+  const TwSrc ts{smtw, S.tw, n, S.tw_fold};
   const float smax = forward_real<E>(x, rem, zf, spec, S, red);
   if (smax < 0.f) {  // NaN or Inf in the input
     for (int i = tid; i < n; i += nt) orow[i] = x[i];
@@ -38,6 +45,7 @@ __device__ void decompose_resident(const FftSched& S, const SigDesc& d, int sig,
     return;
   }
   const float tau = tie_tau(smax);
+  const float sc = spectrum_scale(n, smax);
   ExtremaInfo e = count_extrema(rem, n, tau, red);
   e.tie = 0;  // the input itself is exact on both sides
   int K = 0, flags = 0, reason = 0;
@@ -56,11 +64,18 @@ __device__ void decompose_resident(const FftSched& S, const SigDesc& d, int sig,
       }
       break;
     }
-    const int m = select_m(spec, S, L, mp, iflags, red);
+    const int m = select_m(spec, S, L, mp, sc, iflags, red);
     apply_multiplier(spec, work, S, L, m);
-    inverse_real<E>(work, S);
-    const float imax = store_imf_update_rem(work, rem, orow + (size_t)K * n, S, red);
-    e = count_extrema(rem, n, tau, red);
+    inverse_real<E>(work, S, ts);
+    float imax;
+    if (!S.odd) {
+      const EpiOut eo = epilogue_extrema_even(work, rem, orow + (size_t)K * n, S, tau, red);
+      imax = eo.imax;
+      e = ExtremaInfo{eo.k, eo.zc, eo.tie, eo.rmax};
+    } else {
+      imax = store_imf_update_rem(work, rem, orow + (size_t)K * n, S, red);
+      e = count_extrema(rem, n, tau, red);
+    }
     if (tid == 0) {
       m_out[K] = m;
       if (!mp.force_L) L_io[K] = L;
@@ -102,7 +117,8 @@ __global__ void __launch_bounds__(512, 1) fused_kernel(const SigDesc* __restrict
     float2* work = reinterpret_cast<float2*>(dyn + rem_bytes(S));
     float2* spec = work + work_points(S);
     ffc* zf = reinterpret_cast<ffc*>(dyn);
-    decompose_resident<E>(S, d, d.idx, mp, signals, out, spec, work, rem, zf, &sh->red);
+    float2* smtw = S.tw_shared ? spec + S.P : nullptr;
+    decompose_resident<E>(S, d, d.idx, mp, signals, out, spec, work, rem, zf, smtw, &sh->red);
     __syncthreads();
   }
 }

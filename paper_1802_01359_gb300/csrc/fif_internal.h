@@ -27,6 +27,10 @@ struct FftSched {
   int npass;
   int radix[kMaxPass];
   int Lmax;                    // largest L with 2L-1 <= n
+  int tw_fold;                 // symmetry folds of the shared twiddle table: 3 (octant, 8 | n),
+                               // 2 (quarter, 4 | n), 1 (half, 2 | n), 0 (none)
+  int tw_entries;              // entries of the shared twiddle table: n / 2^tw_fold + 1
+  int tw_shared;               // 1 if the fused kernel keeps the table in shared memory
   const float2* tw;            // [n]  exp(-2 pi i t/n), rounded from binary64
   const float2* tw_lo;         // [n]  binary64 value minus tw, rounded (float-float twiddles)
   const float2* wtab;          // [Lmax * P]  row L-1: {log2(1 - w_hat_k), w_hat_k}
@@ -70,8 +74,11 @@ struct Outputs {
 // not read back).
 __host__ __device__ inline size_t rem_bytes(const FftSched& s) { return ((size_t)s.n * sizeof(float) + 15) & ~(size_t)15; }
 __host__ __device__ inline size_t work_points(const FftSched& s) { return (size_t)(s.odd ? s.n : s.Nc + 1); }
+__host__ __device__ inline size_t tw_table_bytes(const FftSched& s) {
+  return s.tw_shared ? (((size_t)s.tw_entries * sizeof(float2) + 15) & ~(size_t)15) : 0;
+}
 inline size_t fused_smem_bytes(const FftSched& s) {
-  return 1024 + rem_bytes(s) + (work_points(s) + (size_t)s.P) * sizeof(float2);
+  return 1024 + rem_bytes(s) + (work_points(s) + (size_t)s.P) * sizeof(float2) + tw_table_bytes(s);
 }
 
 inline int sched_threads(const FftSched& s) {

@@ -76,7 +76,8 @@ __global__ void __launch_bounds__(512, 1) staged_select(FftSched S, StagedScratc
     }
     return;
   }
-  const int m = select_m(scr.spec, S, L, mp, iflags, &red);
+  const float sc = spectrum_scale(S.n, __int_as_float(st[ST_SMAX]));
+  const int m = select_m(scr.spec, S, L, mp, sc, iflags, &red);
   if (threadIdx.x == 0) {
     st[ST_L] = L;
     st[ST_M] = m;
@@ -107,12 +108,27 @@ __global__ void __launch_bounds__(512, 1) staged_inverse(FftSched S, StagedScrat
   int* st = scr.state;
   if (st[ST_DONE]) return;
   float2* work = reinterpret_cast<float2*>(smem);
+  float2* smtw = work + ((work_points(S) + 1) & ~(size_t)1);
   for (int k = threadIdx.x; k < S.P; k += blockDim.x) work[k] = scr.work[k];
+  for (int u = threadIdx.x; u < S.tw_entries; u += blockDim.x) {
+    const float2 w = __ldg(&S.tw[u]);
+    smtw[u] = make_float2(w.x, -w.y);
+  }
   __syncthreads();
-  inverse_real<E>(work, S);
+  const TwSrc ts{smtw, S.tw, S.n, S.tw_fold};
+  inverse_real<E>(work, S, ts);
   const int K = st[ST_K];
-  const float imax = store_imf_update_rem(work, scr.rem, out.imfs + (size_t)K * S.n, S, &red);
-  const ExtremaInfo e = count_extrema(scr.rem, S.n, tie_tau(__int_as_float(st[ST_SMAX])), &red);
+  const float tau = tie_tau(__int_as_float(st[ST_SMAX]));
+  float imax;
+  ExtremaInfo e;
+  if (!S.odd) {
+    const EpiOut eo = epilogue_extrema_even(work, scr.rem, out.imfs + (size_t)K * S.n, S, tau, &red);
+    imax = eo.imax;
+    e = ExtremaInfo{eo.k, eo.zc, eo.tie, eo.rmax};
+  } else {
+    imax = store_imf_update_rem(work, scr.rem, out.imfs + (size_t)K * S.n, S, &red);
+    e = count_extrema(scr.rem, S.n, tau, &red);
+  }
   if (threadIdx.x == 0) {
     const int iflags = st[ST_IFLAGS];
     out.m[K] = st[ST_M];
@@ -142,7 +158,8 @@ static cudaError_t launch_staged_e(const FftSched& s, const MethodParams& mp, co
   cudaFuncSetAttribute(staged_forward<E>, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn_max);
   cudaFuncSetAttribute(staged_inverse<E>, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn_max);
   const int threads = sched_threads(s);
-  const size_t work_bytes = work_points(s) * sizeof(float2);
+  const size_t work_bytes = ((work_points(s) + 1) & ~(size_t)1) * sizeof(float2) +
+                            (size_t)s.tw_entries * sizeof(float2);
   const size_t ff_bytes = (size_t)s.Nc * sizeof(ffc);
   staged_forward<E><<<1, threads, ff_bytes, st>>>(s, signal, scr, out, mp);
   cudaError_t e = cudaGetLastError();
