@@ -170,6 +170,35 @@ fif_status fif_decompose_batch_host(fif_plan_t plan, const float* signals, const
                                     int32_t* m, int32_t* mask_len, int32_t* n_imfs,
                                     int32_t* sig_status, fif_imf_diag* diag);
 
+/* ---- allocation-free single-signal entry point ----------------------------
+ * The paper has no counterpart to this; it exists for callers of this
+ * library that cannot allocate device memory at the moment they decompose:
+ * latency-critical code (cudaMalloc synchronises the device and can take
+ * milliseconds), hosts that hand all device memory to their own pool at
+ * start-up, and plug-in integrations that may only allocate during setup.
+ *
+ * Same method, parameters and outputs as fif_decompose, but no plan: desc is
+ * read on every call (desc->max_n is ignored) and every array besides the
+ * caller's inputs and outputs lives in one fixed file-scope device array of
+ * the library (about 0.8 MB, sized for FIF_NOALLOC_MAX_N), which each GPU that
+ * loads the library keeps until the process exits.  The call allocates and
+ * frees nothing.
+ *   - n must be 2^a 3^b with 4 <= n <= FIF_NOALLOC_MAX_N; larger n returns
+ *     FIF_EUNSUPPORTED, smaller FIF_EINVAL.
+ *   - The first call on each device looks up the device address of the array
+ *     (with that device current); make that first call before any stream
+ *     capture.
+ *   - All calls share the array.  Each call rewrites everything it reads from
+ *     it, but calls whose GPU work overlaps (several streams, several host
+ *     threads) race on it and must be serialised by the caller.
+ * Pointers: signal, imfs, m, mask_len, n_imfs, sig_status, diag as in
+ * fif_decompose (device memory); cuda_stream is a cudaStream_t or NULL.
+ * Errors: FIF_EINVAL, FIF_EUNSUPPORTED, FIF_ECUDA. */
+#define FIF_NOALLOC_MAX_N 16384
+fif_status fif_decompose_noalloc(const fif_plan_desc* desc, const float* signal, int64_t n,
+                                 float* imfs, int32_t* m, int32_t* mask_len, int32_t* n_imfs,
+                                 int32_t* sig_status, fif_imf_diag* diag, void* cuda_stream);
+
 /* Largest n the fused (shared-memory resident) batch path supports on the
  * current device (0 if the device query fails). */
 int64_t fif_fused_max_n(void);

@@ -58,3 +58,14 @@ cudaError_t build_tables(int n, int P, int Lmax, float2* tw, float2* tw_lo, floa
 }
 
 }  // namespace fif
+
+namespace fif {
+
+// Twiddles and the binary64 sine table only (no window table), into caller
+// memory.
+cudaError_t build_twiddles(int n, float2* tw, float2* tw_lo, double* sin64, cudaStream_t st) {
+  twiddle_kernel<<<(n + 255) / 256, 256, 0, st>>>(tw, tw_lo, sin64, n);
+  return cudaGetLastError();
+}
+
+}  // namespace fif

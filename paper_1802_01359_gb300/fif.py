@@ -38,7 +38,8 @@ FORCE_L = 1
 # every symbol include/fif.h declares
 EXPORTS = ("fif_plan_create", "fif_plan_destroy", "fif_plan_set_stream", "fif_plan_prepare",
            "fif_decompose", "fif_decompose_batch", "fif_decompose_batch_host", "fif_fused_max_n",
-           "fif_status_string")
+           "fif_status_string", "fif_decompose_noalloc")
+NOALLOC_MAX_N = 16384
 
 
 class FifError(RuntimeError):
@@ -83,6 +84,9 @@ def load_library(path: str = LIB_PATH):
     lib.fif_decompose_batch.argtypes = [vp, fp, i64p, ctypes.c_int64, fp, i64p, i32p, i32p, i32p,
                                         i32p, vp]
     lib.fif_decompose_batch_host.argtypes = lib.fif_decompose_batch.argtypes
+    lib.fif_decompose_noalloc.argtypes = [ctypes.POINTER(PlanDesc), fp, ctypes.c_int64, fp, i32p,
+                                          i32p, i32p, i32p, vp, vp]
+    lib.fif_decompose_noalloc.restype = ctypes.c_int
     lib.fif_fused_max_n.argtypes = []
     lib.fif_fused_max_n.restype = ctypes.c_int64
     lib.fif_status_string.argtypes = [ctypes.c_int]
@@ -296,3 +300,36 @@ class Plan:
             _np_ptr(out["status"]), _np_ptr(out["diag"])), "fif_decompose_batch_host")
         return BatchResult(out["imfs"], oo, lengths, out["m"], out["mask_len"], out["n_imfs"],
                            out["status"], out["diag"], K)
+
+
+def decompose_noalloc(signal, *, nu: float = 1.6, mask_scale: int = 1, delta: float = 1e-3,
+                      max_inner: int = 200, max_imfs: int = 10, mask_len=None, diag: bool = False,
+                      stream=None) -> Decomposition:
+    """fif_decompose_noalloc on one float32 CUDA tensor (no plan, no device allocation
+    inside the library; the output tensors are allocated here by PyTorch)."""
+    import torch
+    assert signal.is_cuda and signal.dtype == torch.float32 and signal.dim() == 1
+    signal = signal.contiguous()
+    n = signal.numel()
+    dev = signal.device
+    K = max_imfs
+    desc = PlanDesc(0, nu, mask_scale, delta, max_inner, max_imfs, 0, n,
+                    FORCE_L if mask_len is not None else 0)
+    imfs = torch.zeros((K + 1, n), dtype=torch.float32, device=dev)
+    m = torch.zeros(max(K, 1), dtype=torch.int32, device=dev)
+    L = torch.zeros(max(K, 1), dtype=torch.int32, device=dev)
+    if mask_len is not None:
+        L[:len(mask_len)] = torch.as_tensor(np.asarray(mask_len, dtype=np.int32), device=dev)
+    nim = torch.zeros(1, dtype=torch.int32, device=dev)
+    st = torch.zeros(1, dtype=torch.int32, device=dev)
+    dg = torch.zeros((K + 1, 4), dtype=torch.int32, device=dev) if diag else None
+    if stream is None:
+        stream = torch.cuda.current_stream(dev)
+    _check(load_library().fif_decompose_noalloc(
+        ctypes.byref(desc), _ptr(signal), n, _ptr(imfs), _ptr(m), _ptr(L), _ptr(nim), _ptr(st),
+        _ptr(dg), ctypes.c_void_p(stream.cuda_stream)), "fif_decompose_noalloc")
+    stream.synchronize()
+    d = None
+    if dg is not None:
+        d = np.ascontiguousarray(dg.cpu().numpy()).view(DIAG_DTYPE).reshape(-1)
+    return Decomposition(imfs, m[:K], L[:K], int(nim.item()), int(st.item()), d)
