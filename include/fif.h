@@ -81,6 +81,9 @@ typedef enum {
 #define FIF_FORCE_L 1  /* mask_len[] is an INPUT: L for IMF K is mask_len[K]; a value <= 0 ends the
                           decomposition (FIF_STOP_FORCED_END).  The extrema test is skipped.  For
                           tests of linearity and worked examples. */
+#define FIF_FORCE_MULTIPASS 2  /* run every signal through the multi-pass path that long signals
+                                  take (FFT passes through global memory), whatever its length;
+                                  for tests that compare the two paths */
 
 typedef struct {
   fif_window window;        /* FIF_WIN_TRIANGLE */
@@ -92,7 +95,7 @@ typedef struct {
   int32_t max_imfs;         /* cap on the number of IMFs (remainder not counted), 0 .. 64 */
   fif_precision precision;  /* FIF_PREC_FP32 */
   int64_t max_n;            /* largest signal length this plan accepts */
-  int32_t flags;            /* 0 or FIF_FORCE_L */
+  int32_t flags;            /* 0 or FIF_FORCE_L | FIF_FORCE_MULTIPASS */
 } fif_plan_desc;
 
 /* Optional per-IMF diagnostics, one record per outer step: record K < n_imfs

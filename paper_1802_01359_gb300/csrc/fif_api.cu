@@ -35,6 +35,26 @@ struct BatchLayout {
 
 }  // namespace
 
+struct LargeTables {
+  LgSched G;
+  std::vector<void*> allocs;
+};
+
+struct LargeBuffers {
+  int64_t n = 0;
+  int cap = 0;                 // signals the buffers hold
+  std::vector<void*> allocs;
+  float4* za = nullptr;
+  float4* zb = nullptr;
+  float2* spec = nullptr;
+  float2* work = nullptr;
+  float2* work2 = nullptr;
+  float* rem = nullptr;
+  float2* row = nullptr;
+  int* st = nullptr;
+  LgSig* d_sigs = nullptr;
+};
+
 struct fif_plan_s {
   fif_plan_desc desc;
   MethodParams mp;
@@ -49,6 +69,9 @@ struct fif_plan_s {
   // host-buffer entry point staging
   void* h2d_buf = nullptr;
   size_t h2d_cap = 0;
+  // large-length path
+  std::map<int64_t, LargeTables> large;
+  std::map<int64_t, LargeBuffers> large_bufs;
 };
 
 namespace {
@@ -186,7 +209,7 @@ fif_status validate_desc(const fif_plan_desc* d) {
   if (d->max_inner < 1 || d->max_inner > (1 << 20)) return FIF_EINVAL;
   if (d->max_imfs < 0 || d->max_imfs > kMaxImfs) return FIF_EINVAL;
   if (d->max_n < 4 || d->max_n > (1 << 24)) return FIF_EINVAL;
-  if (d->flags & ~FIF_FORCE_L) return FIF_EINVAL;
+  if (d->flags & ~(FIF_FORCE_L | FIF_FORCE_MULTIPASS)) return FIF_EINVAL;
   if (!(d->flags & FIF_FORCE_L)) {
     if (!(d->nu > 0.0) || !isfinite(d->nu)) return FIF_EINVAL;
     if (d->mask_scale < 1 || d->mask_scale > 2) return FIF_EINVAL;
@@ -197,7 +220,7 @@ fif_status validate_desc(const fif_plan_desc* d) {
 // Sort signals by length (longest first), one class per distinct length, and
 // upload the descriptors.  Reused while the same layout is passed again.
 fif_status prepare_layout(fif_plan_t p, const int64_t* offsets, const int64_t* out_offsets,
-                          int64_t batch) {
+                          int64_t batch, const std::vector<int>& subset) {
   BatchLayout& l = p->layout;
   if (p->layout_valid && (int64_t)l.out_offsets.size() == batch &&
       std::equal(l.offsets.begin(), l.offsets.end(), offsets) &&
@@ -205,15 +228,15 @@ fif_status prepare_layout(fif_plan_t p, const int64_t* offsets, const int64_t* o
     return FIF_OK;
   free_layout(l);
   p->layout_valid = false;
-  std::vector<int> order((size_t)batch);
-  for (int64_t i = 0; i < batch; i++) order[(size_t)i] = (int)i;
+  std::vector<int> order(subset);
   std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
     return offsets[a + 1] - offsets[a] > offsets[b + 1] - offsets[b];
   });
-  std::vector<SigDesc> sigs((size_t)batch);
+  const int64_t nfused = (int64_t)order.size();
+  std::vector<SigDesc> sigs((size_t)nfused);
   std::vector<FftSched> scheds;
   std::map<int64_t, int> sched_idx;
-  for (int64_t r = 0; r < batch; r++) {
+  for (int64_t r = 0; r < nfused; r++) {
     const int i = order[(size_t)r];
     const int64_t n = offsets[i + 1] - offsets[i];
     LengthTables* t = nullptr;
@@ -236,11 +259,11 @@ fif_status prepare_layout(fif_plan_t p, const int64_t* offsets, const int64_t* o
     if (occ <= 0) return FIF_EUNSUPPORTED;
     c.grid = std::min(c.count, occ * p->num_sms);
   }
-  cudaError_t e = cudaMalloc(&l.d_sigs, sizeof(SigDesc) * (size_t)std::max<int64_t>(batch, 1));
+  cudaError_t e = cudaMalloc(&l.d_sigs, sizeof(SigDesc) * (size_t)std::max<int64_t>(nfused, 1));
   if (e == cudaSuccess) e = cudaMalloc(&l.d_scheds, sizeof(FftSched) * std::max<size_t>(scheds.size(), 1));
   if (e == cudaSuccess) e = cudaMalloc(&l.d_counters, sizeof(int) * std::max<size_t>(l.classes.size(), 1));
-  if (e == cudaSuccess && batch)
-    e = cudaMemcpyAsync(l.d_sigs, sigs.data(), sizeof(SigDesc) * (size_t)batch,
+  if (e == cudaSuccess && nfused)
+    e = cudaMemcpyAsync(l.d_sigs, sigs.data(), sizeof(SigDesc) * (size_t)nfused,
                         cudaMemcpyHostToDevice, p->stream);
   if (e == cudaSuccess && !scheds.empty())
     e = cudaMemcpyAsync(l.d_scheds, scheds.data(), sizeof(FftSched) * scheds.size(),
@@ -253,6 +276,214 @@ fif_status prepare_layout(fif_plan_t p, const int64_t* offsets, const int64_t* o
   l.offsets.assign(offsets, offsets + batch + 1);
   l.out_offsets.assign(out_offsets, out_offsets + batch);
   p->layout_valid = true;
+  return FIF_OK;
+}
+
+}  // namespace
+
+namespace {
+
+bool make_sub_sched(int R, FftSched& s) {
+  memset(&s, 0, sizeof(s));
+  s.n = R;
+  s.Nc = R;
+  s.odd = 1;  // complex transform of R points
+  s.P = R;
+  s.tw_fold = R % 8 == 0 ? 3 : R % 4 == 0 ? 2 : R % 2 == 0 ? 1 : 0;
+  s.tw_entries = s.tw_fold == 0 ? R : (R >> s.tw_fold) + 1;
+  s.tw_shared = 1;
+  return make_fft_plan(R, s);
+}
+
+int pick_tj(int R, int T, int count, size_t elem, size_t extra, int smem_limit) {
+  for (int tj : {4, 3, 2, 1}) {
+    if (count % tj) continue;
+    if (tj * T > 512) continue;
+    if ((size_t)tj * R * elem + extra + 1024 > (size_t)smem_limit) continue;
+    return tj;
+  }
+  return 0;
+}
+
+// Nc = R1 R2 with R1, R2 <= 4096, as balanced as possible.
+bool make_large_sched(int64_t n64, int smem_limit, LgSched& G) {
+  if (n64 < 4 || n64 > (1 << 25) || !is_smooth(n64)) return false;
+  memset(&G, 0, sizeof(G));
+  FftSched& s = G.S;
+  const int n = (int)n64;
+  s.n = n;
+  s.odd = n & 1;
+  s.Nc = s.odd ? n : n / 2;
+  s.P = s.odd ? (n + 1) / 2 : n / 2 + 1;
+  s.Lmax = (n + 1) / 2;
+  const int Nc = s.Nc;
+  int best = 0;
+  for (int d = 1; d <= 4096 && d <= Nc; d++) {
+    if (Nc % d || Nc / d > 4096 || !is_smooth(d)) continue;
+    const int e = Nc / d;
+    if (!best || abs(d - e) < abs(best - Nc / best)) best = d;
+  }
+  if (!best) return false;
+  G.R1 = best >= Nc / best ? best : Nc / best;
+  G.R2 = Nc / G.R1;
+  if (G.R2 < 2) return false;
+  if (!make_sub_sched(G.R1, G.S1) || !make_sub_sched(G.R2, G.S2)) return false;
+  const size_t t1 = (size_t)G.S1.tw_entries * sizeof(float2), t2 = (size_t)G.S2.tw_entries * sizeof(float2);
+  G.TJ1 = pick_tj(G.R1, G.S1.T, G.R2, 8, t1, smem_limit);
+  G.TJ2 = pick_tj(G.R2, G.S2.T, G.R1, 8, t2, smem_limit);
+  G.TJF1 = pick_tj(G.R1, G.S1.T, G.R2, 16, 0, smem_limit);
+  G.TJF2 = pick_tj(G.R2, G.S2.T, G.R1, 16, 0, smem_limit);
+  if (!G.TJ1 || !G.TJ2 || !G.TJF1 || !G.TJF2) return false;
+  int B = 1;
+  while ((int64_t)B * B < Nc) B++;
+  G.B = B;
+  return true;
+}
+
+fif_status get_large(fif_plan_t p, int64_t n, LargeTables** out) {
+  auto it = p->large.find(n);
+  if (it != p->large.end()) {
+    *out = &it->second;
+    return FIF_OK;
+  }
+  LargeTables lt;
+  if (!make_large_sched(n, p->smem_optin, lt.G)) return FIF_EUNSUPPORTED;
+  LgSched& G = lt.G;
+  cudaError_t e = cudaSuccess;
+  auto alloc = [&](size_t bytes) -> void* {
+    void* ptr = nullptr;
+    if (e == cudaSuccess) e = cudaMalloc(&ptr, bytes < 16 ? 16 : bytes);
+    if (e == cudaSuccess) lt.allocs.push_back(ptr);
+    return ptr;
+  };
+  const int n32 = (int)n, Nc = G.S.Nc, nhi = (Nc + G.B - 1) / G.B;
+  float2* tw = (float2*)alloc(sizeof(float2) * n32);
+  float2* twl = (float2*)alloc(sizeof(float2) * n32);
+  double* s64 = (double*)alloc(sizeof(double) * (n32 / 2 + 1));
+  float2* tw1 = (float2*)alloc(sizeof(float2) * G.R1);
+  float2* tw1l = (float2*)alloc(sizeof(float2) * G.R1);
+  double* d1 = (double*)alloc(sizeof(double) * (G.R1 / 2 + 1));
+  float2* tw2 = (float2*)alloc(sizeof(float2) * G.R2);
+  float2* tw2l = (float2*)alloc(sizeof(float2) * G.R2);
+  double* d2 = (double*)alloc(sizeof(double) * (G.R2 / 2 + 1));
+  float2* thi = (float2*)alloc(sizeof(float2) * nhi);
+  float2* thil = (float2*)alloc(sizeof(float2) * nhi);
+  float2* tlo = (float2*)alloc(sizeof(float2) * G.B);
+  float2* tlol = (float2*)alloc(sizeof(float2) * G.B);
+  float2* sff = (float2*)alloc(sizeof(float2) * (n32 / 2 + 1));
+  float2* rff = (float2*)alloc(sizeof(float2) * (n32 / 2 + 1));
+  if (e == cudaSuccess) e = build_twiddles(n32, tw, twl, s64, p->stream);
+  if (e == cudaSuccess) e = build_twiddles(G.R1, tw1, tw1l, d1, p->stream);
+  if (e == cudaSuccess) e = build_twiddles(G.R2, tw2, tw2l, d2, p->stream);
+  G.S.tw = tw;
+  G.S.tw_lo = twl;
+  G.S.sin64 = s64;
+  G.S1.tw = tw1;
+  G.S1.tw_lo = tw1l;
+  G.S2.tw = tw2;
+  G.S2.tw_lo = tw2l;
+  G.thi = thi;
+  G.thi_lo = thil;
+  G.tlo = tlo;
+  G.tlo_lo = tlol;
+  G.sinff = sff;
+  G.rcpff = rff;
+  if (e == cudaSuccess) e = large_build_tables(G, thi, thil, tlo, tlol, sff, rff, p->stream);
+  if (e != cudaSuccess) {
+    for (void* a : lt.allocs) cudaFree(a);
+    cudaGetLastError();
+    return cuda_status(e);
+  }
+  auto res = p->large.emplace(n, lt);
+  *out = &res.first->second;
+  return FIF_OK;
+}
+
+void free_large_buffers(LargeBuffers& b) {
+  for (void* a : b.allocs) cudaFree(a);
+  b = LargeBuffers();
+}
+
+// Working arrays of one large class for nsig signals (grow-only, per length).
+fif_status large_buffers(fif_plan_t p, const LgSched& G, int nsig, LargeBuffers** out) {
+  LargeBuffers& b = p->large_bufs[G.S.n];
+  if (b.cap >= nsig) {
+    *out = &b;
+    return FIF_OK;
+  }
+  cudaStreamSynchronize(p->stream);
+  free_large_buffers(b);
+  const size_t Nc = (size_t)G.S.Nc, n = (size_t)G.S.n, P = (size_t)G.S.P, S = (size_t)nsig;
+  cudaError_t e = cudaSuccess;
+  auto alloc = [&](size_t bytes) -> void* {
+    void* ptr = nullptr;
+    if (e == cudaSuccess) e = cudaMalloc(&ptr, bytes);
+    if (e == cudaSuccess) b.allocs.push_back(ptr);
+    return ptr;
+  };
+  b.za = (float4*)alloc(16 * Nc * S);
+  b.zb = (float4*)alloc(16 * Nc * S);
+  b.spec = (float2*)alloc(8 * (Nc + 1) * S);
+  b.work = (float2*)alloc(8 * (Nc + 1) * S);
+  b.work2 = (float2*)alloc(8 * (Nc + 1) * S);
+  b.rem = (float*)alloc(4 * n * S);
+  b.row = (float2*)alloc(8 * P * S);
+  b.st = (int*)alloc(64 * S);
+  b.d_sigs = (LgSig*)alloc(sizeof(LgSig) * S);
+  if (e != cudaSuccess) {
+    free_large_buffers(b);
+    cudaGetLastError();
+    return cuda_status(e);
+  }
+  b.n = G.S.n;
+  b.cap = nsig;
+  *out = &b;
+  return FIF_OK;
+}
+
+// Run the large path for signals idx[0..count) of one length n.
+fif_status run_large_class(fif_plan_t p, int64_t n, const float* signals, const int64_t* offsets,
+                           const std::vector<int>& idx, float* imfs, const int64_t* out_offsets,
+                           int32_t* m, int32_t* mask_len, int32_t* n_imfs, int32_t* sig_status,
+                           fif_imf_diag* diag, bool single) {
+  LargeTables* lt = nullptr;
+  fif_status s = get_large(p, n, &lt);
+  if (s != FIF_OK) return s;
+  const LgSched& G = lt->G;
+  const int K = p->desc.max_imfs;
+  for (size_t c0 = 0; c0 < idx.size(); c0 += 32768) {
+    const int cnt = (int)std::min<size_t>(32768, idx.size() - c0);
+    LargeBuffers* b = nullptr;
+    s = large_buffers(p, G, cnt, &b);
+    if (s != FIF_OK) return s;
+    std::vector<LgSig> h(cnt);
+    const size_t Nc = (size_t)G.S.Nc, P = (size_t)G.S.P;
+    for (int q = 0; q < cnt; q++) {
+      const int i = idx[c0 + q];
+      LgSig& g = h[q];
+      g.x = signals + (single ? 0 : offsets[i]);
+      g.out = imfs + (single ? 0 : out_offsets[i]);
+      g.m = m + (single ? 0 : (size_t)i * K);
+      g.mask_len = mask_len + (single ? 0 : (size_t)i * K);
+      g.n_imfs = n_imfs + (single ? 0 : i);
+      g.status = sig_status + (single ? 0 : i);
+      g.diag = diag ? diag + (single ? 0 : (size_t)i * (K + 1)) : nullptr;
+      g.za = b->za + Nc * q;
+      g.zb = b->zb + Nc * q;
+      g.spec = b->spec + (Nc + 1) * q;
+      g.work = b->work + (Nc + 1) * q;
+      g.work2 = b->work2 + (Nc + 1) * q;
+      g.rem = b->rem + (size_t)G.S.n * q;
+      g.row = b->row + P * q;
+      g.st = b->st + 16 * q;
+    }
+    cudaError_t e = cudaMemcpyAsync(b->d_sigs, h.data(), sizeof(LgSig) * cnt,
+                                    cudaMemcpyHostToDevice, p->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->st, 0, 64 * (size_t)cnt, p->stream);
+    if (e == cudaSuccess) e = large_run(G, b->d_sigs, cnt, p->mp, p->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);  // h and the buffers are reused
+    if (e != cudaSuccess) return cuda_status(e);
+  }
   return FIF_OK;
 }
 
@@ -330,6 +561,9 @@ fif_status fif_plan_destroy(fif_plan_t p) {
     cudaFree(kv.second.sin64);
   }
   free_layout(p->layout);
+  for (auto& kv : p->large)
+    for (void* a : kv.second.allocs) cudaFree(a);
+  for (auto& kv : p->large_bufs) free_large_buffers(kv.second);
   cudaFree(p->scr.spec);
   cudaFree(p->scr.work);
   cudaFree(p->scr.rem);
@@ -362,10 +596,17 @@ fif_status fif_decompose(fif_plan_t p, const float* signal, int64_t n, float* im
   if (!p || !signal || !imfs || !n_imfs || !sig_status) return FIF_EINVAL;
   if (p->desc.max_imfs > 0 && (!m || !mask_len)) return FIF_EINVAL;
   if (n < 4 || n > p->desc.max_n) return n < 4 ? FIF_EINVAL : FIF_EUNSUPPORTED;
+  if (!is_smooth(n)) return FIF_EUNSUPPORTED;
+  FftSched probe;
+  if ((p->desc.flags & FIF_FORCE_MULTIPASS) || !make_sched(n, probe, p->smem_optin) ||
+      !staged_fits(probe, p->smem_optin)) {
+    std::vector<int> one(1, 0);
+    return run_large_class(p, n, signal, nullptr, one, imfs, nullptr, m, mask_len, n_imfs,
+                           sig_status, diag, true);
+  }
   LengthTables* t = nullptr;
   fif_status st = get_tables(p, n, &t);
   if (st != FIF_OK) return st;
-  if (!staged_fits(t->sched, p->smem_optin) || t->sched.T > 512) return FIF_EUNSUPPORTED;
   Outputs o{imfs, m, mask_len, n_imfs, sig_status, diag};
   return cuda_status(launch_staged(t->sched, nullptr, p->mp, signal, o, p->scr, p->stream));
 }
@@ -383,10 +624,14 @@ static fif_status check_batch(fif_plan_t p, const float* signals, const int64_t*
     const int64_t n = offsets[i + 1] - offsets[i];
     if (n < 4 || out_offsets[i] < 0) return FIF_EINVAL;
     if (n > p->desc.max_n || !is_smooth(n)) return FIF_EUNSUPPORTED;
-    FftSched s;
-    if (!make_sched(n, s, p->smem_optin) || !fused_fits(s, p->smem_optin)) return FIF_EUNSUPPORTED;
   }
   return FIF_OK;
+}
+
+bool fits_fused(fif_plan_t p, int64_t n) {
+  if (p->desc.flags & FIF_FORCE_MULTIPASS) return false;
+  FftSched s;
+  return make_sched(n, s, p->smem_optin) && fused_fits(s, p->smem_optin);
 }
 
 fif_status fif_decompose_batch(fif_plan_t p, const float* signals, const int64_t* offsets,
@@ -396,15 +641,32 @@ fif_status fif_decompose_batch(fif_plan_t p, const float* signals, const int64_t
   fif_status st = check_batch(p, signals, offsets, batch, imfs, out_offsets, m, mask_len, n_imfs,
                               sig_status);
   if (st != FIF_OK || batch == 0) return st;
-  st = prepare_layout(p, offsets, out_offsets, batch);
-  if (st != FIF_OK) return st;
-  Outputs o{imfs, m, mask_len, n_imfs, sig_status, diag};
-  const BatchLayout& l = p->layout;
-  for (size_t c = 0; c < l.classes.size(); c++) {
-    const auto& cl = l.classes[c];
-    cudaError_t e = launch_fused(cl.E, l.d_sigs + cl.first, cl.count, l.d_scheds, cl.smem, cl.threads,
-                                 cl.grid, p->mp, signals, o, l.d_counters + c, p->stream);
-    if (e != cudaSuccess) return cuda_status(e);
+  std::vector<int> fused;
+  std::map<int64_t, std::vector<int>> large;
+  for (int64_t i = 0; i < batch; i++) {
+    const int64_t n = offsets[i + 1] - offsets[i];
+    if (fits_fused(p, n))
+      fused.push_back((int)i);
+    else
+      large[n].push_back((int)i);
+  }
+  if (!fused.empty()) {
+    st = prepare_layout(p, offsets, out_offsets, batch, fused);
+    if (st != FIF_OK) return st;
+    Outputs o{imfs, m, mask_len, n_imfs, sig_status, diag};
+    const BatchLayout& l = p->layout;
+    for (size_t c = 0; c < l.classes.size(); c++) {
+      const auto& cl = l.classes[c];
+      cudaError_t e = launch_fused(cl.E, l.d_sigs + cl.first, cl.count, l.d_scheds, cl.smem,
+                                   cl.threads, cl.grid, p->mp, signals, o, l.d_counters + c,
+                                   p->stream);
+      if (e != cudaSuccess) return cuda_status(e);
+    }
+  }
+  for (auto& kv : large) {
+    st = run_large_class(p, kv.first, signals, offsets, kv.second, imfs, out_offsets, m, mask_len,
+                         n_imfs, sig_status, diag, false);
+    if (st != FIF_OK) return st;
   }
   return FIF_OK;
 }

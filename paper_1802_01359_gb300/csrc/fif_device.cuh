@@ -323,9 +323,8 @@ struct TwArg<ffc> {
 // transformed, and stored at (j - j mod Ns) R + j mod Ns + r Ns.
 template <class Cx, bool INV, int R, int E>
 __device__ __forceinline__ void fft_pass(Cx* buf, const FftSched& S,
-                                         const typename TwArg<Cx>::type& tws, int Ns) {
+                                         const typename TwArg<Cx>::type& tws, int Ns, int tid) {
   constexpr int NB = E / R;
-  const int tid = threadIdx.x;
   const int T = S.T;
   const int stride = S.Nc / R;
   const bool active = tid < T;
@@ -360,15 +359,16 @@ __device__ __forceinline__ void fft_pass(Cx* buf, const FftSched& S,
 // register needs do not add to the main loop's.
 template <class Cx, bool INV, int E>
 __device__ __noinline__ void fft_tail_pass(Cx* buf, const FftSched& S,
-                                           const typename TwArg<Cx>::type& tws, int Ns, int R) {
+                                           const typename TwArg<Cx>::type& tws, int Ns, int R,
+                                           int tid) {
   if constexpr (E % 8 == 0) {
-    if (R == 8) fft_pass<Cx, INV, 8, E>(buf, S, tws, Ns);
+    if (R == 8) fft_pass<Cx, INV, 8, E>(buf, S, tws, Ns, tid);
   }
   if constexpr (E % 4 == 0) {
-    if (R == 4) fft_pass<Cx, INV, 4, E>(buf, S, tws, Ns);
+    if (R == 4) fft_pass<Cx, INV, 4, E>(buf, S, tws, Ns, tid);
   }
   if constexpr (E % 2 == 0) {
-    if (R == 2) fft_pass<Cx, INV, 2, E>(buf, S, tws, Ns);
+    if (R == 2) fft_pass<Cx, INV, 2, E>(buf, S, tws, Ns, tid);
   }
 }
 
@@ -380,20 +380,23 @@ __host__ __device__ constexpr int main_radix() {
 // Complex FFT of S.Nc points in buf (unnormalised).  Forward: exp(-2 pi i jk/Nc).
 // Every radix of the schedule divides E; all but at most one pass use the
 // main radix (largest power of two dividing E, at most 16) or radix 3.
+// tid is the thread's index among the S.T threads of this transform (several
+// independent transforms may share a CTA); every thread of the CTA calls it.
 template <class Cx, bool INV, int E>
 __device__ __forceinline__ void fft_inplace(Cx* buf, const FftSched& S,
-                                            const typename TwArg<Cx>::type& tws) {
+                                            const typename TwArg<Cx>::type& tws,
+                                            int tid = threadIdx.x) {
   constexpr int RM = main_radix<E>();
   int Ns = 1;
 #pragma unroll 1
   for (int p = 0; p < S.npass; p++) {
     const int R = S.radix[p];
     if (R == RM) {
-      fft_pass<Cx, INV, RM, E>(buf, S, tws, Ns);
+      fft_pass<Cx, INV, RM, E>(buf, S, tws, Ns, tid);
     } else if (E % 3 == 0 && R == 3) {
-      if constexpr (E % 3 == 0 && RM != 3) fft_pass<Cx, INV, 3, E>(buf, S, tws, Ns);
+      if constexpr (E % 3 == 0 && RM != 3) fft_pass<Cx, INV, 3, E>(buf, S, tws, Ns, tid);
     } else {
-      fft_tail_pass<Cx, INV, E>(buf, S, tws, Ns, R);
+      fft_tail_pass<Cx, INV, E>(buf, S, tws, Ns, R, tid);
     }
     Ns *= R;
   }
@@ -752,6 +755,36 @@ static __device__ bool sd_below_first(const float2* spec, const FftSched& S, con
 static __device__ int select_m(const float2* spec, const FftSched& S, int L, const MethodParams& mp,
                                float sc, int& flags, RedScratch* red) {
   const float2* row = wrow(S, L);
+  MSelState st;
+  st.sc = sc;
+  st.hlmax = 0.f;
+  st.flags = 0;
+  int m;
+  const int jmax = mp.max_inner;
+  if (!sd_below_first(spec, S, row, L, jmax, mp, st, red)) {
+    m = jmax;
+    st.flags |= FIF_FLAG_MAX_INNER_HIT;
+  } else {
+    int lo = 0, hi = jmax;
+    while (hi - lo > 1) {
+      const int mid = lo + (hi - lo) / 2;
+      if (sd_below(spec, S, row, L, mid, mp, st, red))
+        hi = mid;
+      else
+        lo = mid;
+    }
+    m = hi;
+  }
+  flags |= st.flags;
+  return m;
+}
+
+// select_m on an explicit window row (row[k] = {log2(1 - w_hat_k), w_hat_k} for
+// the current L), for paths that compute the row per IMF instead of keeping
+// the whole table.
+static __device__ int select_m_on_row(const float2* spec, const FftSched& S, const float2* row,
+                                      int L, const MethodParams& mp, float sc, int& flags,
+                                      RedScratch* red) {
   MSelState st;
   st.sc = sc;
   st.hlmax = 0.f;

@@ -87,6 +87,50 @@ inline int sched_threads(const FftSched& s) {
   return (t + 31) & ~31;
 }
 
+// ---- large-signal path (fif_large.cu) ----
+// The complex FFT of Nc = R1 R2 points runs as two passes through global
+// memory, each a set of shared-memory sub-FFTs of R1 (then R2) points.
+struct LgSched {
+  FftSched S;             // the signal length: n, Nc, odd, P, Lmax, tw/tw_lo over n, sin64
+  FftSched S1, S2;        // complex sub-FFTs of R1 and R2 points (n = Nc = R)
+  int R1, R2;
+  int TJ1, TJ2;           // sub-FFTs per CTA in the FP32 passes
+  int TJF1, TJF2;         // sub-FFTs per CTA in the float-float passes
+  int B;                  // W^m = thi[m / B] * tlo[m % B], W = exp(-2 pi i / Nc)
+  const float2* thi;
+  const float2* thi_lo;
+  const float2* tlo;
+  const float2* tlo_lo;
+  const float2* sinff;    // {hi, lo} of sin(pi t/n), t = 0..n/2
+  const float2* rcpff;    // {hi, lo} of 1/sin(pi k/n), k = 1..n/2 (entry 0 unused)
+};
+
+// One signal of a large-length class; za/zb hold float-float complex points
+// (16 bytes each) during the forward transform.
+struct LgSig {
+  const float* x;
+  float* out;
+  int32_t* m;
+  int32_t* mask_len;
+  int32_t* n_imfs;
+  int32_t* status;
+  fif_imf_diag* diag;
+  float4* za;
+  float4* zb;
+  float2* spec;
+  float2* work;
+  float2* work2;
+  float* rem;
+  float2* row;
+  int* st;                // 16 state words, zeroed before each run
+};
+
+cudaError_t large_build_tables(const LgSched& G, float2* thi, float2* thi_lo, float2* tlo,
+                               float2* tlo_lo, float2* sinff, float2* rcpff, cudaStream_t st);
+cudaError_t large_run(const LgSched& G, const LgSig* d_sigs, int nsig, const MethodParams& mp,
+                      cudaStream_t st);
+size_t large_level_smem(const LgSched& G, int level, bool ff);
+
 // Kernel launchers (fif_fused.cu, fif_staged.cu, fif_tables.cu).
 cudaError_t launch_fused(int E, const SigDesc* d_sigs, int nsig, const FftSched* d_scheds,
                          int smem_bytes, int threads, int grid, const MethodParams& mp,
@@ -106,5 +150,6 @@ cudaError_t launch_staged(const FftSched& s, const FftSched* d_sched, const Meth
 
 cudaError_t build_tables(int n, int P, int Lmax, float2* tw, float2* tw_lo, float2* wtab,
                          double* sin64, cudaStream_t st);
+cudaError_t build_twiddles(int n, float2* tw, float2* tw_lo, double* sin64, cudaStream_t st);
 
 }  // namespace fif

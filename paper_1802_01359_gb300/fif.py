@@ -34,6 +34,7 @@ FLAG_MAX_INNER_HIT = 1 << 10
 FLAG_FP64_TIEBREAK = 1 << 11
 FLAG_L_CLAMPED = 1 << 12
 FORCE_L = 1
+FORCE_MULTIPASS = 2
 
 # every symbol include/fif.h declares
 EXPORTS = ("fif_plan_create", "fif_plan_destroy", "fif_plan_set_stream", "fif_plan_prepare",
@@ -172,14 +173,14 @@ class Plan:
 
     def __init__(self, *, nu: float = 1.6, mask_scale: int = 1, delta: float = 1e-3,
                  max_inner: int = 200, max_imfs: int = 10, max_n: int = 16384,
-                 force_L: bool = False, stream=None):
+                 force_L: bool = False, multipass: bool = False, stream=None):
         import torch
         lib = load_library()
         self.max_imfs = max_imfs
         self.max_n = max_n
         self.force_L = force_L
         self.desc = PlanDesc(0, nu, mask_scale, delta, max_inner, max_imfs, 0, max_n,
-                             FORCE_L if force_L else 0)
+                             (FORCE_L if force_L else 0) | (FORCE_MULTIPASS if multipass else 0))
         if stream is None:
             stream = torch.cuda.current_stream()
         self._stream = stream

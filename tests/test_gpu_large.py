@@ -1,0 +1,112 @@
+"""GPU parity of the multi-pass path (FFTs through global memory) used for long signals."""
+import numpy as np
+import pytest
+
+import parity
+from paper_1802_01359_gb300 import fif, signals
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def dev():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1802_01359_gb300 import build
+    build.build()
+    return torch.device("cuda:0")
+
+
+def _pack(sigs, dev):
+    lens = np.array([s.size for s in sigs], dtype=np.int64)
+    offs = np.zeros(lens.size + 1, dtype=np.int64)
+    offs[1:] = np.cumsum(lens)
+    return torch.from_numpy(np.concatenate(sigs).astype(np.float32)).to(dev), offs
+
+
+MP_LENGTHS = [8, 12, 18, 27, 64, 96, 243, 256, 729, 1024, 1536, 2187, 4096, 6144, 6561, 16384]
+
+
+def test_multipass_forced_small_lengths_match_oracle(dev, oracle_mod):
+    sigs = [signals.component_signal(70, i, n) for i, n in enumerate(MP_LENGTHS)]
+    x, offs = _pack(sigs, dev)
+    with fif.Plan(max_n=16384, max_imfs=5, multipass=True) as plan:
+        res = plan.decompose_batch(x, offs, diag=True)
+        torch.cuda.synchronize()
+    for i, s in enumerate(sigs):
+        ref = oracle_mod.direct(s.astype(np.float64), max_imfs=5)
+        parity.compare(res.signal(i), ref)
+
+
+def test_multipass_and_fused_agree(dev):
+    sigs = [signals.component_signal(71, i, n) for i, n in enumerate([2048, 4096, 12288, 16384])]
+    x, offs = _pack(sigs, dev)
+    with fif.Plan(max_n=16384) as a, fif.Plan(max_n=16384, multipass=True) as b:
+        ra = a.decompose_batch(x, offs, diag=True)
+        rb = b.decompose_batch(x, offs, diag=True)
+        torch.cuda.synchronize()
+    for i in range(len(sigs)):
+        da, db = ra.signal(i), rb.signal(i)
+        assert da.n_imfs == db.n_imfs and da.status == db.status
+        K = da.n_imfs
+        assert np.array_equal(da.m.cpu().numpy()[:K], db.m.cpu().numpy()[:K])
+        assert np.array_equal(da.mask_len.cpu().numpy()[:K], db.mask_len.cpu().numpy()[:K])
+        A = da.imfs.cpu().numpy().astype(np.float64)
+        B = db.imfs.cpu().numpy().astype(np.float64)
+        for k in range(K + 1):
+            assert parity.rel_l2(B[k], A[k]) < 2 * parity.IMF_TOL
+
+
+LONG = [20736, 32768, 39366, 59049, 65536, 131072]
+
+
+def test_long_lengths_match_oracle(dev, oracle_mod):
+    sigs = [signals.component_signal(72, i, n) for i, n in enumerate(LONG)]
+    x, offs = _pack(sigs, dev)
+    with fif.Plan(max_n=1 << 17, max_imfs=4) as plan:
+        res = plan.decompose_batch(x, offs, diag=True)
+        torch.cuda.synchronize()
+    for i, s in enumerate(sigs):
+        ref = oracle_mod.direct(s.astype(np.float64), max_imfs=4)
+        parity.compare(res.signal(i), ref)
+
+
+def test_mixed_short_and_long_batch(dev, oracle_mod):
+    lens = [4096, 24576, 729, 20736, 16384, 46656]
+    sigs = [signals.component_signal(73, i, n) for i, n in enumerate(lens)]
+    x, offs = _pack(sigs, dev)
+    with fif.Plan(max_n=1 << 16, max_imfs=3) as plan:
+        res = plan.decompose_batch(x, offs, diag=True)
+        torch.cuda.synchronize()
+    for i, s in enumerate(sigs):
+        ref = oracle_mod.direct(s.astype(np.float64), max_imfs=3)
+        parity.compare(res.signal(i), ref)
+
+
+def test_single_signal_entry_long(dev, oracle_mod):
+    n = 1 << 18
+    s = signals.component_signal(74, 0, n)
+    with fif.Plan(max_n=n, max_imfs=2) as plan:
+        d = plan.decompose(torch.from_numpy(s).to(dev), diag=True)
+    ref = oracle_mod.direct(s.astype(np.float64), max_imfs=2)
+    parity.compare(d, ref)
+    # sum of IMFs and remainder reconstructs the input
+    imfs = d.imfs.cpu().numpy().astype(np.float64)
+    rec = imfs[:d.n_imfs + 1].sum(0)
+    assert np.abs(rec - s).max() < 1e-5 * np.abs(s).max()
+
+
+def test_long_degenerate_inputs(dev):
+    n = 32768
+    z = np.zeros(n, np.float32)
+    nanv = np.ones(n, np.float32)
+    nanv[1234] = np.nan
+    x, offs = _pack([z, nanv], dev)
+    with fif.Plan(max_n=n) as plan:
+        res = plan.decompose_batch(x, offs)
+        torch.cuda.synchronize()
+    assert res.signal(0).stop == fif.STOP_EXTREMA and res.signal(0).n_imfs == 0
+    assert res.signal(1).stop == fif.STOP_NONFINITE and res.signal(1).n_imfs == 0
+    assert np.array_equal(res.signal(1).imfs[0].cpu().numpy(), nanv, equal_nan=True)
