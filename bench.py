@@ -40,6 +40,73 @@ BATCH, N = 1024, 16384
 PARAMS = dict(nu=1.6, mask_scale=1, delta=1e-3, max_inner=200, max_imfs=10)
 WORKLOAD = (f"batch of {BATCH} float32 signals, n={N}, 2-5 chirped AM components + N(0,0.01^2) "
             "noise; triangle window, nu=1.6, delta=1e-3, max_inner=200, max_imfs=10")
+
+# Other synthetic workloads (not the default line): name -> description, generator args
+WORKLOADS = {
+    "batch16384": dict(desc=WORKLOAD),
+    "single4096": dict(desc="one n=4096 three-component test signal (noise from default_rng(0)); "
+                            "delta=1e-3, max_inner=200, max_imfs=10"),
+    "uneven": dict(desc="4096 float32 signals, n log-uniform in [256, 2^20] rounded to 2^a 3^b, "
+                        "2-5 chirped AM components + noise; delta=1e-3, max_imfs=10"),
+    "long": dict(desc="one float32 signal, n=2^24, 6 components f0=10^{0..6}, noise 1e-3; "
+                      "delta=1e-3, max_imfs=10"),
+    "batch4096": dict(desc="65536 float32 signals, n=4096, 2-5 chirped AM components + noise; "
+                           "delta=1e-3, max_imfs=12"),
+    "batch4096_d1e-4": dict(desc="65536 float32 signals, n=4096, as batch4096 with delta=1e-4"),
+}
+
+
+def _gen_chunk(args):
+    wid, first, lens = args
+    sys.path.insert(0, ROOT)
+    from paper_1802_01359_gb300 import signals
+    return [signals.component_signal(wid, first + i, int(n)) for i, n in enumerate(lens)]
+
+
+def generate(wid, lens, first=0):
+    """Signals first.. of workload wid with the given lengths, generated on a spawn process
+    pool (started before any CUDA call).  Returns (float32 data, int64 offsets)."""
+    import multiprocessing as mp
+    lens = np.asarray(lens, dtype=np.int64)
+    offs = np.zeros(lens.size + 1, dtype=np.int64)
+    offs[1:] = np.cumsum(lens)
+    data = np.empty(int(offs[-1]), dtype=np.float32)
+    chunk = max(1, lens.size // 64)
+    jobs = [(wid, first + a, lens[a:a + chunk]) for a in range(0, lens.size, chunk)]
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    procs = max(1, min(16, (os.cpu_count() or 1) // max(world, 1)))
+    with mp.get_context("spawn").Pool(procs) as pool:
+        pos = 0
+        for part in pool.map(_gen_chunk, jobs):
+            for s in part:
+                data[pos:pos + s.size] = s
+                pos += s.size
+    return data, offs
+
+
+def make_workload(name, rank=0):
+    """(data, offsets, params) of a named workload."""
+    from paper_1802_01359_gb300 import signals
+    params = dict(PARAMS)
+    if name == "batch16384":
+        data, offs = generate(signals.W_BATCH_16384, np.full(BATCH, N), first=rank * BATCH)
+    elif name == "single4096":
+        s = signals.single_4096()
+        data, offs = s, np.array([0, s.size], dtype=np.int64)
+    elif name == "uneven":
+        lens = signals.uneven_lengths(4096)
+        data, offs = generate(signals.W_UNEVEN, lens)
+    elif name == "long":
+        s = signals.long_signal()
+        data, offs = s, np.array([0, s.size], dtype=np.int64)
+    elif name in ("batch4096", "batch4096_d1e-4"):
+        data, offs = generate(signals.W_BATCH_4096, np.full(65536, 4096))
+        params["max_imfs"] = 12
+        if name == "batch4096_d1e-4":
+            params["delta"] = 1e-4
+    else:
+        raise SystemExit(f"unknown workload {name}")
+    return data, offs, params
 L2_FLUSH_BYTES = 512 << 20
 FUSED_SOURCES = ("paper_1802_01359_gb300/csrc/fif_device.cuh",
                  "paper_1802_01359_gb300/csrc/fif_fused.cu",
@@ -132,7 +199,7 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def oracle_sample(data, offs, idx, threads):
+def oracle_sample(data, offs, idx, threads, params=None):
     """The FP64 oracle (direct method, tier B) on signals idx, one signal per task on a
     thread pool (the C oracle releases the GIL).  Returns (results, seconds)."""
     import concurrent.futures as cf
@@ -140,8 +207,10 @@ def oracle_sample(data, offs, idx, threads):
     import oracle
     oracle.build()
 
+    prm = params or PARAMS
+
     def one(i):
-        return oracle.direct(data[offs[i]:offs[i + 1]].astype(np.float64), **PARAMS)
+        return oracle.direct(data[offs[i]:offs[i + 1]].astype(np.float64), **prm)
 
     t0 = time.perf_counter()
     with cf.ThreadPoolExecutor(max_workers=threads) as ex:
@@ -215,43 +284,51 @@ def main():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="fif")
+    ap.add_argument("--workload", default="batch16384", choices=sorted(WORKLOADS))
     ap.add_argument("--cpu-sample", type=int, default=48)
     ap.add_argument("--plain-signals", type=int, default=64)
+    ap.add_argument("--no-e2e", action="store_true")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", str(args.gpus)))
     local = int(os.environ.get("LOCAL_RANK", "0"))
-    dist = None
-    if world > 1 and "RANK" in os.environ:
-        import torch.distributed as dist
-        import torch
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl")
 
     if args.impl == "reference":
+        dist = None
+        if world > 1 and "RANK" in os.environ:
+            import torch.distributed as dist
+            dist.init_process_group("gloo")
         run_reference(args, rank, world)
         if dist is not None:
             dist.barrier()
             dist.destroy_process_group()
         return
 
-    import torch
+    # inputs first: the generator pool is spawned before any CUDA call
+    data, offs, params = make_workload(args.workload, rank)
+    lens = np.diff(offs)
+    nsig = lens.size
 
-    from paper_1802_01359_gb300 import build, fif, signals
+    dist = None
+    import torch
+    if world > 1 and "RANK" in os.environ:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+
+    from paper_1802_01359_gb300 import build, fif
     build.build()
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
 
-    # weak scaling: every rank decomposes its own batch of the workload
-    data, offs = signals.batch(signals.W_BATCH_16384, BATCH, N, first=rank * BATCH)
     x = torch.from_numpy(data).to(dev)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.Stream(dev)
-    plan = fif.Plan(max_n=N, stream=stream, **PARAMS)
-    plan.prepare([N])
-    out = plan.alloc_batch_outputs(np.diff(offs), dev)
+    plan = fif.Plan(max_n=int(lens.max()), stream=stream, **params)
+    plan.prepare(sorted(set(int(v) for v in lens)))
+    out = plan.alloc_batch_outputs(lens, dev)
 
     def step():
         plan.decompose_batch(x, offs, out=out)
@@ -286,80 +363,86 @@ def main():
     samples_per_step = int(offs[-1]) * world
     value = samples_per_step * args.steps / t_total
 
-    # ---- algorithmic bytes of one launch: read s, write K_i IMFs + remainder, ints
+    # ---- algorithmic bytes of one step: read s, write K_i IMFs + remainder, ints
     nim = out.n_imfs.cpu().numpy().astype(np.int64)
-    lens = np.diff(offs)
-    alg_bytes = int((4 * lens + 4 * lens * (nim + 1)).sum() + BATCH * (8 * PARAMS["max_imfs"] + 8))
+    K = params["max_imfs"]
+    alg_bytes = int((4 * lens + 4 * lens * (nim + 1)).sum() + nsig * (8 * K + 8))
     kern_s = statistics.mean(step_ms) / 1e3
     peak, peak_kind = peaks()
     achieved = alg_bytes / kern_s / 1e9
-    traffic = recorded_traffic(BATCH)
+    fused_only = args.workload.startswith("batch") or args.workload == "single4096"
+    traffic = recorded_traffic(nsig) if args.workload == "batch16384" else None
 
+    desc = WORKLOADS[args.workload]["desc"]
     result = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * t_total / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD, "batch": BATCH, "n": N, "path": "fused batch (one CTA "
-                   "per signal, shared-memory resident)", "l2": "flushed between steps "
-                   f"({L2_FLUSH_BYTES >> 20} MiB write); inputs 64 MiB, outputs > L2",
+        "config": {"workload": desc, "name": args.workload, "signals": nsig,
+                   "samples": int(offs[-1]),
+                   "path": "fused batch (one CTA per signal, shared-memory resident)" if fused_only
+                   else "batch: fused for short signals, multi-pass for long ones, one CUDA graph",
+                   "l2": f"flushed between steps ({L2_FLUSH_BYTES >> 20} MiB write)",
                    "mean_imfs": float(nim.mean())},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
                      "peak_kind": f"{peak_kind} HBM copy bandwidth",
-                     "kernel": "fused_kernel<16>", "alg_bytes_per_launch": alg_bytes},
+                     "kernel": "fused_kernel<16>" if args.workload == "batch16384" else "whole step",
+                     "alg_bytes_per_launch": alg_bytes},
         "gpu_launches": args.steps,
         "clocks": clk.summary(),
     }
 
     # ---- e2e through the host-buffer C entry point (pinned host memory)
-    K1 = PARAMS["max_imfs"] + 1
-    h_in = torch.from_numpy(data).pin_memory().numpy()
-    h_out = dict(imfs=torch.empty(int(offs[-1]) * K1, dtype=torch.float32).pin_memory().numpy(),
-                 m=np.zeros((BATCH, K1 - 1), np.int32), mask_len=np.zeros((BATCH, K1 - 1), np.int32),
-                 n_imfs=np.zeros(BATCH, np.int32), status=np.zeros(BATCH, np.int32), diag=None)
-    for _ in range(2):
-        plan.decompose_batch_host(h_in, offs, out=h_out)
-    if dist is not None:
-        dist.barrier()
-    e2e_steps = max(3, min(args.steps, 5))
-    t0 = time.perf_counter()
-    for _ in range(e2e_steps):
-        plan.decompose_batch_host(h_in, offs, out=h_out)
-    te = time.perf_counter() - t0
-    if dist is not None:
-        tt = torch.tensor([te], dtype=torch.float64, device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        te = float(tt.item())
-    result["e2e"] = {"value": samples_per_step * e2e_steps / te, "unit": UNIT,
-                     "h2d_bytes_per_step": int(h_in.nbytes),
-                     "d2h_bytes_per_step": int(h_out["imfs"].nbytes + 4 * BATCH * (2 * (K1 - 1) + 2))}
+    if not args.no_e2e:
+        K1 = K + 1
+        h_in = torch.from_numpy(data).pin_memory().numpy()
+        h_out = dict(imfs=torch.empty(int(offs[-1]) * K1, dtype=torch.float32).pin_memory().numpy(),
+                     m=np.zeros((nsig, K), np.int32), mask_len=np.zeros((nsig, K), np.int32),
+                     n_imfs=np.zeros(nsig, np.int32), status=np.zeros(nsig, np.int32), diag=None)
+        for _ in range(2):
+            plan.decompose_batch_host(h_in, offs, out=h_out)
+        if dist is not None:
+            dist.barrier()
+        e2e_steps = max(3, min(args.steps, 5))
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            plan.decompose_batch_host(h_in, offs, out=h_out)
+        te = time.perf_counter() - t0
+        if dist is not None:
+            tt = torch.tensor([te], dtype=torch.float64, device=dev)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            te = float(tt.item())
+        result["e2e"] = {"value": samples_per_step * e2e_steps / te, "unit": UNIT,
+                         "h2d_bytes_per_step": int(h_in.nbytes),
+                         "d2h_bytes_per_step": int(h_out["imfs"].nbytes + 4 * nsig * (2 * K + 2))}
 
     # ---- plain staged path (one launch per step of the method) on a subset
-    if rank == 0 and args.plain_signals > 0:
-        P = min(args.plain_signals, BATCH)
+    if rank == 0 and args.plain_signals > 0 and fused_only:
+        P = min(args.plain_signals, nsig)
+        n0 = int(lens[0])
         with torch.cuda.stream(stream):
-            plan_out = plan.decompose(x[:N])            # warm
+            plan.decompose(x[:n0])            # warm
         stream.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         views = [x[int(offs[i]):int(offs[i + 1])] for i in range(P)]
         lib = fif.load_library()
-        K = PARAMS["max_imfs"]
-        imfs = torch.empty((K + 1) * N, dtype=torch.float32, device=dev)
-        mm = torch.empty(K, dtype=torch.int32, device=dev)
-        LL = torch.empty(K, dtype=torch.int32, device=dev)
+        imfs = torch.empty((K + 1) * n0, dtype=torch.float32, device=dev)
+        mm = torch.empty(max(K, 1), dtype=torch.int32, device=dev)
+        LL = torch.empty(max(K, 1), dtype=torch.int32, device=dev)
         ni = torch.empty(1, dtype=torch.int32, device=dev)
         ss = torch.empty(1, dtype=torch.int32, device=dev)
         torch.cuda.synchronize()
         e0.record(stream)
         for v in views:
-            rc = lib.fif_decompose(plan.handle, v.data_ptr(), N, imfs.data_ptr(), mm.data_ptr(),
+            rc = lib.fif_decompose(plan.handle, v.data_ptr(), n0, imfs.data_ptr(), mm.data_ptr(),
                                    LL.data_ptr(), ni.data_ptr(), ss.data_ptr(), None)
             assert rc == 0, fif.status_string(rc)
         e1.record(stream)
         torch.cuda.synchronize()
         tp = e0.elapsed_time(e1) / 1e3
-        result["plain"] = {"value": P * N / tp, "unit": UNIT, "signals_timed": P,
+        result["plain"] = {"value": P * n0 / tp, "unit": UNIT, "signals_timed": P,
                            "launches_per_signal": 1 + 3 * (K + 1),
                            "path": "staged, one kernel launch per step per outer iteration"}
         result["batched_over_plain"] = value / world / result["plain"]["value"]
@@ -368,12 +451,22 @@ def main():
     if rank == 0 and world == 1 and args.cpu_sample > 0:
         threads = os.cpu_count() or 1
         rng = np.random.default_rng(12345)
-        idx = sorted(rng.choice(BATCH, size=min(args.cpu_sample, BATCH), replace=False).tolist())
-        refs, tc = oracle_sample(data, offs, idx, threads)
-        result["cpu_baseline"] = {"value": len(idx) * N / tc, "unit": UNIT, "cores": threads,
+        # a bounded sample: about 30 s of oracle work on the machine's cores
+        order = rng.permutation(nsig)
+        budget = 16 * threads * 16384 if args.workload != "long" else 1 << 24
+        idx, tot = [], 0
+        for i in order[:max(args.cpu_sample, 1)]:
+            if tot + lens[i] > budget and idx:
+                continue
+            idx.append(int(i))
+            tot += int(lens[i])
+        idx.sort()
+        refs, tc = oracle_sample(data, offs, idx, threads, params)
+        result["cpu_baseline"] = {"value": tot / tc, "unit": UNIT, "cores": min(threads, len(idx)),
                                   "kind": "oracle",
-                                  "sample": f"{len(idx)} random signals of the workload, FP64 "
-                                            "direct method (tier B), one signal per thread"}
+                                  "sample": f"{len(idx)} random signals of the workload "
+                                            f"({tot} samples), FP64 direct method (tier B), one "
+                                            "signal per thread"}
         result["parity"] = parity_summary(out, refs, idx)
 
     plan.close()

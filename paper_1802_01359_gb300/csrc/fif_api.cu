@@ -11,6 +11,9 @@
 
 using namespace fif;
 
+struct LargeTables;
+struct LargeBuffers;
+
 namespace {
 
 struct LengthTables {
@@ -23,6 +26,16 @@ struct LengthTables {
 
 struct BatchLayout {
   std::vector<int64_t> offsets, out_offsets;
+  struct LargeCls {
+    int64_t n;
+    int count;
+    LargeTables* lt;
+    LargeBuffers* b;
+  };
+  std::vector<LargeCls> lcls;
+  // CUDA graph of the whole call, valid for the pointers in key
+  cudaGraphExec_t exec = nullptr;
+  const void* key[8] = {nullptr};
   // classes: contiguous ranges of the sorted signal list sharing one length
   struct Cls {
     int first, count, smem, threads, grid, E;
@@ -71,7 +84,13 @@ struct fif_plan_s {
   size_t h2d_cap = 0;
   // large-length path
   std::map<int64_t, LargeTables> large;
-  std::map<int64_t, LargeBuffers> large_bufs;
+  std::map<int64_t, LargeBuffers> large_bufs;         // per length, batch layouts
+  std::map<int64_t, LargeBuffers> large_single_bufs;  // per length, fif_decompose
+  // branches of the batch graph: one per length class, round robin
+  static constexpr int kBranches = 8;
+  cudaStream_t aux[kBranches] = {nullptr};
+  cudaEvent_t ev_fork = nullptr;
+  cudaEvent_t ev_join[kBranches] = {nullptr};
 };
 
 namespace {
@@ -195,6 +214,7 @@ fif_status get_tables(fif_plan_t p, int64_t n, LengthTables** out) {
 }
 
 void free_layout(BatchLayout& l) {
+  if (l.exec) cudaGraphExecDestroy(l.exec);
   cudaFree(l.d_sigs);
   cudaFree(l.d_scheds);
   cudaFree(l.d_counters);
@@ -222,10 +242,6 @@ fif_status validate_desc(const fif_plan_desc* d) {
 fif_status prepare_layout(fif_plan_t p, const int64_t* offsets, const int64_t* out_offsets,
                           int64_t batch, const std::vector<int>& subset) {
   BatchLayout& l = p->layout;
-  if (p->layout_valid && (int64_t)l.out_offsets.size() == batch &&
-      std::equal(l.offsets.begin(), l.offsets.end(), offsets) &&
-      std::equal(l.out_offsets.begin(), l.out_offsets.end(), out_offsets))
-    return FIF_OK;
   free_layout(l);
   p->layout_valid = false;
   std::vector<int> order(subset);
@@ -389,6 +405,7 @@ fif_status get_large(fif_plan_t p, int64_t n, LargeTables** out) {
   G.sinff = sff;
   G.rcpff = rff;
   if (e == cudaSuccess) e = large_build_tables(G, thi, thil, tlo, tlol, sff, rff, p->stream);
+  if (e == cudaSuccess) e = large_set_attrs(G);
   if (e != cudaSuccess) {
     for (void* a : lt.allocs) cudaFree(a);
     cudaGetLastError();
@@ -405,8 +422,9 @@ void free_large_buffers(LargeBuffers& b) {
 }
 
 // Working arrays of one large class for nsig signals (grow-only, per length).
-fif_status large_buffers(fif_plan_t p, const LgSched& G, int nsig, LargeBuffers** out) {
-  LargeBuffers& b = p->large_bufs[G.S.n];
+fif_status large_buffers(fif_plan_t p, const LgSched& G, int nsig, LargeBuffers** out,
+                         bool single = false) {
+  LargeBuffers& b = single ? p->large_single_bufs[G.S.n] : p->large_bufs[G.S.n];
   if (b.cap >= nsig) {
     *out = &b;
     return FIF_OK;
@@ -441,50 +459,127 @@ fif_status large_buffers(fif_plan_t p, const LgSched& G, int nsig, LargeBuffers*
   return FIF_OK;
 }
 
-// Run the large path for signals idx[0..count) of one length n.
-fif_status run_large_class(fif_plan_t p, int64_t n, const float* signals, const int64_t* offsets,
-                           const std::vector<int>& idx, float* imfs, const int64_t* out_offsets,
-                           int32_t* m, int32_t* mask_len, int32_t* n_imfs, int32_t* sig_status,
-                           fif_imf_diag* diag, bool single) {
+// Fill the descriptors of idx[0..count) (one length) into b->d_sigs (blocking
+// upload) and return the class.
+fif_status upload_large_class(fif_plan_t p, const LgSched& G, LargeBuffers* b,
+                              const int64_t* offsets, const int64_t* out_offsets,
+                              const std::vector<int>& idx) {
+  const int cnt = (int)idx.size();
+  std::vector<LgSig> h(cnt);
+  const size_t Nc = (size_t)G.S.Nc, P = (size_t)G.S.P;
+  for (int q = 0; q < cnt; q++) {
+    const int i = idx[q];
+    LgSig& g = h[q];
+    memset(&g, 0, sizeof(g));
+    g.in_off = offsets ? offsets[i] : 0;
+    g.out_off = out_offsets ? out_offsets[i] : 0;
+    g.idx = i;
+    g.za = b->za + Nc * q;
+    g.zb = b->zb + Nc * q;
+    g.spec = b->spec + (Nc + 1) * q;
+    g.work = b->work + (Nc + 1) * q;
+    g.work2 = b->work2 + (Nc + 1) * q;
+    g.rem = b->rem + (size_t)G.S.n * q;
+    g.row = b->row + P * q;
+    g.st = b->st + 16 * q;
+  }
+  cudaError_t e = cudaMemcpyAsync(b->d_sigs, h.data(), sizeof(LgSig) * cnt,
+                                  cudaMemcpyHostToDevice, p->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
+  return cuda_status(e);
+}
+
+// One signal of length n through the multi-pass path (fif_decompose).
+fif_status run_large_single(fif_plan_t p, int64_t n, const float* signal, const Outputs& o) {
   LargeTables* lt = nullptr;
   fif_status s = get_large(p, n, &lt);
   if (s != FIF_OK) return s;
-  const LgSched& G = lt->G;
-  const int K = p->desc.max_imfs;
-  for (size_t c0 = 0; c0 < idx.size(); c0 += 32768) {
-    const int cnt = (int)std::min<size_t>(32768, idx.size() - c0);
-    LargeBuffers* b = nullptr;
-    s = large_buffers(p, G, cnt, &b);
+  LargeBuffers* b = nullptr;
+  s = large_buffers(p, lt->G, 1, &b, true);
+  if (s != FIF_OK) return s;
+  std::vector<int> one(1, 0);
+  s = upload_large_class(p, lt->G, b, nullptr, nullptr, one);
+  if (s != FIF_OK) return s;
+  cudaError_t e = cudaMemsetAsync(b->st, 0, 64, p->stream);
+  if (e == cudaSuccess) e = large_run(lt->G, b->d_sigs, 1, p->mp, signal, o, p->stream);
+  return cuda_status(e);
+}
+
+// Tables, working arrays and descriptors of the large classes of a fresh
+// layout.
+fif_status prepare_large(fif_plan_t p, const int64_t* offsets, const int64_t* out_offsets,
+                         const std::map<int64_t, std::vector<int>>& groups) {
+  BatchLayout& l = p->layout;
+  l.lcls.clear();
+  for (const auto& kv : groups) {
+    LargeTables* lt = nullptr;
+    fif_status s = get_large(p, kv.first, &lt);
     if (s != FIF_OK) return s;
-    std::vector<LgSig> h(cnt);
-    const size_t Nc = (size_t)G.S.Nc, P = (size_t)G.S.P;
-    for (int q = 0; q < cnt; q++) {
-      const int i = idx[c0 + q];
-      LgSig& g = h[q];
-      g.x = signals + (single ? 0 : offsets[i]);
-      g.out = imfs + (single ? 0 : out_offsets[i]);
-      g.m = m + (single ? 0 : (size_t)i * K);
-      g.mask_len = mask_len + (single ? 0 : (size_t)i * K);
-      g.n_imfs = n_imfs + (single ? 0 : i);
-      g.status = sig_status + (single ? 0 : i);
-      g.diag = diag ? diag + (single ? 0 : (size_t)i * (K + 1)) : nullptr;
-      g.za = b->za + Nc * q;
-      g.zb = b->zb + Nc * q;
-      g.spec = b->spec + (Nc + 1) * q;
-      g.work = b->work + (Nc + 1) * q;
-      g.work2 = b->work2 + (Nc + 1) * q;
-      g.rem = b->rem + (size_t)G.S.n * q;
-      g.row = b->row + P * q;
-      g.st = b->st + 16 * q;
-    }
-    cudaError_t e = cudaMemcpyAsync(b->d_sigs, h.data(), sizeof(LgSig) * cnt,
-                                    cudaMemcpyHostToDevice, p->stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(b->st, 0, 64 * (size_t)cnt, p->stream);
-    if (e == cudaSuccess) e = large_run(G, b->d_sigs, cnt, p->mp, p->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);  // h and the buffers are reused
-    if (e != cudaSuccess) return cuda_status(e);
+    const int cnt = (int)kv.second.size();
+    if (cnt > 65535) return FIF_EUNSUPPORTED;
+    LargeBuffers* b = nullptr;
+    s = large_buffers(p, lt->G, cnt, &b);
+    if (s != FIF_OK) return s;
+    s = upload_large_class(p, lt->G, b, offsets, out_offsets, kv.second);
+    if (s != FIF_OK) return s;
+    l.lcls.push_back(BatchLayout::LargeCls{kv.first, cnt, lt, b});
   }
   return FIF_OK;
+}
+
+// Enqueue every class of the current layout; with more than one class each
+// goes to its own branch stream (fork/join by events), so that independent
+// lengths run side by side (and become parallel branches of a captured graph).
+fif_status enqueue_batch(fif_plan_t p, const float* signals, const Outputs& o) {
+  const BatchLayout& l = p->layout;
+  const int ncls = (int)(l.classes.size() + l.lcls.size());
+  const bool fork = ncls > 1;
+  cudaError_t e = cudaSuccess;
+  if (fork) e = cudaEventRecord(p->ev_fork, p->stream);
+  bool used[fif_plan_s::kBranches] = {false};
+  int bi = 0;
+  auto branch = [&]() -> cudaStream_t {
+    if (!fork) return p->stream;
+    const int a = bi++ % fif_plan_s::kBranches;
+    if (!used[a] && e == cudaSuccess) e = cudaStreamWaitEvent(p->aux[a], p->ev_fork, 0);
+    used[a] = true;
+    return p->aux[a];
+  };
+  for (size_t c = 0; c < l.classes.size() && e == cudaSuccess; c++) {
+    const auto& cl = l.classes[c];
+    cudaStream_t s = branch();
+    if (e == cudaSuccess)
+      e = launch_fused(cl.E, l.d_sigs + cl.first, cl.count, l.d_scheds, cl.smem, cl.threads,
+                       cl.grid, p->mp, signals, o, l.d_counters + c, s);
+  }
+  for (size_t c = 0; c < l.lcls.size() && e == cudaSuccess; c++) {
+    const auto& lc = l.lcls[c];
+    cudaStream_t s = branch();
+    if (e == cudaSuccess) e = cudaMemsetAsync(lc.b->st, 0, 64 * (size_t)lc.count, s);
+    if (e == cudaSuccess) e = large_run(lc.lt->G, lc.b->d_sigs, lc.count, p->mp, signals, o, s);
+  }
+  if (fork) {
+    for (int a = 0; a < fif_plan_s::kBranches && e == cudaSuccess; a++) {
+      if (!used[a]) continue;
+      e = cudaEventRecord(p->ev_join[a], p->aux[a]);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(p->stream, p->ev_join[a], 0);
+    }
+  }
+  return cuda_status(e);
+}
+
+bool fits_fused(fif_plan_t p, int64_t n) {
+  if (p->desc.flags & FIF_FORCE_MULTIPASS) return false;
+  FftSched s;
+  return make_sched(n, s, p->smem_optin) && fused_fits(s, p->smem_optin);
+}
+
+bool layout_matches(fif_plan_t p, const int64_t* offsets, const int64_t* out_offsets,
+                    int64_t batch) {
+  const BatchLayout& l = p->layout;
+  return p->layout_valid && (int64_t)l.out_offsets.size() == batch &&
+         std::equal(l.offsets.begin(), l.offsets.end(), offsets) &&
+         std::equal(l.out_offsets.begin(), l.out_offsets.end(), out_offsets);
 }
 
 }  // namespace
@@ -546,6 +641,16 @@ fif_status fif_plan_create(fif_plan_t* out, const fif_plan_desc* desc, void* cud
     cudaGetLastError();
     return cuda_status(e);
   }
+  for (int a = 0; a < fif_plan_s::kBranches && e == cudaSuccess; a++) {
+    e = cudaStreamCreateWithFlags(&p->aux[a], cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->ev_join[a], cudaEventDisableTiming);
+  }
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming);
+  if (e != cudaSuccess) {
+    fif_plan_destroy(p);
+    cudaGetLastError();
+    return cuda_status(e);
+  }
   p->scr_n = n;
   *out = p;
   return FIF_OK;
@@ -569,6 +674,12 @@ fif_status fif_plan_destroy(fif_plan_t p) {
   cudaFree(p->scr.rem);
   cudaFree(p->scr.state);
   cudaFree(p->h2d_buf);
+  for (int a = 0; a < fif_plan_s::kBranches; a++) {
+    if (p->aux[a]) cudaStreamSynchronize(p->aux[a]);
+    if (p->aux[a]) cudaStreamDestroy(p->aux[a]);
+    if (p->ev_join[a]) cudaEventDestroy(p->ev_join[a]);
+  }
+  if (p->ev_fork) cudaEventDestroy(p->ev_fork);
   delete p;
   return FIF_OK;
 }
@@ -581,10 +692,17 @@ fif_status fif_plan_set_stream(fif_plan_t p, void* cuda_stream) {
 
 fif_status fif_plan_prepare(fif_plan_t p, const int64_t* lengths, int64_t count) {
   if (!p || count < 0 || (count > 0 && !lengths)) return FIF_EINVAL;
+  cudaGetLastError();
   for (int64_t i = 0; i < count; i++) {
-    if (lengths[i] > p->desc.max_n) return FIF_EUNSUPPORTED;
-    LengthTables* t = nullptr;
-    fif_status st = get_tables(p, lengths[i], &t);
+    if (lengths[i] > p->desc.max_n || !is_smooth(lengths[i])) return FIF_EUNSUPPORTED;
+    fif_status st;
+    if (fits_fused(p, lengths[i])) {
+      LengthTables* t = nullptr;
+      st = get_tables(p, lengths[i], &t);
+    } else {
+      LargeTables* lt = nullptr;
+      st = get_large(p, lengths[i], &lt);
+    }
     if (st != FIF_OK) return st;
   }
   return cuda_status(cudaStreamSynchronize(p->stream));
@@ -594,15 +712,15 @@ fif_status fif_decompose(fif_plan_t p, const float* signal, int64_t n, float* im
                          int32_t* mask_len, int32_t* n_imfs, int32_t* sig_status,
                          fif_imf_diag* diag) {
   if (!p || !signal || !imfs || !n_imfs || !sig_status) return FIF_EINVAL;
+  cudaGetLastError();  // a pending error of earlier, unrelated work is not this call's
   if (p->desc.max_imfs > 0 && (!m || !mask_len)) return FIF_EINVAL;
   if (n < 4 || n > p->desc.max_n) return n < 4 ? FIF_EINVAL : FIF_EUNSUPPORTED;
   if (!is_smooth(n)) return FIF_EUNSUPPORTED;
   FftSched probe;
   if ((p->desc.flags & FIF_FORCE_MULTIPASS) || !make_sched(n, probe, p->smem_optin) ||
       !staged_fits(probe, p->smem_optin)) {
-    std::vector<int> one(1, 0);
-    return run_large_class(p, n, signal, nullptr, one, imfs, nullptr, m, mask_len, n_imfs,
-                           sig_status, diag, true);
+    Outputs o{imfs, m, mask_len, n_imfs, sig_status, diag};
+    return run_large_single(p, n, signal, o);
   }
   LengthTables* t = nullptr;
   fif_status st = get_tables(p, n, &t);
@@ -628,11 +746,6 @@ static fif_status check_batch(fif_plan_t p, const float* signals, const int64_t*
   return FIF_OK;
 }
 
-bool fits_fused(fif_plan_t p, int64_t n) {
-  if (p->desc.flags & FIF_FORCE_MULTIPASS) return false;
-  FftSched s;
-  return make_sched(n, s, p->smem_optin) && fused_fits(s, p->smem_optin);
-}
 
 fif_status fif_decompose_batch(fif_plan_t p, const float* signals, const int64_t* offsets,
                                int64_t batch, float* imfs, const int64_t* out_offsets, int32_t* m,
@@ -641,34 +754,62 @@ fif_status fif_decompose_batch(fif_plan_t p, const float* signals, const int64_t
   fif_status st = check_batch(p, signals, offsets, batch, imfs, out_offsets, m, mask_len, n_imfs,
                               sig_status);
   if (st != FIF_OK || batch == 0) return st;
-  std::vector<int> fused;
-  std::map<int64_t, std::vector<int>> large;
-  for (int64_t i = 0; i < batch; i++) {
-    const int64_t n = offsets[i + 1] - offsets[i];
-    if (fits_fused(p, n))
-      fused.push_back((int)i);
-    else
-      large[n].push_back((int)i);
-  }
-  if (!fused.empty()) {
+  cudaGetLastError();  // a pending error of earlier, unrelated work is not this call's
+  if (!layout_matches(p, offsets, out_offsets, batch)) {
+    std::vector<int> fused;
+    std::map<int64_t, std::vector<int>> large;
+    for (int64_t i = 0; i < batch; i++) {
+      const int64_t n = offsets[i + 1] - offsets[i];
+      if (fits_fused(p, n))
+        fused.push_back((int)i);
+      else
+        large[n].push_back((int)i);
+    }
+    p->layout_valid = false;
     st = prepare_layout(p, offsets, out_offsets, batch, fused);
-    if (st != FIF_OK) return st;
-    Outputs o{imfs, m, mask_len, n_imfs, sig_status, diag};
-    const BatchLayout& l = p->layout;
-    for (size_t c = 0; c < l.classes.size(); c++) {
-      const auto& cl = l.classes[c];
-      cudaError_t e = launch_fused(cl.E, l.d_sigs + cl.first, cl.count, l.d_scheds, cl.smem,
-                                   cl.threads, cl.grid, p->mp, signals, o, l.d_counters + c,
-                                   p->stream);
-      if (e != cudaSuccess) return cuda_status(e);
+    if (st == FIF_OK) st = prepare_large(p, offsets, out_offsets, large);
+    if (st != FIF_OK) {
+      p->layout_valid = false;
+      return st;
     }
   }
-  for (auto& kv : large) {
-    st = run_large_class(p, kv.first, signals, offsets, kv.second, imfs, out_offsets, m, mask_len,
-                         n_imfs, sig_status, diag, false);
-    if (st != FIF_OK) return st;
+  Outputs o{imfs, m, mask_len, n_imfs, sig_status, diag};
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  cudaError_t e = cudaStreamIsCapturing(p->stream, &cs);
+  if (e != cudaSuccess) return cuda_status(e);
+  if (cs != cudaStreamCaptureStatusNone) return enqueue_batch(p, signals, o);  // caller's graph
+  // The legacy and per-thread default streams cannot be captured: enqueue directly.
+  if (p->stream == nullptr || p->stream == cudaStreamLegacy || p->stream == cudaStreamPerThread)
+    return enqueue_batch(p, signals, o);
+  BatchLayout& l = p->layout;
+  const void* key[8] = {signals, imfs, m, mask_len, n_imfs, sig_status, diag, (const void*)p->stream};
+  if (!l.exec || !std::equal(key, key + 8, l.key)) {
+    if (l.exec) {
+      cudaGraphExecDestroy(l.exec);
+      l.exec = nullptr;
+    }
+    e = cudaStreamBeginCapture(p->stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return enqueue_batch(p, signals, o);
+    }
+    const fif_status es = enqueue_batch(p, signals, o);
+    cudaGraph_t g = nullptr;
+    e = cudaStreamEndCapture(p->stream, &g);
+    if (es != FIF_OK || e != cudaSuccess) {
+      if (g) cudaGraphDestroy(g);
+      cudaGetLastError();
+      return es != FIF_OK ? es : cuda_status(e);
+    }
+    e = cudaGraphInstantiate(&l.exec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+      l.exec = nullptr;
+      return cuda_status(e);
+    }
+    std::copy(key, key + 8, l.key);
   }
-  return FIF_OK;
+  return cuda_status(cudaGraphLaunch(l.exec, p->stream));
 }
 
 fif_status fif_decompose_batch_host(fif_plan_t p, const float* signals, const int64_t* offsets,

@@ -616,31 +616,31 @@ static __device__ double exact_sd(const float2* spec, const FftSched& S, int L, 
 }
 
 // Error band of the FP32 value of SD_j^2 relative to the binary64 value on
-// the same spectrum (u = 2^-24): table rounding of log2(1-w) and of the
-// subtraction/multiplication in the exponent (<= ln2 u (300 + 4 (j-1)
-// |hlmax|) for every weight above 2^-150) plus 2 ulp of exp2f per weight,
-// 3u on w^2, 2u on |r|^2, sequential plus tree summation of the positive
-// terms, one division.  The band is four times that bound.
-// The one-pass evaluation (online) also rescales partial sums by exp2f of
-// exponent differences, at most once per term per thread and once per
-// reduction level: another 2 ulp per rescale on the weights.
-__device__ __forceinline__ float screen_margin(const FftSched& S, int j, float hlmax, bool online) {
+// the same spectrum (u = 2^-24).  Each weight is exp2f(e_k - M) with
+// e_k = 2(j-1) log2(1-w_k): the rounding of the table value log2(1-w_k) and of
+// the product and difference in the exponent give at most
+// ln2 u (300 + 8 (j-1) |hlmax|) on every weight above 2^-150, exp2f adds
+// 2 ulp, and the running rescales of the one-pass accumulation (at most one
+// per term per thread and one per reduction level) 2 ulp each; w^2 carries 3u,
+// |r|^2 2u, the summation of positive terms (per-thread chain plus tree) and
+// the division the rest.  The band is four times that bound.
+__device__ __forceinline__ float screen_margin(const FftSched& S, int j, float hlmax) {
   const float u = 5.9604645e-8f;
   const float per_thread = (float)((S.P + (int)blockDim.x - 1) / (int)blockDim.x);
-  float werr = 0.6931472f * u * (300.f + 4.f * (float)(j - 1) * fabsf(hlmax)) + 4.f * u;
-  if (online) werr += 4.f * u * (per_thread + 10.f);
+  float werr = 0.6931472f * u * (300.f + 8.f * (float)(j - 1) * fabsf(hlmax)) + 4.f * u;
+  werr += 4.f * u * (per_thread + 10.f);
   const float serr = (per_thread + 12.f) * u;
   return 4.f * (2.f * werr + 2.f * serr + 8.f * u);
 }
 
 // Take the decision SD_j < delta from the FP32 ratio num/den if it lies
 // outside the error band, else re-take it on the binary64 value.
-static __device__ bool decide_sd(float num, float den, const float2* spec, const FftSched& S, int L, int j,
-                          const MethodParams& mp, MSelState& st, bool online, RedScratch* red) {
-  const float margin = screen_margin(S, j, st.hlmax, online);
+static __device__ bool decide_sd(float num, float den, const float2* spec, const FftSched& S, int L,
+                                 int j, const MethodParams& mp, MSelState& st, RedScratch* red) {
+  const float margin = screen_margin(S, j, st.hlmax);
   const float d2 = (float)(mp.delta * mp.delta);
   const float ratio = num / den;
-  if (den > 8.27e-25f && ratio == ratio) {  // 2^-80: no weight above the noise floor was lost
+  if (den >= 0.5f && ratio == ratio) {
     if (ratio <= d2 * (1.f - margin)) return true;
     if (ratio >= d2 * (1.f + margin)) return false;
   }
@@ -648,26 +648,6 @@ static __device__ bool decide_sd(float num, float den, const float2* spec, const
   st.flags |= FIF_FLAG_FP64_TIEBREAK;
   if (fabs(sd - mp.delta) <= 1e-6 * mp.delta) st.flags |= FIF_FLAG_NEAR_DELTA_TIE;
   return sd < mp.delta;
-}
-
-// FP32 screen of SD_j with known hlmax: weights exp2(2(j-1)(log2(1-w_k) - hlmax)).
-static __device__ bool sd_below(const float2* spec, const FftSched& S, const float2* row, int L, int j,
-                         const MethodParams& mp, MSelState& st, RedScratch* red) {
-  const int tid = threadIdx.x, nt = blockDim.x;
-  const float e2 = 2.f * (float)(j - 1);
-  float num = 0.f, den = 0.f;
-  for (int k = tid; k < S.P; k += nt) {
-    const float2 z = spec[k];
-    const float2 tv = __ldg(&row[k]);
-    const float re = z.x * st.sc, im = z.y * st.sc;
-    const float q = parseval_weight(S, k) * fmaf(re, re, im * im);
-    const float w = (j == 1) ? 1.f : exp2f(e2 * (tv.x - st.hlmax));
-    const float qw = q * w;
-    den += qw;
-    num = fmaf(qw, tv.y * tv.y, num);
-  }
-  block_reduce2(num, den, OpAdd(), 0.f, red);
-  return decide_sd(num, den, spec, S, L, j, mp, st, false, red);
 }
 
 struct Online {
@@ -685,12 +665,13 @@ __device__ __forceinline__ Online online_merge(Online a, Online b) {
   return Online{a.M, fmaf(b.num, s, a.num), fmaf(b.den, s, a.den)};
 }
 
-// The first evaluation (j = max_inner) in one pass: the normalising maximum of
-// the exponents is found on the fly, rescaling the running sums when it grows
-// (the combination is exact up to the rounding of exp2f and the products).
-// Sets st.hlmax for the evaluations that may follow.
-static __device__ bool sd_below_first(const float2* spec, const FftSched& S, const float2* row, int L,
-                               int j, const MethodParams& mp, MSelState& st, RedScratch* red) {
+// FP32 screen of SD_j in one pass over the bins, for any scale of the
+// spectrum: term k is q_k 2^(e_k - M) with q_k = c_k |sc r_k|^2, e_k =
+// 2(j-1) log2(1-w_k) and M the running maximum of e_k + floor(log2 q_k), so the
+// largest term lies in [1, 2) and no term that matters under- or overflows;
+// the running sums are rescaled when M grows.  Also sets st.hlmax.
+static __device__ bool sd_below(const float2* spec, const FftSched& S, const float2* row, int L,
+                                int j, const MethodParams& mp, MSelState& st, RedScratch* red) {
   const int tid = threadIdx.x, nt = blockDim.x;
   const float e2 = 2.f * (float)(j - 1);
   Online o{-INFINITY, 0.f, 0.f};
@@ -701,20 +682,21 @@ static __device__ bool sd_below_first(const float2* spec, const FftSched& S, con
     const float2 tv = __ldg(&row[k]);
     const float re = z.x * st.sc, im = z.y * st.sc;
     const float q = parseval_weight(S, k) * fmaf(re, re, im * im);
+    if (!(q > 0.f)) continue;
     hlmax = fmaxf(hlmax, tv.x);
     const float e = (j == 1) ? 0.f : e2 * tv.x;
     if (e == -INFINITY) continue;  // w_hat = 1 (the DC bin): weight 0 for j > 1
-    if (e > o.M) {
-      const float s = exp2f(o.M - e);  // 0 when o.M = -inf
+    const float t = e + (float)(((__float_as_int(q) >> 23) & 0xff) - 127);
+    if (t > o.M) {
+      const float s = exp2f(o.M - t);  // 0 when o.M = -inf
       o.num *= s;
       o.den *= s;
-      o.M = e;
+      o.M = t;
     }
     const float qw = q * exp2f(e - o.M);
     o.den += qw;
     o.num = fmaf(qw, tv.y * tv.y, o.num);
   }
-  // block-wide merge of (M, num, den) and max of hlmax
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) {
     Online b{__shfl_xor_sync(0xffffffffu, o.M, off), __shfl_xor_sync(0xffffffffu, o.num, off),
@@ -743,9 +725,7 @@ static __device__ bool sd_below_first(const float2* spec, const FftSched& S, con
     hm = fmaxf(hm, __shfl_xor_sync(0xffffffffu, hm, off));
   }
   st.hlmax = hm > -INFINITY ? hm : 0.f;
-  // bring the sums to the same normalisation as sd_below: exponent e2 (hl - hlmax)
-  const float shift = (j == 1 || r.M == -INFINITY) ? 1.f : exp2f(r.M - e2 * st.hlmax);
-  return decide_sd(r.num * shift, r.den * shift, spec, S, L, j, mp, st, true, red);
+  return decide_sd(r.num, r.den, spec, S, L, j, mp, st, red);
 }
 
 // m = first j in [1, max_inner] with SD_j < delta, else max_inner (eq. SD,
@@ -761,7 +741,7 @@ static __device__ int select_m(const float2* spec, const FftSched& S, int L, con
   st.flags = 0;
   int m;
   const int jmax = mp.max_inner;
-  if (!sd_below_first(spec, S, row, L, jmax, mp, st, red)) {
+  if (!sd_below(spec, S, row, L, jmax, mp, st, red)) {
     m = jmax;
     st.flags |= FIF_FLAG_MAX_INNER_HIT;
   } else {
@@ -791,7 +771,7 @@ static __device__ int select_m_on_row(const float2* spec, const FftSched& S, con
   st.flags = 0;
   int m;
   const int jmax = mp.max_inner;
-  if (!sd_below_first(spec, S, row, L, jmax, mp, st, red)) {
+  if (!sd_below(spec, S, row, L, jmax, mp, st, red)) {
     m = jmax;
     st.flags |= FIF_FLAG_MAX_INNER_HIT;
   } else {

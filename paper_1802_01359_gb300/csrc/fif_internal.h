@@ -105,16 +105,14 @@ struct LgSched {
   const float2* rcpff;    // {hi, lo} of 1/sin(pi k/n), k = 1..n/2 (entry 0 unused)
 };
 
-// One signal of a large-length class; za/zb hold float-float complex points
-// (16 bytes each) during the forward transform.
+// One signal of a large-length class: offsets into the caller's arrays and
+// the signal's working arrays (za/zb hold float-float complex points, 16
+// bytes each, during the forward transform).
 struct LgSig {
-  const float* x;
-  float* out;
-  int32_t* m;
-  int32_t* mask_len;
-  int32_t* n_imfs;
-  int32_t* status;
-  fif_imf_diag* diag;
+  int64_t in_off;
+  int64_t out_off;
+  int idx;                // signal index in the batch (rows of m, mask_len, ...)
+  int pad;
   float4* za;
   float4* zb;
   float2* spec;
@@ -128,8 +126,9 @@ struct LgSig {
 cudaError_t large_build_tables(const LgSched& G, float2* thi, float2* thi_lo, float2* tlo,
                                float2* tlo_lo, float2* sinff, float2* rcpff, cudaStream_t st);
 cudaError_t large_run(const LgSched& G, const LgSig* d_sigs, int nsig, const MethodParams& mp,
-                      cudaStream_t st);
+                      const float* signals, const Outputs& out, cudaStream_t st);
 size_t large_level_smem(const LgSched& G, int level, bool ff);
+cudaError_t large_set_attrs(const LgSched& G);
 
 // Kernel launchers (fif_fused.cu, fif_staged.cu, fif_tables.cu).
 cudaError_t launch_fused(int E, const SigDesc* d_sigs, int nsig, const FftSched* d_scheds,

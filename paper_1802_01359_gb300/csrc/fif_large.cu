@@ -27,6 +27,30 @@ enum {
   LG_BAD, LG_IMAX
 };
 
+// The caller's arrays of one signal.
+struct LgIO {
+  const float* x;
+  float* out;
+  int32_t* m;
+  int32_t* mask_len;
+  int32_t* n_imfs;
+  int32_t* status;
+  fif_imf_diag* diag;
+};
+
+__device__ __forceinline__ LgIO lg_io(const LgSig& sg, const float* signals, const Outputs& o,
+                                      int K) {
+  LgIO io;
+  io.x = signals + sg.in_off;
+  io.out = o.imfs + sg.out_off;
+  io.m = o.m + (size_t)sg.idx * K;
+  io.mask_len = o.mask_len + (size_t)sg.idx * K;
+  io.n_imfs = o.n_imfs + sg.idx;
+  io.status = o.sig_status + sg.idx;
+  io.diag = o.diag ? o.diag + (size_t)sg.idx * (K + 1) : nullptr;
+  return io;
+}
+
 // W_Nc^m (forward sign), 0 <= m < Nc
 template <class Cx, bool INV>
 __device__ __forceinline__ Cx inter_twiddle(const LgSched& G, int m);
@@ -58,9 +82,10 @@ __device__ __forceinline__ int first_signal_point(int& step) {
 
 // ------------------------------------------------------------ forward
 
-__global__ void lg_pack(const LgSig* __restrict__ sigs, LgSched G) {
+__global__ void lg_pack(const LgSig* __restrict__ sigs, LgSched G, const float* __restrict__ signals) {
   __shared__ RedScratch red;
   const LgSig sg = sigs[blockIdx.y];
+  const float* x = signals + sg.in_off;
   const int n = G.S.n, Nc = G.S.Nc;
   ffc* za = reinterpret_cast<ffc*>(sg.za);
   float amax = 0.f;
@@ -68,13 +93,13 @@ __global__ void lg_pack(const LgSig* __restrict__ sigs, LgSched G) {
   for (int t = first_signal_point(step); t < Nc; t += step) {
     float a, b;
     if (!G.S.odd) {
-      a = sg.x[2 * t];
-      b = sg.x[2 * t + 1];
+      a = x[2 * t];
+      b = x[2 * t + 1];
       sg.rem[2 * t] = a;
       sg.rem[2 * t + 1] = b;
       za[t] = ffc{ff{a, 0.f}, ff{b, 0.f}};
     } else {
-      a = sg.x[t];
+      a = x[t];
       b = 0.f;
       sg.rem[t] = a;
       za[t] = ffc{ff{a, 0.f}, ff{0.f, 0.f}};
@@ -180,18 +205,20 @@ __global__ void lg_split_fwd(const LgSig* __restrict__ sigs, LgSched G) {
 // ------------------------------------------------------------ per IMF
 
 __global__ void __launch_bounds__(512, 1) lg_ctl(const LgSig* __restrict__ sigs, LgSched G,
-                                                 MethodParams mp, int it) {
+                                                 MethodParams mp, int it,
+                                                 const float* __restrict__ signals, Outputs o) {
   __shared__ RedScratch red;
   const LgSig sg = sigs[blockIdx.x];
+  const LgIO io = lg_io(sg, signals, o, mp.max_imfs);
   int* st = sg.st;
   if (st[LG_DONE]) return;
   const int n = G.S.n, tid = threadIdx.x, nt = blockDim.x;
   if (it == 0 && st[LG_BAD]) {
-    for (int i = tid; i < n; i += nt) sg.out[i] = sg.x[i];
+    for (int i = tid; i < n; i += nt) io.out[i] = io.x[i];
     if (tid == 0) {
-      sg.n_imfs[0] = 0;
-      sg.status[0] = FIF_STOP_NONFINITE;
-      if (sg.diag) sg.diag[0] = fif_imf_diag{0, 0, 0, 0.f};
+      io.n_imfs[0] = 0;
+      io.status[0] = FIF_STOP_NONFINITE;
+      if (io.diag) io.diag[0] = fif_imf_diag{0, 0, 0, 0.f};
       st[LG_DONE] = 1;
     }
     return;
@@ -203,11 +230,11 @@ __global__ void __launch_bounds__(512, 1) lg_ctl(const LgSig* __restrict__ sigs,
   if (it > 0) {  // the IMF extracted in the previous iteration
     const int iflags = st[LG_IFLAGS];
     if (tid == 0) {
-      sg.m[K] = st[LG_M];
-      if (!mp.force_L) sg.mask_len[K] = st[LG_L];
-      if (sg.diag) {
-        sg.diag[K].flags = iflags;
-        sg.diag[K].inf_norm = __int_as_float(st[LG_IMAX]);
+      io.m[K] = st[LG_M];
+      if (!mp.force_L) io.mask_len[K] = st[LG_L];
+      if (io.diag) {
+        io.diag[K].flags = iflags;
+        io.diag[K].inf_norm = __int_as_float(st[LG_IMAX]);
       }
     }
     flags |= iflags;
@@ -216,21 +243,21 @@ __global__ void __launch_bounds__(512, 1) lg_ctl(const LgSig* __restrict__ sigs,
     e.tie = 0;  // the input itself is exact on both sides
   }
   int L = 0, iflags = e.tie ? FIF_FLAG_EXTREMA_TIE : 0;
-  const int reason = outer_test(e.k, K, n, mp, sg.mask_len, L, iflags);
-  if (sg.diag && tid == 0) {
-    sg.diag[K].k_extrema = e.k;
-    sg.diag[K].zero_crossings = e.zc;
+  const int reason = outer_test(e.k, K, n, mp, io.mask_len, L, iflags);
+  if (io.diag && tid == 0) {
+    io.diag[K].k_extrema = e.k;
+    io.diag[K].zero_crossings = e.zc;
   }
   if (reason) {
-    float* rrow = sg.out + (size_t)K * n;
+    float* rrow = io.out + (size_t)K * n;
     for (int i = tid; i < n; i += nt) rrow[i] = sg.rem[i];
     if (tid == 0) {
       flags |= iflags & FIF_FLAG_EXTREMA_TIE;
-      sg.n_imfs[0] = K;
-      sg.status[0] = reason | flags;
-      if (sg.diag) {
-        sg.diag[K].flags = iflags & FIF_FLAG_EXTREMA_TIE;
-        sg.diag[K].inf_norm = e.rmax;
+      io.n_imfs[0] = K;
+      io.status[0] = reason | flags;
+      if (io.diag) {
+        io.diag[K].flags = iflags & FIF_FLAG_EXTREMA_TIE;
+        io.diag[K].inf_norm = e.rmax;
       }
       st[LG_K] = K;
       st[LG_FLAGS] = flags;
@@ -347,13 +374,13 @@ __global__ void lg_presplit(const LgSig* __restrict__ sigs, LgSched G) {
   }
 }
 
-__global__ void lg_epilogue(const LgSig* __restrict__ sigs, LgSched G) {
+__global__ void lg_epilogue(const LgSig* __restrict__ sigs, LgSched G, float* __restrict__ imfs) {
   __shared__ RedScratch red;
   const LgSig sg = sigs[blockIdx.y];
   if (sg.st[LG_DONE]) return;
   const int n = G.S.n, K = sg.st[LG_K];
   const float inv_n = 1.f / (float)n;
-  float* orow = sg.out + (size_t)K * n;
+  float* orow = imfs + sg.out_off + (size_t)K * n;
   float imax = 0.f;
   int step;
   if (!G.S.odd) {
@@ -446,11 +473,9 @@ static cudaError_t launch_level(const LgSched& G, const LgSig* d_sigs, int nsig,
   const size_t smem = large_level_smem(G, LV, FF);
   const dim3 grid(tiles, nsig);
   switch (SR.E) {
-#define FIF_CASE(e)                                                                          \
-  case e:                                                                                    \
-    cudaFuncSetAttribute(lg_level<Cx, INV, e, LV>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
-                         (int)smem);                                                         \
-    lg_level<Cx, INV, e, LV><<<grid, threads, smem, st>>>(d_sigs, G);                        \
+#define FIF_CASE(e)                                                   \
+  case e:                                                             \
+    lg_level<Cx, INV, e, LV><<<grid, threads, smem, st>>>(d_sigs, G); \
     break;
     FIF_LG_E_LIST(FIF_CASE)
 #undef FIF_CASE
@@ -460,15 +485,42 @@ static cudaError_t launch_level(const LgSched& G, const LgSig* d_sigs, int nsig,
   return cudaGetLastError();
 }
 
+template <class Cx, bool INV, int LV>
+static cudaError_t level_attr(const LgSched& G, int smem) {
+  const FftSched& SR = LV == 1 ? G.S1 : G.S2;
+  switch (SR.E) {
+#define FIF_CASE(e) \
+  case e:           \
+    return cudaFuncSetAttribute(lg_level<Cx, INV, e, LV>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    FIF_LG_E_LIST(FIF_CASE)
+#undef FIF_CASE
+  }
+  return cudaErrorInvalidValue;
+}
+
+// Allow the level kernels this length uses the device's whole opt-in shared
+// memory (the instantiations are shared by lengths with other needs); call
+// before any stream capture.
+cudaError_t large_set_attrs(const LgSched& G) {
+  int dev = 0, optin = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (e == cudaSuccess) e = level_attr<ffc, false, 1>(G, optin);
+  if (e == cudaSuccess) e = level_attr<ffc, false, 2>(G, optin);
+  if (e == cudaSuccess) e = level_attr<float2, true, 1>(G, optin);
+  if (e == cudaSuccess) e = level_attr<float2, true, 2>(G, optin);
+  return e;
+}
+
 cudaError_t large_run(const LgSched& G, const LgSig* d_sigs, int nsig, const MethodParams& mp,
-                      cudaStream_t st) {
+                      const float* signals, const Outputs& out, cudaStream_t st) {
   const int pts = G.S.odd ? G.S.n : G.S.Nc;
   const int bx_pts = (pts + 255) / 256 < 1024 ? (pts + 255) / 256 : 1024;
   const int bx_bins = (G.S.P + 255) / 256 < 1024 ? (G.S.P + 255) / 256 : 1024;
   const int nc = G.S.Nc;
   const int bx_half = (nc / 2 + 256) / 256 < 1024 ? (nc / 2 + 256) / 256 : 1024;
   const int bx_split = G.S.odd ? bx_bins : bx_half;
-  lg_pack<<<dim3(bx_pts, nsig), 256, 0, st>>>(d_sigs, G);
+  lg_pack<<<dim3(bx_pts, nsig), 256, 0, st>>>(d_sigs, G, signals);
   cudaError_t e = cudaGetLastError();
   if (e == cudaSuccess) e = launch_level<ffc, false, 1>(G, d_sigs, nsig, st);
   if (e == cudaSuccess) e = launch_level<ffc, false, 2>(G, d_sigs, nsig, st);
@@ -477,7 +529,7 @@ cudaError_t large_run(const LgSched& G, const LgSig* d_sigs, int nsig, const Met
     e = cudaGetLastError();
   }
   for (int it = 0; e == cudaSuccess && it <= mp.max_imfs; it++) {
-    lg_ctl<<<nsig, 512, 0, st>>>(d_sigs, G, mp, it);
+    lg_ctl<<<nsig, 512, 0, st>>>(d_sigs, G, mp, it, signals, out);
     lg_row<<<dim3(bx_bins, nsig), 256, 0, st>>>(d_sigs, G);
     lg_select<<<nsig, 512, 0, st>>>(d_sigs, G, mp);
     lg_multiply<<<dim3(bx_bins, nsig), 256, 0, st>>>(d_sigs, G);
@@ -486,7 +538,7 @@ cudaError_t large_run(const LgSched& G, const LgSig* d_sigs, int nsig, const Met
     if (e == cudaSuccess) e = launch_level<float2, true, 1>(G, d_sigs, nsig, st);
     if (e == cudaSuccess) e = launch_level<float2, true, 2>(G, d_sigs, nsig, st);
     if (e == cudaSuccess) {
-      lg_epilogue<<<dim3(bx_pts, nsig), 256, 0, st>>>(d_sigs, G);
+      lg_epilogue<<<dim3(bx_pts, nsig), 256, 0, st>>>(d_sigs, G, out.imfs);
       e = cudaGetLastError();
     }
   }

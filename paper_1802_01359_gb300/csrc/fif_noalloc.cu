@@ -142,7 +142,7 @@ __global__ void __launch_bounds__(512, 1) na_select(FftSched S, NaScratch scr, M
   ms.flags = 0;
   int m;
   const int jmax = mp.max_inner;
-  if (!sd_below_first(scr.spec, S, scr.row, L, jmax, mp, ms, &red)) {
+  if (!sd_below(scr.spec, S, scr.row, L, jmax, mp, ms, &red)) {
     m = jmax;
     ms.flags |= FIF_FLAG_MAX_INNER_HIT;
   } else {
@@ -344,6 +344,7 @@ extern "C" fif_status fif_decompose_noalloc(const fif_plan_desc* d, const float*
     if (!ok) return FIF_EUNSUPPORTED;
   }
 
+  cudaGetLastError();  // a pending error of earlier, unrelated work is not this call's
   void* base = nullptr;
   cudaError_t e = scratch_address(&base);
   if (e != cudaSuccess) return FIF_ECUDA;

@@ -110,3 +110,50 @@ def test_long_degenerate_inputs(dev):
     assert res.signal(0).stop == fif.STOP_EXTREMA and res.signal(0).n_imfs == 0
     assert res.signal(1).stop == fif.STOP_NONFINITE and res.signal(1).n_imfs == 0
     assert np.array_equal(res.signal(1).imfs[0].cpu().numpy(), nanv, equal_nan=True)
+
+
+def test_batch_graph_replay_and_recapture(dev):
+    """Repeated calls with one layout replay the captured graph; new output pointers
+    re-capture; both give bit-identical results."""
+    lens = [4096, 24576, 729, 20736, 16384]
+    sigs = [signals.component_signal(75, i, n) for i, n in enumerate(lens)]
+    x, offs = _pack(sigs, dev)
+    with fif.Plan(max_n=1 << 15, max_imfs=4) as plan:
+        r1 = plan.decompose_batch(x, offs)
+        torch.cuda.synchronize()
+        first = [r1.signal(i).imfs[:r1.signal(i).n_imfs + 1].clone() for i in range(len(lens))]
+        m1 = r1.m.clone()
+        r1.imfs.fill_(0.0)
+        plan.decompose_batch(x, offs, out=r1)          # same pointers: graph replay
+        r2 = plan.decompose_batch(x, offs)             # new outputs: re-capture
+        torch.cuda.synchronize()
+        for r in (r1, r2):
+            assert torch.equal(r.m, m1)
+            for i in range(len(lens)):
+                d = r.signal(i)
+                assert torch.equal(d.imfs[:d.n_imfs + 1], first[i])
+
+
+def test_batch_inside_callers_cuda_graph(dev):
+    """With the plan's stream set to a capturing stream, the call is recorded into the
+    caller's graph (its layout was prepared by an earlier call)."""
+    lens = [2048, 20736]
+    sigs = [signals.component_signal(76, i, n) for i, n in enumerate(lens)]
+    x, offs = _pack(sigs, dev)
+    with fif.Plan(max_n=1 << 15, max_imfs=3) as plan:
+        ref = plan.decompose_batch(x, offs)
+        torch.cuda.synchronize()
+        out = plan.alloc_batch_outputs(np.diff(offs), dev)
+        g = torch.cuda.CUDAGraph()
+        s = torch.cuda.Stream()
+        s.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(s):
+            with torch.cuda.graph(g, stream=s):
+                plan.set_stream(torch.cuda.current_stream())
+                plan.decompose_batch(x, offs, out=out)
+        g.replay()
+        torch.cuda.synchronize()
+        assert torch.equal(out.m, ref.m) and torch.equal(out.n_imfs, ref.n_imfs)
+        for i in range(len(lens)):
+            a, b = out.signal(i), ref.signal(i)
+            assert torch.equal(a.imfs[:a.n_imfs + 1], b.imfs[:b.n_imfs + 1])
