@@ -65,6 +65,7 @@ struct LargeBuffers {
   float* rem = nullptr;
   float2* row = nullptr;
   int* st = nullptr;
+  unsigned char* part = nullptr;
   LgSig* d_sigs = nullptr;
 };
 
@@ -365,6 +366,13 @@ fif_status get_large(fif_plan_t p, int64_t n, LargeTables** out) {
   LargeTables lt;
   if (!make_large_sched(n, p->smem_optin, lt.G)) return FIF_EUNSUPPORTED;
   LgSched& G = lt.G;
+  {
+    // m search: 4 CTAs per SM, at least 2048 bins per CTA
+    const int want = (G.S.P + 2047) / 2048, cap = 4 * (p->num_sms > 0 ? p->num_sms : 1);
+    G.sel_blocks = want < cap ? want : cap;
+    if (G.sel_blocks > kSelBlocksMax) G.sel_blocks = kSelBlocksMax;
+    if (G.sel_blocks < 1) G.sel_blocks = 1;
+  }
   cudaError_t e = cudaSuccess;
   auto alloc = [&](size_t bytes) -> void* {
     void* ptr = nullptr;
@@ -446,7 +454,8 @@ fif_status large_buffers(fif_plan_t p, const LgSched& G, int nsig, LargeBuffers*
   b.work2 = (float2*)alloc(8 * (Nc + 1) * S);
   b.rem = (float*)alloc(4 * n * S);
   b.row = (float2*)alloc(8 * P * S);
-  b.st = (int*)alloc(64 * S);
+  b.st = (int*)alloc(sizeof(int) * kLgStateWords * S);
+  b.part = (unsigned char*)alloc((size_t)G.sel_blocks * kSelCand * kSelPartBytes * S);
   b.d_sigs = (LgSig*)alloc(sizeof(LgSig) * S);
   if (e != cudaSuccess) {
     free_large_buffers(b);
@@ -481,7 +490,8 @@ fif_status upload_large_class(fif_plan_t p, const LgSched& G, LargeBuffers* b,
     g.work2 = b->work2 + (Nc + 1) * q;
     g.rem = b->rem + (size_t)G.S.n * q;
     g.row = b->row + P * q;
-    g.st = b->st + 16 * q;
+    g.st = b->st + (size_t)kLgStateWords * q;
+    g.part = b->part + (size_t)G.sel_blocks * kSelCand * kSelPartBytes * q;
   }
   cudaError_t e = cudaMemcpyAsync(b->d_sigs, h.data(), sizeof(LgSig) * cnt,
                                   cudaMemcpyHostToDevice, p->stream);
@@ -500,7 +510,7 @@ fif_status run_large_single(fif_plan_t p, int64_t n, const float* signal, const 
   std::vector<int> one(1, 0);
   s = upload_large_class(p, lt->G, b, nullptr, nullptr, one);
   if (s != FIF_OK) return s;
-  cudaError_t e = cudaMemsetAsync(b->st, 0, 64, p->stream);
+  cudaError_t e = cudaMemsetAsync(b->st, 0, sizeof(int) * kLgStateWords, p->stream);
   if (e == cudaSuccess) e = large_run(lt->G, b->d_sigs, 1, p->mp, signal, o, p->stream);
   return cuda_status(e);
 }
@@ -555,7 +565,7 @@ fif_status enqueue_batch(fif_plan_t p, const float* signals, const Outputs& o) {
   for (size_t c = 0; c < l.lcls.size() && e == cudaSuccess; c++) {
     const auto& lc = l.lcls[c];
     cudaStream_t s = branch();
-    if (e == cudaSuccess) e = cudaMemsetAsync(lc.b->st, 0, 64 * (size_t)lc.count, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(lc.b->st, 0, sizeof(int) * kLgStateWords * (size_t)lc.count, s);
     if (e == cudaSuccess) e = large_run(lc.lt->G, lc.b->d_sigs, lc.count, p->mp, signals, o, s);
   }
   if (fork) {

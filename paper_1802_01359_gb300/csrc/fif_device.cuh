@@ -616,21 +616,28 @@ static __device__ double exact_sd(const float2* spec, const FftSched& S, int L, 
 }
 
 // Error band of the FP32 value of SD_j^2 relative to the binary64 value on
-// the same spectrum (u = 2^-24).  Each weight is exp2f(e_k - M) with
-// e_k = 2(j-1) log2(1-w_k): the rounding of the table value log2(1-w_k) and of
-// the product and difference in the exponent give at most
-// ln2 u (300 + 8 (j-1) |hlmax|) on every weight above 2^-150, exp2f adds
+// the same spectrum (u = 2^-24), for sums built from per-thread chains of at
+// most `chain` terms combined over at most `levels` merge steps.  Each weight
+// is exp2f(e_k - M) with e_k = 2(j-1) log2(1-w_k): the rounding of the table
+// value log2(1-w_k) and of the product and difference in the exponent give at
+// most ln2 u (300 + 8 (j-1) |hlmax|) on every weight above 2^-150, exp2f adds
 // 2 ulp, and the running rescales of the one-pass accumulation (at most one
-// per term per thread and one per reduction level) 2 ulp each; w^2 carries 3u,
-// |r|^2 2u, the summation of positive terms (per-thread chain plus tree) and
-// the division the rest.  The band is four times that bound.
-__device__ __forceinline__ float screen_margin(const FftSched& S, int j, float hlmax) {
+// per term of a chain and one per merge step) 2 ulp each; w^2 carries 3u,
+// |r|^2 2u, the summation of positive terms (chain plus merges) and the
+// division the rest.  The band is four times that bound.
+__host__ __device__ __forceinline__ float screen_margin_for(float chain, float levels, int j,
+                                                            float hlmax) {
   const float u = 5.9604645e-8f;
-  const float per_thread = (float)((S.P + (int)blockDim.x - 1) / (int)blockDim.x);
   float werr = 0.6931472f * u * (300.f + 8.f * (float)(j - 1) * fabsf(hlmax)) + 4.f * u;
-  werr += 4.f * u * (per_thread + 10.f);
-  const float serr = (per_thread + 12.f) * u;
+  werr += 4.f * u * (chain + levels);
+  const float serr = (chain + levels + 2.f) * u;
   return 4.f * (2.f * werr + 2.f * serr + 8.f * u);
+}
+
+// The band of one CTA's strided pass (ten merge steps: warp and CTA trees).
+__device__ __forceinline__ float screen_margin(const FftSched& S, int j, float hlmax) {
+  const float per_thread = (float)((S.P + (int)blockDim.x - 1) / (int)blockDim.x);
+  return screen_margin_for(per_thread, 10.f, j, hlmax);
 }
 
 // Take the decision SD_j < delta from the FP32 ratio num/den if it lies

@@ -103,7 +103,16 @@ struct LgSched {
   const float2* tlo_lo;
   const float2* sinff;    // {hi, lo} of sin(pi t/n), t = 0..n/2
   const float2* rcpff;    // {hi, lo} of 1/sin(pi k/n), k = 1..n/2 (entry 0 unused)
+  int sel_blocks;         // CTAs per signal in the grid-wide m search
 };
+
+// The grid-wide m search evaluates SD_j at up to kSelCand values of j per
+// round; each CTA leaves one partial per candidate (kSelPartBytes each, FP32
+// screen and binary64 tie-break side by side).
+constexpr int kSelCand = 16;
+constexpr int kSelBlocksMax = 1024;
+constexpr int kSelPartBytes = 48;
+constexpr int kLgStateWords = 32;
 
 // One signal of a large-length class: offsets into the caller's arrays and
 // the signal's working arrays (za/zb hold float-float complex points, 16
@@ -120,7 +129,8 @@ struct LgSig {
   float2* work2;
   float* rem;
   float2* row;
-  int* st;                // 16 state words, zeroed before each run
+  int* st;                // kLgStateWords state words, zeroed before each run
+  unsigned char* part;    // sel_blocks * kSelCand * kSelPartBytes
 };
 
 cudaError_t large_build_tables(const LgSched& G, float2* thi, float2* thi_lo, float2* tlo,
@@ -129,6 +139,7 @@ cudaError_t large_run(const LgSched& G, const LgSig* d_sigs, int nsig, const Met
                       const float* signals, const Outputs& out, cudaStream_t st);
 size_t large_level_smem(const LgSched& G, int level, bool ff);
 cudaError_t large_set_attrs(const LgSched& G);
+int large_sel_rounds(int max_inner);
 
 // Kernel launchers (fif_fused.cu, fif_staged.cu, fif_tables.cu).
 cudaError_t launch_fused(int E, const SigDesc* d_sigs, int nsig, const FftSched* d_scheds,

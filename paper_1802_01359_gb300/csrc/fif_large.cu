@@ -9,23 +9,34 @@
 //             Stockham factorisation with radices R1 and R2)
 //   split     real-transform split, rounded once to the FP32 spectrum
 // then per outer iteration:
-//   ctl       one CTA per signal: extrema count of r, bookkeeping of the last
-//             IMF, outer-loop test (Algorithm 2); on a stop the remainder row
+//   extrema   extrema and zero-crossing count of r over the whole grid
+//   ctl       one thread per signal: bookkeeping of the last IMF, outer-loop
+//             test (Algorithm 2)
+//   finish    on a stop, the remainder row
 //   row       window eigenvalues {log2(1-w_hat_k), w_hat_k} for this L, in
 //             float-float from sine and reciprocal-sine tables
-//   select    one CTA per signal: m by eq. SD (FP32 screen, binary64 tie-break)
+//   sel32/64  m by eq. SD: rounds of a 16-way search over j, each an FP32
+//             screen of SD_j at 16 values of j over the whole grid, then a
+//             binary64 pass for the values the screen cannot decide; the last
+//             CTA to finish a pass merges the partials and takes the decision
 //   multiply  IMF_hat = (1-w_hat)^m r_hat, r_hat <- (1 - (1-w_hat)^m) r_hat
 //   presplit  inverse real-transform split
 //   level 1/2 inverse complex FFT
 //   epilogue  IMF row = C2R / n, r <- r - IMF
+#include <map>
+
 #include "fif_device.cuh"
 
 namespace fif {
 
+// State words of one signal (zeroed before each run).
 enum {
-  LG_K = 0, LG_KEXT, LG_ZC, LG_TIE, LG_FLAGS, LG_DONE, LG_L, LG_M, LG_IFLAGS, LG_SMAX, LG_RMAX,
-  LG_BAD, LG_IMAX
+  LG_K = 0, LG_FLAGS, LG_DONE, LG_L, LG_M, LG_IFLAGS, LG_SMAX, LG_BAD, LG_IMAX,
+  LG_EXT, LG_ZC, LG_TIE, LG_RMAX,         // extrema count of the remainder (atomics)
+  LG_LO, LG_HI, LG_STAT, LG_AMB, LG_CNT,  // m search: bracket, statuses, arrivals
+  LG_NWORDS
 };
+static_assert(LG_NWORDS <= kLgStateWords, "state words");
 
 // The caller's arrays of one signal.
 struct LgIO {
@@ -204,38 +215,77 @@ __global__ void lg_split_fwd(const LgSig* __restrict__ sigs, LgSched G) {
 
 // ------------------------------------------------------------ per IMF
 
-__global__ void __launch_bounds__(512, 1) lg_ctl(const LgSig* __restrict__ sigs, LgSched G,
-                                                 MethodParams mp, int it,
-                                                 const float* __restrict__ signals, Outputs o) {
+// Extrema count, zero crossings, tie test and max |r| of the remainder (same
+// definitions as count_extrema), accumulated over the grid into the state.
+__global__ void lg_extrema(const LgSig* __restrict__ sigs, LgSched G) {
   __shared__ RedScratch red;
+  const LgSig sg = sigs[blockIdx.y];
+  int* st = sg.st;
+  if (st[LG_DONE] || st[LG_BAD]) return;
+  const float tau = tie_tau(__int_as_float(st[LG_SMAX]));
+  const float* rem = sg.rem;
+  const int n = G.S.n;
+  int ext = 0, zc = 0, tie = 0, step;
+  float rmax = 0.f;
+  for (int i = first_signal_point(step); i < n; i += step) {
+    const int im1 = i == 0 ? n - 1 : i - 1;
+    const int ip1 = i + 1 == n ? 0 : i + 1;
+    const int ip2 = ip1 + 1 == n ? 0 : ip1 + 1;
+    const float a = rem[im1], b = rem[i], c = rem[ip1], d = rem[ip2];
+    const float dm = b - a, d0 = c - b, dp = d - c;
+    ext += (dm > 0.f && d0 < 0.f) || (dm < 0.f && d0 > 0.f);
+    zc += (b > 0.f && c < 0.f) || (b < 0.f && c > 0.f);
+    tie |= fabsf(d0) <= tau && (fabsf(dm) <= tau || fabsf(dp) <= tau || ((dm > 0.f) == (dp > 0.f)));
+    rmax = fmaxf(rmax, fabsf(b));
+  }
+  tie = __syncthreads_or(tie);
+  float fe = (float)ext, fz = (float)zc;  // exact: a CTA counts far fewer than 2^24
+  block_reduce2(fe, fz, OpAdd(), 0.f, &red);
+  float dummy = 0.f;
+  block_reduce2(rmax, dummy, OpMax(), 0.f, &red);
+  if (threadIdx.x == 0) {
+    atomicAdd(&st[LG_EXT], (int)fe);
+    atomicAdd(&st[LG_ZC], (int)fz);
+    if (tie) atomicOr(&st[LG_TIE], 1);
+    atomicMax(&st[LG_RMAX], __float_as_int(rmax));
+  }
+}
+
+// Bookkeeping of the IMF extracted in the previous iteration and the outer
+// loop test of Algorithm 2 (one thread per signal).  On a stop the remainder
+// row is written by lg_finish; st[LG_DONE] records the iteration + 1.
+__global__ void lg_ctl(const LgSig* __restrict__ sigs, LgSched G, MethodParams mp, int it,
+                       const float* __restrict__ signals, Outputs o) {
   const LgSig sg = sigs[blockIdx.x];
   const LgIO io = lg_io(sg, signals, o, mp.max_imfs);
   int* st = sg.st;
   if (st[LG_DONE]) return;
-  const int n = G.S.n, tid = threadIdx.x, nt = blockDim.x;
   if (it == 0 && st[LG_BAD]) {
-    for (int i = tid; i < n; i += nt) io.out[i] = io.x[i];
-    if (tid == 0) {
-      io.n_imfs[0] = 0;
-      io.status[0] = FIF_STOP_NONFINITE;
-      if (io.diag) io.diag[0] = fif_imf_diag{0, 0, 0, 0.f};
-      st[LG_DONE] = 1;
-    }
+    io.n_imfs[0] = 0;
+    io.status[0] = FIF_STOP_NONFINITE;
+    if (io.diag) io.diag[0] = fif_imf_diag{0, 0, 0, 0.f};
+    st[LG_DONE] = it + 1;
     return;
   }
-  const float tau = tie_tau(__int_as_float(st[LG_SMAX]));
-  ExtremaInfo e = count_extrema(sg.rem, n, tau, &red);
+  const int n = G.S.n;
+  ExtremaInfo e;
+  e.k = st[LG_EXT];
+  e.zc = st[LG_ZC];
+  e.tie = st[LG_TIE];
+  e.rmax = __int_as_float(st[LG_RMAX]);
+  st[LG_EXT] = 0;
+  st[LG_ZC] = 0;
+  st[LG_TIE] = 0;
+  st[LG_RMAX] = 0;
   int K = st[LG_K];
   int flags = st[LG_FLAGS];
   if (it > 0) {  // the IMF extracted in the previous iteration
     const int iflags = st[LG_IFLAGS];
-    if (tid == 0) {
-      io.m[K] = st[LG_M];
-      if (!mp.force_L) io.mask_len[K] = st[LG_L];
-      if (io.diag) {
-        io.diag[K].flags = iflags;
-        io.diag[K].inf_norm = __int_as_float(st[LG_IMAX]);
-      }
+    io.m[K] = st[LG_M];
+    if (!mp.force_L) io.mask_len[K] = st[LG_L];
+    if (io.diag) {
+      io.diag[K].flags = iflags;
+      io.diag[K].inf_norm = __int_as_float(st[LG_IMAX]);
     }
     flags |= iflags;
     K++;
@@ -244,34 +294,44 @@ __global__ void __launch_bounds__(512, 1) lg_ctl(const LgSig* __restrict__ sigs,
   }
   int L = 0, iflags = e.tie ? FIF_FLAG_EXTREMA_TIE : 0;
   const int reason = outer_test(e.k, K, n, mp, io.mask_len, L, iflags);
-  if (io.diag && tid == 0) {
+  if (io.diag) {
     io.diag[K].k_extrema = e.k;
     io.diag[K].zero_crossings = e.zc;
   }
+  st[LG_K] = K;
   if (reason) {
-    float* rrow = io.out + (size_t)K * n;
-    for (int i = tid; i < n; i += nt) rrow[i] = sg.rem[i];
-    if (tid == 0) {
-      flags |= iflags & FIF_FLAG_EXTREMA_TIE;
-      io.n_imfs[0] = K;
-      io.status[0] = reason | flags;
-      if (io.diag) {
-        io.diag[K].flags = iflags & FIF_FLAG_EXTREMA_TIE;
-        io.diag[K].inf_norm = e.rmax;
-      }
-      st[LG_K] = K;
-      st[LG_FLAGS] = flags;
-      st[LG_DONE] = 1;
+    flags |= iflags & FIF_FLAG_EXTREMA_TIE;
+    io.n_imfs[0] = K;
+    io.status[0] = reason | flags;
+    if (io.diag) {
+      io.diag[K].flags = iflags & FIF_FLAG_EXTREMA_TIE;
+      io.diag[K].inf_norm = e.rmax;
     }
+    st[LG_FLAGS] = flags;
+    st[LG_DONE] = it + 1;
     return;
   }
-  if (tid == 0) {
-    st[LG_K] = K;
-    st[LG_FLAGS] = flags;
-    st[LG_L] = L;
-    st[LG_IFLAGS] = iflags;
-    st[LG_IMAX] = 0;
-  }
+  st[LG_FLAGS] = flags;
+  st[LG_L] = L;
+  st[LG_IFLAGS] = iflags;
+  st[LG_IMAX] = 0;
+  st[LG_LO] = 0;
+  st[LG_HI] = mp.max_inner + 1;  // no j tested below delta yet
+  st[LG_M] = mp.max_inner;
+  st[LG_AMB] = 0;
+  st[LG_STAT] = 0;
+  st[LG_CNT] = 0;
+}
+
+// The remainder row of a signal that stopped in this iteration (a NaN input
+// is its own remainder: lg_pack copied it).
+__global__ void lg_finish(const LgSig* __restrict__ sigs, LgSched G, int it, float* __restrict__ imfs) {
+  const LgSig sg = sigs[blockIdx.y];
+  if (sg.st[LG_DONE] != it + 1) return;
+  const int n = G.S.n;
+  float* orow = imfs + sg.out_off + (size_t)sg.st[LG_K] * n;
+  int step;
+  for (int i = first_signal_point(step); i < n; i += step) orow[i] = sg.rem[i];
 }
 
 // x / L in float-float for an integer 1 <= L < 2^24 (exact in binary32)
@@ -318,20 +378,369 @@ __global__ void lg_row(const LgSig* __restrict__ sigs, LgSched G) {
   }
 }
 
-__global__ void __launch_bounds__(512, 1) lg_select(const LgSig* __restrict__ sigs, LgSched G,
-                                                    MethodParams mp) {
-  __shared__ RedScratch red;
-  const LgSig sg = sigs[blockIdx.x];
+// ------------------------------------------------------------ m search
+
+// Candidates of round `round` of the search for m = the first j in
+// [1, max_inner] with SD_j < delta (eq. SD, Sec. 4).  Round 0 tests
+// ceil((i+1) max_inner / c), i < c = min(16, max_inner), which includes
+// max_inner itself; a later round tests the j strictly inside the bracket
+// (lo, hi) left by the one before: all of them if there are at most 16, else
+// 16 evenly spaced ones.  Candidates are strictly increasing.
+__host__ __device__ __forceinline__ int sel_count(int lo, int hi, int jmax, int round) {
+  if (round == 0) return jmax < kSelCand ? jmax : kSelCand;
+  const int u = hi - lo - 1;
+  return u <= 0 ? 0 : (u < kSelCand ? u : kSelCand);
+}
+__host__ __device__ __forceinline__ int sel_cand(int lo, int hi, int jmax, int round, int i) {
+  if (round == 0) {
+    const int c = jmax < kSelCand ? jmax : kSelCand;
+    return (int)(((long long)(i + 1) * jmax + c - 1) / c);
+  }
+  const int u = hi - lo - 1;
+  if (u <= kSelCand) return lo + 1 + i;
+  return lo + (int)(((long long)(i + 1) * (u + 1) + kSelCand) / (kSelCand + 1));
+}
+
+// Rounds after which every bracket is closed, from the gaps each round can
+// leave (the search runs this many rounds; a closed bracket makes the
+// remaining ones return at once).  Only the gap sizes that occur are visited.
+static int sel_rounds_after(int u, int jmax, std::map<int, int>& memo) {
+  if (u <= 0) return 0;
+  auto f = memo.find(u);
+  if (f != memo.end()) return f->second;
+  const int c = sel_count(0, u + 1, jmax, 1);
+  int prev = 0, w = 0;
+  for (int i = 0; i <= c; i++) {
+    const int j = i < c ? sel_cand(0, u + 1, jmax, 1, i) : u + 1;
+    const int r = sel_rounds_after(j - prev - 1, jmax, memo);
+    if (r > w) w = r;
+    prev = j;
+  }
+  memo[u] = 1 + w;
+  return 1 + w;
+}
+
+int large_sel_rounds(int jmax) {
+  std::map<int, int> memo;
+  const int c0 = sel_count(0, jmax + 1, jmax, 0);
+  int prev = 0, w = 0;
+  for (int i = 0; i < c0; i++) {
+    const int j = sel_cand(0, jmax + 1, jmax, 0, i);
+    const int r = sel_rounds_after(j - prev - 1, jmax, memo);
+    if (r > w) w = r;
+    prev = j;
+  }
+  return 1 + w;
+}
+
+enum { SEL_F = 0, SEL_T = 1, SEL_AMB = 2 };  // SD_j >= delta, SD_j < delta, undecided
+
+struct SelStep {
+  int lo, hi, amb;
+};
+
+// New bracket from the statuses of this round's candidates: hi = the first
+// candidate below delta, lo = the last candidate at or above delta before it.
+// Undecided candidates between them (and, in round 0, an undecided max_inner,
+// which alone decides m = max_inner when SD_max_inner >= delta) are returned
+// in amb for the binary64 pass.
+__device__ SelStep sel_update(int lo, int hi, int jmax, int round, unsigned stat) {
+  SelStep r{lo, hi, 0};
+  const int c = sel_count(lo, hi, jmax, round);
+  if (round == 0) {
+    const unsigned s = (stat >> (2 * (c - 1))) & 3u;
+    if (s == SEL_F) return SelStep{jmax, jmax + 1, 0};
+    if (s == SEL_AMB) r.amb |= 1 << (c - 1);
+  }
+  int iT = c;
+  for (int i = 0; i < c; i++)
+    if (((stat >> (2 * i)) & 3u) == SEL_T) {
+      iT = i;
+      break;
+    }
+  if (iT < c) r.hi = sel_cand(lo, hi, jmax, round, iT);
+  for (int i = 0; i < iT; i++)
+    if (((stat >> (2 * i)) & 3u) == SEL_F) r.lo = sel_cand(lo, hi, jmax, round, i);
+  for (int i = 0; i < iT; i++) {
+    const int j = sel_cand(lo, hi, jmax, round, i);
+    if (j > r.lo && ((stat >> (2 * i)) & 3u) == SEL_AMB) r.amb |= 1 << i;
+  }
+  return r;
+}
+
+// Store a decided bracket; a closed one gives m (max_inner when no tested j
+// had SD_j < delta).
+__device__ void sel_commit(int* st, const SelStep& r, int jmax, int flags) {
+  st[LG_LO] = r.lo;
+  st[LG_HI] = r.hi;
+  st[LG_AMB] = 0;
+  if (r.hi - r.lo <= 1) {
+    if (r.hi == jmax + 1) {
+      st[LG_M] = jmax;
+      flags |= FIF_FLAG_MAX_INNER_HIT;
+    } else {
+      st[LG_M] = r.hi;
+    }
+  }
+  st[LG_IFLAGS] |= flags;
+}
+
+template <class T>
+struct OnlineT {
+  T M, num, den;
+};
+
+template <class T>
+__device__ __forceinline__ OnlineT<T> online_merge_t(OnlineT<T> a, OnlineT<T> b) {
+  if (a.M < b.M) {
+    const OnlineT<T> t = a;
+    a = b;
+    b = t;
+  }
+  if (b.M == -INFINITY) return a;
+  const T s = exp2(b.M - a.M);
+  return OnlineT<T>{a.M, b.num * s + a.num, b.den * s + a.den};
+}
+
+template <class T>
+__device__ __forceinline__ OnlineT<T> warp_merge(OnlineT<T> o) {
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    OnlineT<T> b{__shfl_xor_sync(0xffffffffu, o.M, off), __shfl_xor_sync(0xffffffffu, o.num, off),
+                 __shfl_xor_sync(0xffffffffu, o.den, off)};
+    o = online_merge_t(o, b);
+  }
+  return o;
+}
+
+__device__ __forceinline__ float4* part32(const LgSig& sg, int b, int i) {
+  return reinterpret_cast<float4*>(sg.part + ((size_t)b * kSelCand + i) * kSelPartBytes);
+}
+__device__ __forceinline__ double* part64(const LgSig& sg, int b, int i) {
+  return reinterpret_cast<double*>(sg.part + ((size_t)b * kSelCand + i) * kSelPartBytes + 16);
+}
+
+// True in every thread of the last CTA of this signal to reach this point
+// (after its partials are visible); resets the arrival counter.
+__device__ __forceinline__ bool last_to_arrive(int* cnt) {
+  __shared__ int last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    last = atomicAdd(cnt, 1) == (int)gridDim.x - 1;
+    if (last) *cnt = 0;
+  }
+  __syncthreads();
+  if (last) __threadfence();
+  return last;
+}
+
+constexpr int kSelThreads = 256;
+
+// FP32 screen of SD_j for this round's candidates over the grid: per bin the
+// term of sd_below for each candidate, accumulated online per thread, merged
+// per CTA into sg.part; the last CTA merges the CTAs in index order and
+// classifies each candidate against delta with the error band of this
+// reduction (screen_margin_for).
+__global__ void __launch_bounds__(kSelThreads) lg_sel32(const LgSig* __restrict__ sigs, LgSched G,
+                                                         MethodParams mp, int round) {
+  __shared__ float4 wpart[kSelThreads / 32][kSelCand];
+  __shared__ float4 fin[kSelCand];
+  const LgSig sg = sigs[blockIdx.y];
   int* st = sg.st;
   if (st[LG_DONE]) return;
-  const int L = st[LG_L];
-  int iflags = st[LG_IFLAGS];
-  const float sc = spectrum_scale(G.S.n, __int_as_float(st[LG_SMAX]));
-  const int m = select_m_on_row(sg.spec, G.S, sg.row, L, mp, sc, iflags, &red);
-  if (threadIdx.x == 0) {
-    st[LG_M] = m;
-    st[LG_IFLAGS] = iflags;
+  const int jmax = mp.max_inner, lo = st[LG_LO], hi = st[LG_HI];
+  const int c = sel_count(lo, hi, jmax, round);
+  if (c == 0) return;
+  const FftSched& S = G.S;
+  const float sc = spectrum_scale(S.n, __int_as_float(st[LG_SMAX]));
+  OnlineT<float> o[kSelCand];
+  float e2[kSelCand];
+#pragma unroll
+  for (int i = 0; i < kSelCand; i++) {
+    o[i] = OnlineT<float>{-INFINITY, 0.f, 0.f};
+    e2[i] = i < c ? 2.f * (float)(sel_cand(lo, hi, jmax, round, i) - 1) : 0.f;
   }
+  float hlmax = -INFINITY;
+  const int stride = gridDim.x * blockDim.x;
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < S.P; k += stride) {
+    const float2 z = sg.spec[k];
+    if (z.x == 0.f && z.y == 0.f) continue;
+    const float2 tv = sg.row[k];
+    const float re = z.x * sc, im = z.y * sc;
+    const float q = parseval_weight(S, k) * fmaf(re, re, im * im);
+    if (!(q > 0.f)) continue;
+    hlmax = fmaxf(hlmax, tv.x);
+    const float qe = (float)(((__float_as_int(q) >> 23) & 0xff) - 127);
+    const float w2 = tv.y * tv.y;
+#pragma unroll
+    for (int i = 0; i < kSelCand; i++) {
+      if (i < c) {
+        const float e = e2[i] == 0.f ? 0.f : e2[i] * tv.x;
+        if (e != -INFINITY) {  // w_hat = 1 (the DC bin): weight 0 for j > 1
+          const float t = e + qe;
+          if (t > o[i].M) {
+            const float s = exp2f(o[i].M - t);  // 0 when M = -inf
+            o[i].num *= s;
+            o[i].den *= s;
+            o[i].M = t;
+          }
+          const float qw = q * exp2f(e - o[i].M);
+          o[i].den += qw;
+          o[i].num = fmaf(qw, w2, o[i].num);
+        }
+      }
+    }
+  }
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) hlmax = fmaxf(hlmax, __shfl_xor_sync(0xffffffffu, hlmax, off));
+#pragma unroll
+  for (int i = 0; i < kSelCand; i++) {
+    if (i < c) {
+      const OnlineT<float> r = warp_merge(o[i]);
+      if (lane == 0) wpart[wid][i] = make_float4(r.M, r.num, r.den, hlmax);
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x < c) {
+    const int i = threadIdx.x;
+    OnlineT<float> r{-INFINITY, 0.f, 0.f};
+    float hm = -INFINITY;
+    for (int w = 0; w < kSelThreads / 32; w++) {
+      const float4 v = wpart[w][i];
+      r = online_merge_t(r, OnlineT<float>{v.x, v.y, v.z});
+      hm = fmaxf(hm, v.w);
+    }
+    *part32(sg, blockIdx.x, i) = make_float4(r.M, r.num, r.den, hm);
+  }
+  if (!last_to_arrive(&st[LG_CNT])) return;
+  const int nb = gridDim.x;
+  for (int i = wid; i < c; i += kSelThreads / 32) {
+    OnlineT<float> r{-INFINITY, 0.f, 0.f};
+    float hm = -INFINITY;
+    for (int b = lane; b < nb; b += 32) {
+      const float4 v = __ldcg(part32(sg, b, i));
+      r = online_merge_t(r, OnlineT<float>{v.x, v.y, v.z});
+      hm = fmaxf(hm, v.w);
+    }
+    r = warp_merge(r);
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) hm = fmaxf(hm, __shfl_xor_sync(0xffffffffu, hm, off));
+    if (lane == 0) fin[i] = make_float4(r.M, r.num, r.den, hm);
+  }
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  float hm = -INFINITY;
+  for (int i = 0; i < c; i++) hm = fmaxf(hm, fin[i].w);
+  if (!(hm > -INFINITY)) hm = 0.f;
+  // chain: bins per thread, then the warps of a CTA and the CTAs per lane of
+  // the final merge; levels: two warp trees
+  const float chain = (float)((S.P + stride - 1) / stride + kSelThreads / 32 + (nb + 31) / 32);
+  const float d2 = (float)(mp.delta * mp.delta);
+  unsigned stat = 0;
+  for (int i = 0; i < c; i++) {
+    const int j = sel_cand(lo, hi, jmax, round, i);
+    const float margin = screen_margin_for(chain, 10.f, j, hm);
+    const float ratio = fin[i].y / fin[i].z;
+    unsigned s = SEL_AMB;
+    if (fin[i].z >= 0.5f && ratio == ratio) {
+      if (ratio <= d2 * (1.f - margin)) s = SEL_T;
+      else if (ratio >= d2 * (1.f + margin)) s = SEL_F;
+    }
+    stat |= s << (2 * i);
+  }
+  const SelStep r = sel_update(lo, hi, jmax, round, stat);
+  if (r.amb) {
+    st[LG_STAT] = (int)stat;
+    st[LG_AMB] = r.amb;
+  } else {
+    sel_commit(st, r, jmax, 0);
+  }
+}
+
+// Binary64 SD_j (the terms of exact_sd, accumulated online) for the
+// candidates the screen left undecided; the last CTA resolves them and
+// closes the round.
+__global__ void __launch_bounds__(kSelThreads) lg_sel64(const LgSig* __restrict__ sigs, LgSched G,
+                                                         MethodParams mp, int round) {
+  __shared__ double wpart[kSelThreads / 32][3];
+  __shared__ double sd[kSelCand];
+  const LgSig sg = sigs[blockIdx.y];
+  int* st = sg.st;
+  if (st[LG_DONE]) return;
+  const int amb = st[LG_AMB];
+  if (amb == 0) return;
+  const int jmax = mp.max_inner, lo = st[LG_LO], hi = st[LG_HI], L = st[LG_L];
+  const FftSched& S = G.S;
+  const double inv_ln2 = 1.4426950408889634;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int stride = gridDim.x * blockDim.x;
+  for (int i = 0; i < kSelCand; i++) {
+    if (!((amb >> i) & 1)) continue;
+    const int j = sel_cand(lo, hi, jmax, round, i);
+    OnlineT<double> o{-INFINITY, 0.0, 0.0};
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < S.P; k += stride) {
+      const float2 z = sg.spec[k];
+      const double q = (double)parseval_weight(S, k) * ((double)z.x * z.x + (double)z.y * z.y);
+      if (!(q > 0.0)) continue;
+      const double w = what64(S, L, k);
+      double lw = log2(q);
+      if (j > 1) lw += 2.0 * (j - 1) * log1p(-w) * inv_ln2;
+      if (lw == -INFINITY) continue;
+      if (lw > o.M) {
+        const double s = exp2(o.M - lw);
+        o.num *= s;
+        o.den *= s;
+        o.M = lw;
+      }
+      const double t = exp2(lw - o.M);
+      o.den += t;
+      o.num += t * w * w;
+    }
+    o = warp_merge(o);
+    __syncthreads();
+    if (lane == 0) {
+      wpart[wid][0] = o.M;
+      wpart[wid][1] = o.num;
+      wpart[wid][2] = o.den;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      OnlineT<double> r{-INFINITY, 0.0, 0.0};
+      for (int w = 0; w < kSelThreads / 32; w++)
+        r = online_merge_t(r, OnlineT<double>{wpart[w][0], wpart[w][1], wpart[w][2]});
+      double* d = part64(sg, blockIdx.x, i);
+      d[0] = r.M;
+      d[1] = r.num;
+      d[2] = r.den;
+    }
+  }
+  if (!last_to_arrive(&st[LG_CNT])) return;
+  const int nb = gridDim.x;
+  for (int i = wid; i < kSelCand; i += kSelThreads / 32) {
+    if (!((amb >> i) & 1)) continue;
+    OnlineT<double> r{-INFINITY, 0.0, 0.0};
+    for (int b = lane; b < nb; b += 32) {
+      const double* d = part64(sg, b, i);
+      r = online_merge_t(r, OnlineT<double>{__ldcg(d), __ldcg(d + 1), __ldcg(d + 2)});
+    }
+    r = warp_merge(r);
+    if (lane == 0) sd[i] = r.den > 0.0 ? sqrt(r.num / r.den) : 0.0;
+  }
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  unsigned stat = (unsigned)st[LG_STAT];
+  int flags = FIF_FLAG_FP64_TIEBREAK;
+  for (int i = 0; i < kSelCand; i++) {
+    if (!((amb >> i) & 1)) continue;
+    if (fabs(sd[i] - mp.delta) <= 1e-6 * mp.delta) flags |= FIF_FLAG_NEAR_DELTA_TIE;
+    const unsigned s = sd[i] < mp.delta ? SEL_T : SEL_F;
+    stat = (stat & ~(3u << (2 * i))) | (s << (2 * i));
+  }
+  SelStep r = sel_update(lo, hi, jmax, round, stat);
+  r.amb = 0;  // every candidate that could move the bracket is now decided
+  sel_commit(st, r, jmax, flags);
 }
 
 __global__ void lg_multiply(const LgSig* __restrict__ sigs, LgSched G) {
@@ -520,6 +929,8 @@ cudaError_t large_run(const LgSched& G, const LgSig* d_sigs, int nsig, const Met
   const int nc = G.S.Nc;
   const int bx_half = (nc / 2 + 256) / 256 < 1024 ? (nc / 2 + 256) / 256 : 1024;
   const int bx_split = G.S.odd ? bx_bins : bx_half;
+  const int bx_n = (G.S.n + 255) / 256 < 1024 ? (G.S.n + 255) / 256 : 1024;
+  const int rounds = large_sel_rounds(mp.max_inner);
   lg_pack<<<dim3(bx_pts, nsig), 256, 0, st>>>(d_sigs, G, signals);
   cudaError_t e = cudaGetLastError();
   if (e == cudaSuccess) e = launch_level<ffc, false, 1>(G, d_sigs, nsig, st);
@@ -529,9 +940,14 @@ cudaError_t large_run(const LgSched& G, const LgSig* d_sigs, int nsig, const Met
     e = cudaGetLastError();
   }
   for (int it = 0; e == cudaSuccess && it <= mp.max_imfs; it++) {
-    lg_ctl<<<nsig, 512, 0, st>>>(d_sigs, G, mp, it, signals, out);
+    lg_extrema<<<dim3(bx_n, nsig), 256, 0, st>>>(d_sigs, G);
+    lg_ctl<<<nsig, 1, 0, st>>>(d_sigs, G, mp, it, signals, out);
+    lg_finish<<<dim3(bx_n, nsig), 256, 0, st>>>(d_sigs, G, it, out.imfs);
     lg_row<<<dim3(bx_bins, nsig), 256, 0, st>>>(d_sigs, G);
-    lg_select<<<nsig, 512, 0, st>>>(d_sigs, G, mp);
+    for (int r = 0; r < rounds; r++) {
+      lg_sel32<<<dim3(G.sel_blocks, nsig), kSelThreads, 0, st>>>(d_sigs, G, mp, r);
+      lg_sel64<<<dim3(G.sel_blocks, nsig), kSelThreads, 0, st>>>(d_sigs, G, mp, r);
+    }
     lg_multiply<<<dim3(bx_bins, nsig), 256, 0, st>>>(d_sigs, G);
     lg_presplit<<<dim3(bx_split, nsig), 256, 0, st>>>(d_sigs, G);
     e = cudaGetLastError();

@@ -157,3 +157,19 @@ def test_batch_inside_callers_cuda_graph(dev):
         for i in range(len(lens)):
             a, b = out.signal(i), ref.signal(i)
             assert torch.equal(a.imfs[:a.n_imfs + 1], b.imfs[:b.n_imfs + 1])
+
+
+@pytest.mark.parametrize("max_inner", [1, 2, 15, 16, 17, 40, 200, 289, 290, 1000])
+def test_multipass_m_search_any_max_inner(dev, oracle_mod, max_inner):
+    """The grid-wide search for m (rounds of up to 16 candidates j) closes its
+    bracket for every cap: m and every other integer match the oracle."""
+    lens = [4096, 6561, 20736]
+    sigs = [signals.component_signal(77, i, n) for i, n in enumerate(lens)]
+    x, offs = _pack(sigs, dev)
+    with fif.Plan(max_n=1 << 15, max_imfs=4, max_inner=max_inner, delta=1e-4,
+                  multipass=True) as plan:
+        res = plan.decompose_batch(x, offs, diag=True)
+        torch.cuda.synchronize()
+    for i, s in enumerate(sigs):
+        ref = oracle_mod.direct(s.astype(np.float64), max_imfs=4, max_inner=max_inner, delta=1e-4)
+        parity.compare(res.signal(i), ref)
