@@ -38,7 +38,7 @@ struct BatchLayout {
   const void* key[8] = {nullptr};
   // classes: contiguous ranges of the sorted signal list sharing one length
   struct Cls {
-    int first, count, smem, threads, grid, E;
+    int first, count, smem, threads, grid, E, n;
   };
   std::vector<Cls> classes;
   SigDesc* d_sigs = nullptr;
@@ -267,7 +267,7 @@ fif_status prepare_layout(fif_plan_t p, const int64_t* offsets, const int64_t* o
     if (r == 0 || sigs[(size_t)r - 1].n != (int)n) {
       const int smem = (int)fused_smem_bytes(t->sched);
       const int threads = sched_threads(t->sched);
-      l.classes.push_back(BatchLayout::Cls{(int)r, 0, smem, threads, 0, t->sched.E});
+      l.classes.push_back(BatchLayout::Cls{(int)r, 0, smem, threads, 0, t->sched.E, (int)n});
     }
     l.classes.back().count++;
   }
@@ -367,8 +367,8 @@ fif_status get_large(fif_plan_t p, int64_t n, LargeTables** out) {
   if (!make_large_sched(n, p->smem_optin, lt.G)) return FIF_EUNSUPPORTED;
   LgSched& G = lt.G;
   {
-    // m search: 4 CTAs per SM, at least 2048 bins per CTA
-    const int want = (G.S.P + 2047) / 2048, cap = 4 * (p->num_sms > 0 ? p->num_sms : 1);
+    // m search: at most 4 CTAs per SM, at least 32 bins per thread
+    const int want = (G.S.P + 32 * 256 - 1) / (32 * 256), cap = 4 * (p->num_sms > 0 ? p->num_sms : 1);
     G.sel_blocks = want < cap ? want : cap;
     if (G.sel_blocks > kSelBlocksMax) G.sel_blocks = kSelBlocksMax;
     if (G.sel_blocks < 1) G.sel_blocks = 1;
@@ -540,33 +540,51 @@ fif_status prepare_large(fif_plan_t p, const int64_t* offsets, const int64_t* ou
 // Enqueue every class of the current layout; with more than one class each
 // goes to its own branch stream (fork/join by events), so that independent
 // lengths run side by side (and become parallel branches of a captured graph).
+// Each length class runs on one of kBranches forked streams (parallel
+// branches of the captured graph).  Classes are dealt longest first to the
+// branch with the least estimated work (count * n log2 n, the multi-pass path
+// weighted for its passes through global memory).
 fif_status enqueue_batch(fif_plan_t p, const float* signals, const Outputs& o) {
   const BatchLayout& l = p->layout;
-  const int ncls = (int)(l.classes.size() + l.lcls.size());
+  const int nf = (int)l.classes.size(), ncls = nf + (int)l.lcls.size();
   const bool fork = ncls > 1;
   cudaError_t e = cudaSuccess;
   if (fork) e = cudaEventRecord(p->ev_fork, p->stream);
-  bool used[fif_plan_s::kBranches] = {false};
-  int bi = 0;
-  auto branch = [&]() -> cudaStream_t {
-    if (!fork) return p->stream;
-    const int a = bi++ % fif_plan_s::kBranches;
-    if (!used[a] && e == cudaSuccess) e = cudaStreamWaitEvent(p->aux[a], p->ev_fork, 0);
-    used[a] = true;
-    return p->aux[a];
+  struct Job {
+    double cost;
+    int cls;
   };
-  for (size_t c = 0; c < l.classes.size() && e == cudaSuccess; c++) {
-    const auto& cl = l.classes[c];
-    cudaStream_t s = branch();
-    if (e == cudaSuccess)
-      e = launch_fused(cl.E, l.d_sigs + cl.first, cl.count, l.d_scheds, cl.smem, cl.threads,
-                       cl.grid, p->mp, signals, o, l.d_counters + c, s);
+  std::vector<Job> jobs;
+  for (int c = 0; c < ncls; c++) {
+    const double n = c < nf ? (double)l.classes[c].n : (double)l.lcls[c - nf].n;
+    const double cnt = c < nf ? (double)l.classes[c].count : (double)l.lcls[c - nf].count;
+    jobs.push_back(Job{cnt * n * std::log2(n + 1.0) * (c < nf ? 1.0 : 3.0), c});
   }
-  for (size_t c = 0; c < l.lcls.size() && e == cudaSuccess; c++) {
-    const auto& lc = l.lcls[c];
-    cudaStream_t s = branch();
-    if (e == cudaSuccess) e = cudaMemsetAsync(lc.b->st, 0, sizeof(int) * kLgStateWords * (size_t)lc.count, s);
-    if (e == cudaSuccess) e = large_run(lc.lt->G, lc.b->d_sigs, lc.count, p->mp, signals, o, s);
+  std::stable_sort(jobs.begin(), jobs.end(), [](const Job& a, const Job& b) { return a.cost > b.cost; });
+  double load[fif_plan_s::kBranches] = {0.0};
+  bool used[fif_plan_s::kBranches] = {false};
+  for (const Job& jb : jobs) {
+    if (e != cudaSuccess) break;
+    cudaStream_t s = p->stream;
+    if (fork) {
+      int a = 0;
+      for (int b = 1; b < fif_plan_s::kBranches; b++)
+        if (load[b] < load[a]) a = b;
+      load[a] += jb.cost;
+      if (!used[a]) e = cudaStreamWaitEvent(p->aux[a], p->ev_fork, 0);
+      used[a] = true;
+      s = p->aux[a];
+    }
+    if (e != cudaSuccess) break;
+    if (jb.cls < nf) {
+      const auto& cl = l.classes[jb.cls];
+      e = launch_fused(cl.E, l.d_sigs + cl.first, cl.count, l.d_scheds, cl.smem, cl.threads,
+                       cl.grid, p->mp, signals, o, l.d_counters + jb.cls, s);
+    } else {
+      const auto& lc = l.lcls[jb.cls - nf];
+      e = cudaMemsetAsync(lc.b->st, 0, sizeof(int) * kLgStateWords * (size_t)lc.count, s);
+      if (e == cudaSuccess) e = large_run(lc.lt->G, lc.b->d_sigs, lc.count, p->mp, signals, o, s);
+    }
   }
   if (fork) {
     for (int a = 0; a < fif_plan_s::kBranches && e == cudaSuccess; a++) {

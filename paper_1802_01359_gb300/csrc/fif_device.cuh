@@ -405,7 +405,7 @@ __device__ __forceinline__ void fft_inplace(Cx* buf, const FftSched& S,
 // ------------------------------------------------------------ reductions
 
 struct RedScratch {
-  double d[64];
+  double d[96];
 };
 
 template <typename T, typename Op>
@@ -567,7 +567,6 @@ __device__ __forceinline__ double what64(const FftSched& S, int L, int k) {
 
 struct MSelState {
   float sc;      // power-of-two scale of the spectrum (|sc r_k| <= 1 for every k)
-  float hlmax;   // max log2(1 - w_hat_k) over bins with energy
   int flags;
 };
 
@@ -615,51 +614,16 @@ static __device__ double exact_sd(const float2* spec, const FftSched& S, int L, 
   return den > 0.0 ? sqrt(num / den) : 0.0;
 }
 
-// Error band of the FP32 value of SD_j^2 relative to the binary64 value on
-// the same spectrum (u = 2^-24), for sums built from per-thread chains of at
-// most `chain` terms combined over at most `levels` merge steps.  Each weight
-// is exp2f(e_k - M) with e_k = 2(j-1) log2(1-w_k): the rounding of the table
-// value log2(1-w_k) and of the product and difference in the exponent give at
-// most ln2 u (300 + 8 (j-1) |hlmax|) on every weight above 2^-150, exp2f adds
-// 2 ulp, and the running rescales of the one-pass accumulation (at most one
-// per term of a chain and one per merge step) 2 ulp each; w^2 carries 3u,
-// |r|^2 2u, the summation of positive terms (chain plus merges) and the
-// division the rest.  The band is four times that bound.
-__host__ __device__ __forceinline__ float screen_margin_for(float chain, float levels, int j,
-                                                            float hlmax) {
-  const float u = 5.9604645e-8f;
-  float werr = 0.6931472f * u * (300.f + 8.f * (float)(j - 1) * fabsf(hlmax)) + 4.f * u;
-  werr += 4.f * u * (chain + levels);
-  const float serr = (chain + levels + 2.f) * u;
-  return 4.f * (2.f * werr + 2.f * serr + 8.f * u);
-}
-
-// The band of one CTA's strided pass (ten merge steps: warp and CTA trees).
-__device__ __forceinline__ float screen_margin(const FftSched& S, int j, float hlmax) {
-  const float per_thread = (float)((S.P + (int)blockDim.x - 1) / (int)blockDim.x);
-  return screen_margin_for(per_thread, 10.f, j, hlmax);
-}
-
-// Take the decision SD_j < delta from the FP32 ratio num/den if it lies
-// outside the error band, else re-take it on the binary64 value.
-static __device__ bool decide_sd(float num, float den, const float2* spec, const FftSched& S, int L,
-                                 int j, const MethodParams& mp, MSelState& st, RedScratch* red) {
-  const float margin = screen_margin(S, j, st.hlmax);
-  const float d2 = (float)(mp.delta * mp.delta);
-  const float ratio = num / den;
-  if (den >= 0.5f && ratio == ratio) {
-    if (ratio <= d2 * (1.f - margin)) return true;
-    if (ratio >= d2 * (1.f + margin)) return false;
-  }
-  const double sd = exact_sd(spec, S, L, j, red);
-  st.flags |= FIF_FLAG_FP64_TIEBREAK;
-  if (fabs(sd - mp.delta) <= 1e-6 * mp.delta) st.flags |= FIF_FLAG_NEAR_DELTA_TIE;
-  return sd < mp.delta;
-}
-
+// One-pass sums of the FP32 screen of SD_j, all relative to 2^M: den =
+// sum_k qw_k and num = sum_k qw_k w_k^2 with qw_k the weight of bin k, and the
+// error weights aden = sum_k qw_k |e_k|, anum = sum_k qw_k w_k^2 |e_k|.
 struct Online {
-  float M, num, den;
+  float M, num, den, anum, aden;
 };
+
+// Binades a term may exceed the running reference exponent of the one-pass
+// screen before the sums are rescaled.
+constexpr float kLazyRescale = 32.f;
 
 __device__ __forceinline__ Online online_merge(Online a, Online b) {
   if (a.M < b.M) {
@@ -669,20 +633,135 @@ __device__ __forceinline__ Online online_merge(Online a, Online b) {
   }
   if (b.M == -INFINITY) return a;
   const float s = exp2f(b.M - a.M);
-  return Online{a.M, fmaf(b.num, s, a.num), fmaf(b.den, s, a.den)};
+  return Online{a.M, fmaf(b.num, s, a.num), fmaf(b.den, s, a.den), fmaf(b.anum, s, a.anum),
+                fmaf(b.aden, s, a.aden)};
 }
 
-// FP32 screen of SD_j in one pass over the bins, for any scale of the
-// spectrum: term k is q_k 2^(e_k - M) with q_k = c_k |sc r_k|^2, e_k =
-// 2(j-1) log2(1-w_k) and M the running maximum of e_k + floor(log2 q_k), so the
-// largest term lies in [1, 2) and no term that matters under- or overflows;
-// the running sums are rescaled when M grows.  Also sets st.hlmax.
+// q = qm 2^qe exactly, qe an integer in [-127, 1] for 0 < q < 4: the
+// exponent field of a normal q, and -127 with qm = q 2^127 (normal) for a
+// subnormal one.
+__device__ __forceinline__ void q_split(float q, float& qm, float& qe) {
+  const int b = __float_as_int(q);
+  const int ex = (b >> 23) & 0xff;
+  if (ex != 0) {
+    qm = __int_as_float((b & 0x007fffff) | 0x3f800000);
+    qe = (float)(ex - 127);
+  } else {
+    qm = q * 1.7014118346046923e38f;  // 2^127
+    qe = -127.f;
+  }
+}
+
+// Term k of the screen for any scale of the spectrum: qw_k = qm_k 2^(t_k - M)
+// with q_k = c_k |sc r_k|^2 = qm_k 2^(qe_k), t_k = e_k + qe_k, e_k =
+// 2(j-1) log2(1-w_k), and M a running reference raised to t_k whenever t_k
+// exceeds it by more than kLazyRescale (the sums are rescaled then).  Every
+// term is below 2^(kLazyRescale+1), the largest is at least 2^-22, and no
+// intermediate overflows; a term that underflows is below 2^-126 of the
+// largest.
+__device__ __forceinline__ void sd_term(float qm, float qe, float e, float w2, Online& o) {
+  const float t = e + qe;
+  if (t > o.M + kLazyRescale) {
+    const float s = exp2f(o.M - t);  // 0 when o.M = -inf
+    o.num *= s;
+    o.den *= s;
+    o.anum *= s;
+    o.aden *= s;
+    o.M = t;
+  }
+  const float qw = qm * exp2f(t - o.M);
+  const float qwe = qw * fabsf(e);
+  o.den += qw;
+  o.num = fmaf(qw, w2, o.num);
+  o.aden += qwe;
+  o.anum = fmaf(qwe, w2, o.anum);
+}
+
+// Error band of the FP32 ratio num/den relative to the binary64 SD_j^2 on the
+// same spectrum (u = 2^-24), for sums built from per-thread chains of at most
+// `chain` terms combined over at most `levels` merge steps.
+//
+// The weight of term k is 2^(x_k) qm_k with x_k = (e_k + qe_k) - M computed in
+// FP32 from hl_k = log2(1 - w_hat_k), a table value good to 4u relative
+// (binary64 rounded, or the float-float row of the multi-pass path).  The
+// error of x_k is at most (table) 4u|e_k| + (product 2(j-1) hl_k) u/2 |e_k|
+// + (sum) u/2 (|e_k| + |qe_k|) + (difference) u/2 |x_k| <= 5u|e_k| + 139u
+// (|qe_k| <= 127, |x_k| <= 150 on every term above 2^-150 of the largest),
+// ln2 times that on the weight.  Weighted over the sums this is
+// ln2 u (5 aden/den + 139) for den and ln2 u (5 anum/num + 139) for num,
+// measured on the data (a posteriori).  exp2f adds 2 ulp and the product with
+// qm u/2; each running rescale (at most one per term of a chain and one per
+// merge step) 2 ulp; w^2, |r|^2 and the division 8u together; the summation
+// of positive terms (chain + levels + 2) u per sum.  The band is four times
+// the total.
+__host__ __device__ __forceinline__ float screen_margin(const Online& r, float chain, float levels) {
+  const float u = 5.9604645e-8f, c = 0.6931472f * u;
+  const float ed = r.aden / r.den;
+  const float en = r.num > 0.f ? r.anum / r.num : 0.f;
+  const float resc = 2.5f * u + 4.f * u * (chain + levels);
+  const float wden = c * (5.f * ed + 139.f) + resc;
+  const float wnum = c * (5.f * en + 139.f) + resc;
+  const float serr = (chain + levels + 2.f) * u;
+  return 4.f * (wden + wnum + 2.f * serr + 8.f * u);
+}
+
+// Take the decision SD_j < delta from the FP32 sums if the ratio lies
+// outside their error band, else re-take it on the binary64 value.
+static __device__ bool decide_sd(const Online& r, float chain, float levels, const float2* spec,
+                                 const FftSched& S, int L, int j, const MethodParams& mp,
+                                 MSelState& st, RedScratch* red) {
+  const float d2 = (float)(mp.delta * mp.delta);
+  const float ratio = r.num / r.den;
+  if (r.den >= 0.5f && ratio == ratio) {
+    const float margin = screen_margin(r, chain, levels);
+    if (ratio <= d2 * (1.f - margin)) return true;
+    if (ratio >= d2 * (1.f + margin)) return false;
+  }
+  const double sd = exact_sd(spec, S, L, j, red);
+  st.flags |= FIF_FLAG_FP64_TIEBREAK;
+  if (fabs(sd - mp.delta) <= 1e-6 * mp.delta) st.flags |= FIF_FLAG_NEAR_DELTA_TIE;
+  return sd < mp.delta;
+}
+
+__device__ __forceinline__ Online shfl_xor_online(const Online& o, int off) {
+  return Online{__shfl_xor_sync(0xffffffffu, o.M, off), __shfl_xor_sync(0xffffffffu, o.num, off),
+                __shfl_xor_sync(0xffffffffu, o.den, off), __shfl_xor_sync(0xffffffffu, o.anum, off),
+                __shfl_xor_sync(0xffffffffu, o.aden, off)};
+}
+
+__device__ __forceinline__ Online warp_merge(Online o) {
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) o = online_merge(o, shfl_xor_online(o, off));
+  return o;
+}
+
+// Block-wide merge of the per-thread sums; every thread gets the result.
+__device__ __forceinline__ Online online_block_reduce(Online o, RedScratch* red) {
+  o = warp_merge(o);
+  float* s = reinterpret_cast<float*>(red->d);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  __syncthreads();
+  if (lane == 0) {
+    s[5 * wid] = o.M;
+    s[5 * wid + 1] = o.num;
+    s[5 * wid + 2] = o.den;
+    s[5 * wid + 3] = o.anum;
+    s[5 * wid + 4] = o.aden;
+  }
+  __syncthreads();
+  Online r = lane < nw ? Online{s[5 * lane], s[5 * lane + 1], s[5 * lane + 2], s[5 * lane + 3],
+                                s[5 * lane + 4]}
+                       : Online{-INFINITY, 0.f, 0.f, 0.f, 0.f};
+  return warp_merge(r);
+}
+
+// FP32 screen of SD_j < delta over the bins in one CTA pass (sd_term per
+// bin), then the decision.
 static __device__ bool sd_below(const float2* spec, const FftSched& S, const float2* row, int L,
                                 int j, const MethodParams& mp, MSelState& st, RedScratch* red) {
   const int tid = threadIdx.x, nt = blockDim.x;
   const float e2 = 2.f * (float)(j - 1);
-  Online o{-INFINITY, 0.f, 0.f};
-  float hlmax = -INFINITY;
+  Online o{-INFINITY, 0.f, 0.f, 0.f, 0.f};
   for (int k = tid; k < S.P; k += nt) {
     const float2 z = spec[k];
     if (z.x == 0.f && z.y == 0.f) continue;
@@ -690,49 +769,16 @@ static __device__ bool sd_below(const float2* spec, const FftSched& S, const flo
     const float re = z.x * st.sc, im = z.y * st.sc;
     const float q = parseval_weight(S, k) * fmaf(re, re, im * im);
     if (!(q > 0.f)) continue;
-    hlmax = fmaxf(hlmax, tv.x);
     const float e = (j == 1) ? 0.f : e2 * tv.x;
     if (e == -INFINITY) continue;  // w_hat = 1 (the DC bin): weight 0 for j > 1
-    const float t = e + (float)(((__float_as_int(q) >> 23) & 0xff) - 127);
-    if (t > o.M) {
-      const float s = exp2f(o.M - t);  // 0 when o.M = -inf
-      o.num *= s;
-      o.den *= s;
-      o.M = t;
-    }
-    const float qw = q * exp2f(e - o.M);
-    o.den += qw;
-    o.num = fmaf(qw, tv.y * tv.y, o.num);
+    float qm, qe;
+    q_split(q, qm, qe);
+    sd_term(qm, qe, e, tv.y * tv.y, o);
   }
-#pragma unroll
-  for (int off = 16; off > 0; off >>= 1) {
-    Online b{__shfl_xor_sync(0xffffffffu, o.M, off), __shfl_xor_sync(0xffffffffu, o.num, off),
-             __shfl_xor_sync(0xffffffffu, o.den, off)};
-    o = online_merge(o, b);
-    hlmax = fmaxf(hlmax, __shfl_xor_sync(0xffffffffu, hlmax, off));
-  }
-  float* s = reinterpret_cast<float*>(red->d);
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
-  __syncthreads();
-  if (lane == 0) {
-    s[4 * wid] = o.M;
-    s[4 * wid + 1] = o.num;
-    s[4 * wid + 2] = o.den;
-    s[4 * wid + 3] = hlmax;
-  }
-  __syncthreads();
-  Online r = lane < nw ? Online{s[4 * lane], s[4 * lane + 1], s[4 * lane + 2]}
-                       : Online{-INFINITY, 0.f, 0.f};
-  float hm = lane < nw ? s[4 * lane + 3] : -INFINITY;
-#pragma unroll
-  for (int off = 16; off > 0; off >>= 1) {
-    Online b{__shfl_xor_sync(0xffffffffu, r.M, off), __shfl_xor_sync(0xffffffffu, r.num, off),
-             __shfl_xor_sync(0xffffffffu, r.den, off)};
-    r = online_merge(r, b);
-    hm = fmaxf(hm, __shfl_xor_sync(0xffffffffu, hm, off));
-  }
-  st.hlmax = hm > -INFINITY ? hm : 0.f;
-  return decide_sd(r.num, r.den, spec, S, L, j, mp, st, red);
+  const Online r = online_block_reduce(o, red);
+  // chain: bins per thread; levels: the warp and CTA trees
+  const float chain = (float)((S.P + nt - 1) / nt);
+  return decide_sd(r, chain, 10.f, spec, S, L, j, mp, st, red);
 }
 
 // m = first j in [1, max_inner] with SD_j < delta, else max_inner (eq. SD,
@@ -744,7 +790,6 @@ static __device__ int select_m(const float2* spec, const FftSched& S, int L, con
   const float2* row = wrow(S, L);
   MSelState st;
   st.sc = sc;
-  st.hlmax = 0.f;
   st.flags = 0;
   int m;
   const int jmax = mp.max_inner;
@@ -774,7 +819,6 @@ static __device__ int select_m_on_row(const float2* spec, const FftSched& S, con
                                       RedScratch* red) {
   MSelState st;
   st.sc = sc;
-  st.hlmax = 0.f;
   st.flags = 0;
   int m;
   const int jmax = mp.max_inner;

@@ -109,7 +109,7 @@ struct LgSched {
 // The grid-wide m search evaluates SD_j at up to kSelCand values of j per
 // round; each CTA leaves one partial per candidate (kSelPartBytes each, FP32
 // screen and binary64 tie-break side by side).
-constexpr int kSelCand = 16;
+constexpr int kSelCand = 8;
 constexpr int kSelBlocksMax = 1024;
 constexpr int kSelPartBytes = 48;
 constexpr int kLgStateWords = 32;

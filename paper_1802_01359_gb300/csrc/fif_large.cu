@@ -12,13 +12,14 @@
 //   extrema   extrema and zero-crossing count of r over the whole grid
 //   ctl       one thread per signal: bookkeeping of the last IMF, outer-loop
 //             test (Algorithm 2)
-//   finish    on a stop, the remainder row
 //   row       window eigenvalues {log2(1-w_hat_k), w_hat_k} for this L, in
-//             float-float from sine and reciprocal-sine tables
-//   sel32/64  m by eq. SD: rounds of a 16-way search over j, each an FP32
-//             screen of SD_j at 16 values of j over the whole grid, then a
+//             float-float from sine and reciprocal-sine tables; on a stop,
+//             the remainder row instead
+//   sel32/64  m by eq. SD: rounds of an 8-way search over j, each an FP32
+//             screen of SD_j at 8 values of j over the whole grid, then a
 //             binary64 pass for the values the screen cannot decide; the last
 //             CTA to finish a pass merges the partials and takes the decision
+//             (classes of 8 or more signals: one CTA per signal, bisection)
 //   multiply  IMF_hat = (1-w_hat)^m r_hat, r_hat <- (1 - (1-w_hat)^m) r_hat
 //   presplit  inverse real-transform split
 //   level 1/2 inverse complex FFT
@@ -253,7 +254,7 @@ __global__ void lg_extrema(const LgSig* __restrict__ sigs, LgSched G) {
 
 // Bookkeeping of the IMF extracted in the previous iteration and the outer
 // loop test of Algorithm 2 (one thread per signal).  On a stop the remainder
-// row is written by lg_finish; st[LG_DONE] records the iteration + 1.
+// row is written by lg_row; st[LG_DONE] records the iteration + 1.
 __global__ void lg_ctl(const LgSig* __restrict__ sigs, LgSched G, MethodParams mp, int it,
                        const float* __restrict__ signals, Outputs o) {
   const LgSig sg = sigs[blockIdx.x];
@@ -323,17 +324,6 @@ __global__ void lg_ctl(const LgSig* __restrict__ sigs, LgSched G, MethodParams m
   st[LG_CNT] = 0;
 }
 
-// The remainder row of a signal that stopped in this iteration (a NaN input
-// is its own remainder: lg_pack copied it).
-__global__ void lg_finish(const LgSig* __restrict__ sigs, LgSched G, int it, float* __restrict__ imfs) {
-  const LgSig sg = sigs[blockIdx.y];
-  if (sg.st[LG_DONE] != it + 1) return;
-  const int n = G.S.n;
-  float* orow = imfs + sg.out_off + (size_t)sg.st[LG_K] * n;
-  int step;
-  for (int i = first_signal_point(step); i < n; i += step) orow[i] = sg.rem[i];
-}
-
 // x / L in float-float for an integer 1 <= L < 2^24 (exact in binary32)
 __device__ __forceinline__ ff ff_div_int(ff x, int L) {
   const float fl = (float)L;
@@ -347,12 +337,21 @@ __device__ __forceinline__ ff ff_div_int(ff x, int L) {
 // Window eigenvalues for this IMF's L: w_hat_k = [sin(pi k L/n) / (L sin(pi k/n))]^2
 // (eq. Lambdas for the sampled triangle) in float-float, then rounded:
 // row[k] = {log2(1 - w_hat_k), w_hat_k}.
-__global__ void lg_row(const LgSig* __restrict__ sigs, LgSched G) {
+// A signal that stopped in this iteration instead gets its remainder row
+// (a NaN input is its own remainder: lg_pack copied it).
+__global__ void lg_row(const LgSig* __restrict__ sigs, LgSched G, int it, float* __restrict__ imfs) {
   const LgSig sg = sigs[blockIdx.y];
-  if (sg.st[LG_DONE]) return;
-  const int L = sg.st[LG_L];
   const int n = G.S.n;
   int step;
+  const int done = sg.st[LG_DONE];
+  if (done) {
+    if (done == it + 1) {
+      float* orow = imfs + sg.out_off + (size_t)sg.st[LG_K] * n;
+      for (int i = first_signal_point(step); i < n; i += step) orow[i] = sg.rem[i];
+    }
+    return;
+  }
+  const int L = sg.st[LG_L];
   for (int k = first_signal_point(step); k < G.S.P; k += step) {
     float hl, wf;
     if (k == 0) {
@@ -382,10 +381,10 @@ __global__ void lg_row(const LgSig* __restrict__ sigs, LgSched G) {
 
 // Candidates of round `round` of the search for m = the first j in
 // [1, max_inner] with SD_j < delta (eq. SD, Sec. 4).  Round 0 tests
-// ceil((i+1) max_inner / c), i < c = min(16, max_inner), which includes
+// ceil((i+1) max_inner / c), i < c = min(kSelCand, max_inner), which includes
 // max_inner itself; a later round tests the j strictly inside the bracket
-// (lo, hi) left by the one before: all of them if there are at most 16, else
-// 16 evenly spaced ones.  Candidates are strictly increasing.
+// (lo, hi) left by the one before: all of them if there are at most kSelCand,
+// else kSelCand evenly spaced ones.  Candidates are strictly increasing.
 __host__ __device__ __forceinline__ int sel_count(int lo, int hi, int jmax, int round) {
   if (round == 0) return jmax < kSelCand ? jmax : kSelCand;
   const int u = hi - lo - 1;
@@ -485,39 +484,51 @@ __device__ void sel_commit(int* st, const SelStep& r, int jmax, int flags) {
   st[LG_IFLAGS] |= flags;
 }
 
-template <class T>
-struct OnlineT {
-  T M, num, den;
+// Binary64 one-pass sums of exact_sd's terms relative to 2^M.
+struct OnlineD {
+  double M, num, den;
 };
 
-template <class T>
-__device__ __forceinline__ OnlineT<T> online_merge_t(OnlineT<T> a, OnlineT<T> b) {
+__device__ __forceinline__ OnlineD online_merge_d(OnlineD a, OnlineD b) {
   if (a.M < b.M) {
-    const OnlineT<T> t = a;
+    const OnlineD t = a;
     a = b;
     b = t;
   }
   if (b.M == -INFINITY) return a;
-  const T s = exp2(b.M - a.M);
-  return OnlineT<T>{a.M, b.num * s + a.num, b.den * s + a.den};
+  const double s = exp2(b.M - a.M);
+  return OnlineD{a.M, b.num * s + a.num, b.den * s + a.den};
 }
 
-template <class T>
-__device__ __forceinline__ OnlineT<T> warp_merge(OnlineT<T> o) {
+__device__ __forceinline__ OnlineD warp_merge_d(OnlineD o) {
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) {
-    OnlineT<T> b{__shfl_xor_sync(0xffffffffu, o.M, off), __shfl_xor_sync(0xffffffffu, o.num, off),
-                 __shfl_xor_sync(0xffffffffu, o.den, off)};
-    o = online_merge_t(o, b);
+    OnlineD b{__shfl_xor_sync(0xffffffffu, o.M, off), __shfl_xor_sync(0xffffffffu, o.num, off),
+              __shfl_xor_sync(0xffffffffu, o.den, off)};
+    o = online_merge_d(o, b);
   }
   return o;
 }
 
-__device__ __forceinline__ float4* part32(const LgSig& sg, int b, int i) {
-  return reinterpret_cast<float4*>(sg.part + ((size_t)b * kSelCand + i) * kSelPartBytes);
+// Partial of CTA b for candidate i: the FP32 screen's five sums at offset 0,
+// the binary64 sums at offset 24.
+__device__ __forceinline__ float* part32(const LgSig& sg, int b, int i) {
+  return reinterpret_cast<float*>(sg.part + ((size_t)b * kSelCand + i) * kSelPartBytes);
 }
 __device__ __forceinline__ double* part64(const LgSig& sg, int b, int i) {
-  return reinterpret_cast<double*>(sg.part + ((size_t)b * kSelCand + i) * kSelPartBytes + 16);
+  return reinterpret_cast<double*>(sg.part + ((size_t)b * kSelCand + i) * kSelPartBytes + 24);
+}
+static_assert(kSelPartBytes >= 24 + 3 * 8, "partial record");
+
+__device__ __forceinline__ void store_online(float* p, const Online& o) {
+  p[0] = o.M;
+  p[1] = o.num;
+  p[2] = o.den;
+  p[3] = o.anum;
+  p[4] = o.aden;
+}
+__device__ __forceinline__ Online load_online_cg(const float* p) {
+  return Online{__ldcg(p), __ldcg(p + 1), __ldcg(p + 2), __ldcg(p + 3), __ldcg(p + 4)};
 }
 
 // True in every thread of the last CTA of this signal to reach this point
@@ -536,16 +547,17 @@ __device__ __forceinline__ bool last_to_arrive(int* cnt) {
 }
 
 constexpr int kSelThreads = 256;
+constexpr int kSelCtaMinSignals = 8;
 
 // FP32 screen of SD_j for this round's candidates over the grid: per bin the
-// term of sd_below for each candidate, accumulated online per thread, merged
-// per CTA into sg.part; the last CTA merges the CTAs in index order and
-// classifies each candidate against delta with the error band of this
-// reduction (screen_margin_for).
+// term of sd_below (sd_term) for each candidate, accumulated online per
+// thread, merged per CTA into sg.part; the last CTA merges the CTAs in index
+// order and classifies each candidate against delta with the error band of
+// this reduction (screen_margin).
 __global__ void __launch_bounds__(kSelThreads) lg_sel32(const LgSig* __restrict__ sigs, LgSched G,
                                                          MethodParams mp, int round) {
-  __shared__ float4 wpart[kSelThreads / 32][kSelCand];
-  __shared__ float4 fin[kSelCand];
+  __shared__ Online wpart[kSelThreads / 32][kSelCand];
+  __shared__ Online fin[kSelCand];
   const LgSig sg = sigs[blockIdx.y];
   int* st = sg.st;
   if (st[LG_DONE]) return;
@@ -554,14 +566,13 @@ __global__ void __launch_bounds__(kSelThreads) lg_sel32(const LgSig* __restrict_
   if (c == 0) return;
   const FftSched& S = G.S;
   const float sc = spectrum_scale(S.n, __int_as_float(st[LG_SMAX]));
-  OnlineT<float> o[kSelCand];
+  Online o[kSelCand];
   float e2[kSelCand];
 #pragma unroll
   for (int i = 0; i < kSelCand; i++) {
-    o[i] = OnlineT<float>{-INFINITY, 0.f, 0.f};
+    o[i] = Online{-INFINITY, 0.f, 0.f, 0.f, 0.f};
     e2[i] = i < c ? 2.f * (float)(sel_cand(lo, hi, jmax, round, i) - 1) : 0.f;
   }
-  float hlmax = -INFINITY;
   const int stride = gridDim.x * blockDim.x;
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < S.P; k += stride) {
     const float2 z = sg.spec[k];
@@ -570,81 +581,53 @@ __global__ void __launch_bounds__(kSelThreads) lg_sel32(const LgSig* __restrict_
     const float re = z.x * sc, im = z.y * sc;
     const float q = parseval_weight(S, k) * fmaf(re, re, im * im);
     if (!(q > 0.f)) continue;
-    hlmax = fmaxf(hlmax, tv.x);
-    const float qe = (float)(((__float_as_int(q) >> 23) & 0xff) - 127);
+    float qm, qe;
+    q_split(q, qm, qe);
     const float w2 = tv.y * tv.y;
 #pragma unroll
     for (int i = 0; i < kSelCand; i++) {
       if (i < c) {
         const float e = e2[i] == 0.f ? 0.f : e2[i] * tv.x;
-        if (e != -INFINITY) {  // w_hat = 1 (the DC bin): weight 0 for j > 1
-          const float t = e + qe;
-          if (t > o[i].M) {
-            const float s = exp2f(o[i].M - t);  // 0 when M = -inf
-            o[i].num *= s;
-            o[i].den *= s;
-            o[i].M = t;
-          }
-          const float qw = q * exp2f(e - o[i].M);
-          o[i].den += qw;
-          o[i].num = fmaf(qw, w2, o[i].num);
-        }
+        if (e != -INFINITY) sd_term(qm, qe, e, w2, o[i]);  // w_hat = 1: no weight for j > 1
       }
     }
   }
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
-  for (int off = 16; off > 0; off >>= 1) hlmax = fmaxf(hlmax, __shfl_xor_sync(0xffffffffu, hlmax, off));
-#pragma unroll
   for (int i = 0; i < kSelCand; i++) {
     if (i < c) {
-      const OnlineT<float> r = warp_merge(o[i]);
-      if (lane == 0) wpart[wid][i] = make_float4(r.M, r.num, r.den, hlmax);
+      const Online r = warp_merge(o[i]);
+      if (lane == 0) wpart[wid][i] = r;
     }
   }
   __syncthreads();
   if (threadIdx.x < c) {
     const int i = threadIdx.x;
-    OnlineT<float> r{-INFINITY, 0.f, 0.f};
-    float hm = -INFINITY;
-    for (int w = 0; w < kSelThreads / 32; w++) {
-      const float4 v = wpart[w][i];
-      r = online_merge_t(r, OnlineT<float>{v.x, v.y, v.z});
-      hm = fmaxf(hm, v.w);
-    }
-    *part32(sg, blockIdx.x, i) = make_float4(r.M, r.num, r.den, hm);
+    Online r{-INFINITY, 0.f, 0.f, 0.f, 0.f};
+    for (int w = 0; w < kSelThreads / 32; w++) r = online_merge(r, wpart[w][i]);
+    store_online(part32(sg, blockIdx.x, i), r);
   }
   if (!last_to_arrive(&st[LG_CNT])) return;
   const int nb = gridDim.x;
   for (int i = wid; i < c; i += kSelThreads / 32) {
-    OnlineT<float> r{-INFINITY, 0.f, 0.f};
-    float hm = -INFINITY;
-    for (int b = lane; b < nb; b += 32) {
-      const float4 v = __ldcg(part32(sg, b, i));
-      r = online_merge_t(r, OnlineT<float>{v.x, v.y, v.z});
-      hm = fmaxf(hm, v.w);
-    }
+    Online r{-INFINITY, 0.f, 0.f, 0.f, 0.f};
+    for (int b = lane; b < nb; b += 32) r = online_merge(r, load_online_cg(part32(sg, b, i)));
     r = warp_merge(r);
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) hm = fmaxf(hm, __shfl_xor_sync(0xffffffffu, hm, off));
-    if (lane == 0) fin[i] = make_float4(r.M, r.num, r.den, hm);
+    if (lane == 0) fin[i] = r;
   }
   __syncthreads();
   if (threadIdx.x != 0) return;
-  float hm = -INFINITY;
-  for (int i = 0; i < c; i++) hm = fmaxf(hm, fin[i].w);
-  if (!(hm > -INFINITY)) hm = 0.f;
   // chain: bins per thread, then the warps of a CTA and the CTAs per lane of
   // the final merge; levels: two warp trees
   const float chain = (float)((S.P + stride - 1) / stride + kSelThreads / 32 + (nb + 31) / 32);
   const float d2 = (float)(mp.delta * mp.delta);
   unsigned stat = 0;
   for (int i = 0; i < c; i++) {
-    const int j = sel_cand(lo, hi, jmax, round, i);
-    const float margin = screen_margin_for(chain, 10.f, j, hm);
-    const float ratio = fin[i].y / fin[i].z;
+    const Online& r = fin[i];
+    const float ratio = r.num / r.den;
     unsigned s = SEL_AMB;
-    if (fin[i].z >= 0.5f && ratio == ratio) {
+    if (r.den >= 0.5f && ratio == ratio) {
+      const float margin = screen_margin(r, chain, 10.f);
       if (ratio <= d2 * (1.f - margin)) s = SEL_T;
       else if (ratio >= d2 * (1.f + margin)) s = SEL_F;
     }
@@ -679,7 +662,7 @@ __global__ void __launch_bounds__(kSelThreads) lg_sel64(const LgSig* __restrict_
   for (int i = 0; i < kSelCand; i++) {
     if (!((amb >> i) & 1)) continue;
     const int j = sel_cand(lo, hi, jmax, round, i);
-    OnlineT<double> o{-INFINITY, 0.0, 0.0};
+    OnlineD o{-INFINITY, 0.0, 0.0};
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < S.P; k += stride) {
       const float2 z = sg.spec[k];
       const double q = (double)parseval_weight(S, k) * ((double)z.x * z.x + (double)z.y * z.y);
@@ -698,7 +681,7 @@ __global__ void __launch_bounds__(kSelThreads) lg_sel64(const LgSig* __restrict_
       o.den += t;
       o.num += t * w * w;
     }
-    o = warp_merge(o);
+    o = warp_merge_d(o);
     __syncthreads();
     if (lane == 0) {
       wpart[wid][0] = o.M;
@@ -707,9 +690,9 @@ __global__ void __launch_bounds__(kSelThreads) lg_sel64(const LgSig* __restrict_
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-      OnlineT<double> r{-INFINITY, 0.0, 0.0};
+      OnlineD r{-INFINITY, 0.0, 0.0};
       for (int w = 0; w < kSelThreads / 32; w++)
-        r = online_merge_t(r, OnlineT<double>{wpart[w][0], wpart[w][1], wpart[w][2]});
+        r = online_merge_d(r, OnlineD{wpart[w][0], wpart[w][1], wpart[w][2]});
       double* d = part64(sg, blockIdx.x, i);
       d[0] = r.M;
       d[1] = r.num;
@@ -720,12 +703,12 @@ __global__ void __launch_bounds__(kSelThreads) lg_sel64(const LgSig* __restrict_
   const int nb = gridDim.x;
   for (int i = wid; i < kSelCand; i += kSelThreads / 32) {
     if (!((amb >> i) & 1)) continue;
-    OnlineT<double> r{-INFINITY, 0.0, 0.0};
+    OnlineD r{-INFINITY, 0.0, 0.0};
     for (int b = lane; b < nb; b += 32) {
       const double* d = part64(sg, b, i);
-      r = online_merge_t(r, OnlineT<double>{__ldcg(d), __ldcg(d + 1), __ldcg(d + 2)});
+      r = online_merge_d(r, OnlineD{__ldcg(d), __ldcg(d + 1), __ldcg(d + 2)});
     }
-    r = warp_merge(r);
+    r = warp_merge_d(r);
     if (lane == 0) sd[i] = r.den > 0.0 ? sqrt(r.num / r.den) : 0.0;
   }
   __syncthreads();
@@ -741,6 +724,24 @@ __global__ void __launch_bounds__(kSelThreads) lg_sel64(const LgSig* __restrict_
   SelStep r = sel_update(lo, hi, jmax, round, stat);
   r.amb = 0;  // every candidate that could move the bracket is now decided
   sel_commit(st, r, jmax, flags);
+}
+
+// m by eq. SD with one CTA per signal (bisection over j, select_m_on_row):
+// the least work per signal, for classes with enough signals to fill the GPU.
+__global__ void __launch_bounds__(512, 1) lg_select_cta(const LgSig* __restrict__ sigs, LgSched G,
+                                                        MethodParams mp) {
+  __shared__ RedScratch red;
+  const LgSig sg = sigs[blockIdx.x];
+  int* st = sg.st;
+  if (st[LG_DONE]) return;
+  const int L = st[LG_L];
+  int iflags = st[LG_IFLAGS];
+  const float sc = spectrum_scale(G.S.n, __int_as_float(st[LG_SMAX]));
+  const int m = select_m_on_row(sg.spec, G.S, sg.row, L, mp, sc, iflags, &red);
+  if (threadIdx.x == 0) {
+    st[LG_M] = m;
+    st[LG_IFLAGS] = iflags;
+  }
 }
 
 __global__ void lg_multiply(const LgSig* __restrict__ sigs, LgSched G) {
@@ -931,6 +932,10 @@ cudaError_t large_run(const LgSched& G, const LgSig* d_sigs, int nsig, const Met
   const int bx_split = G.S.odd ? bx_bins : bx_half;
   const int bx_n = (G.S.n + 255) / 256 < 1024 ? (G.S.n + 255) / 256 : 1024;
   const int rounds = large_sel_rounds(mp.max_inner);
+  // The grid-wide search does about three times the work of one bisection
+  // per signal but spreads one signal over the whole GPU: it pays off for
+  // classes of few signals.
+  const bool cta_select = nsig >= kSelCtaMinSignals;
   lg_pack<<<dim3(bx_pts, nsig), 256, 0, st>>>(d_sigs, G, signals);
   cudaError_t e = cudaGetLastError();
   if (e == cudaSuccess) e = launch_level<ffc, false, 1>(G, d_sigs, nsig, st);
@@ -942,11 +947,14 @@ cudaError_t large_run(const LgSched& G, const LgSig* d_sigs, int nsig, const Met
   for (int it = 0; e == cudaSuccess && it <= mp.max_imfs; it++) {
     lg_extrema<<<dim3(bx_n, nsig), 256, 0, st>>>(d_sigs, G);
     lg_ctl<<<nsig, 1, 0, st>>>(d_sigs, G, mp, it, signals, out);
-    lg_finish<<<dim3(bx_n, nsig), 256, 0, st>>>(d_sigs, G, it, out.imfs);
-    lg_row<<<dim3(bx_bins, nsig), 256, 0, st>>>(d_sigs, G);
-    for (int r = 0; r < rounds; r++) {
-      lg_sel32<<<dim3(G.sel_blocks, nsig), kSelThreads, 0, st>>>(d_sigs, G, mp, r);
-      lg_sel64<<<dim3(G.sel_blocks, nsig), kSelThreads, 0, st>>>(d_sigs, G, mp, r);
+    lg_row<<<dim3(bx_bins, nsig), 256, 0, st>>>(d_sigs, G, it, out.imfs);
+    if (cta_select) {
+      lg_select_cta<<<nsig, 512, 0, st>>>(d_sigs, G, mp);
+    } else {
+      for (int r = 0; r < rounds; r++) {
+        lg_sel32<<<dim3(G.sel_blocks, nsig), kSelThreads, 0, st>>>(d_sigs, G, mp, r);
+        lg_sel64<<<dim3(G.sel_blocks, nsig), kSelThreads, 0, st>>>(d_sigs, G, mp, r);
+      }
     }
     lg_multiply<<<dim3(bx_bins, nsig), 256, 0, st>>>(d_sigs, G);
     lg_presplit<<<dim3(bx_split, nsig), 256, 0, st>>>(d_sigs, G);

@@ -138,7 +138,6 @@ __global__ void __launch_bounds__(512, 1) na_select(FftSched S, NaScratch scr, M
   int iflags = st[NA_IFLAGS];
   MSelState ms;
   ms.sc = spectrum_scale(S.n, __int_as_float(st[NA_SMAX]));
-  ms.hlmax = 0.f;
   ms.flags = 0;
   int m;
   const int jmax = mp.max_inner;

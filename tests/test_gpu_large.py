@@ -49,7 +49,10 @@ def test_multipass_and_fused_agree(dev):
         torch.cuda.synchronize()
     for i in range(len(sigs)):
         da, db = ra.signal(i), rb.signal(i)
-        assert da.n_imfs == db.n_imfs and da.status == db.status
+        # FP64_TIEBREAK records which screen decisions went to binary64: it
+        # depends on each path's reduction order, the results do not
+        path_flag = fif.FLAG_FP64_TIEBREAK
+        assert da.n_imfs == db.n_imfs and (da.status & ~path_flag) == (db.status & ~path_flag)
         K = da.n_imfs
         assert np.array_equal(da.m.cpu().numpy()[:K], db.m.cpu().numpy()[:K])
         assert np.array_equal(da.mask_len.cpu().numpy()[:K], db.mask_len.cpu().numpy()[:K])
@@ -172,4 +175,18 @@ def test_multipass_m_search_any_max_inner(dev, oracle_mod, max_inner):
         torch.cuda.synchronize()
     for i, s in enumerate(sigs):
         ref = oracle_mod.direct(s.astype(np.float64), max_imfs=4, max_inner=max_inner, delta=1e-4)
+        parity.compare(res.signal(i), ref)
+
+
+def test_long_classes_of_many_signals_match_oracle(dev, oracle_mod):
+    """Classes of 8 or more long signals take m from one CTA per signal (bisection);
+    smaller classes from the grid-wide search.  Both match the oracle."""
+    lens = [20736] * 8 + [24576] * 9 + [32768] * 2
+    sigs = [signals.component_signal(78, i, n) for i, n in enumerate(lens)]
+    x, offs = _pack(sigs, dev)
+    with fif.Plan(max_n=1 << 15, max_imfs=3) as plan:
+        res = plan.decompose_batch(x, offs, diag=True)
+        torch.cuda.synchronize()
+    for i, s in enumerate(sigs):
+        ref = oracle_mod.direct(s.astype(np.float64), max_imfs=3)
         parity.compare(res.signal(i), ref)

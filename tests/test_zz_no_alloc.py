@@ -31,7 +31,8 @@ def test_noalloc_matches_plan_entry_point_two_calls():
         with fif.Plan(max_n=n) as plan:
             ref = plan.decompose(x, diag=True)
         got = fif.decompose_noalloc(x, diag=True)
-        assert got.n_imfs == ref.n_imfs and got.status == ref.status
+        path_flag = fif.FLAG_FP64_TIEBREAK  # which screen decisions went to binary64
+        assert got.n_imfs == ref.n_imfs and (got.status & ~path_flag) == (ref.status & ~path_flag)
         K = got.n_imfs
         assert np.array_equal(got.m.cpu().numpy()[:K], ref.m.cpu().numpy()[:K])
         assert np.array_equal(got.mask_len.cpu().numpy()[:K], ref.mask_len.cpu().numpy()[:K])
