@@ -106,21 +106,51 @@ bool is_smooth(int64_t n) {
 // Pick elements-per-thread E and the radix passes for a complex FFT of Nc
 // points (Nc = 2^p 3^q).  Every radix must divide E (a thread holds E/R
 // butterflies of one pass in registers); T = Nc/E threads, at most 512.
-bool make_fft_plan(int Nc, FftSched& s) {
+// FFT plan for Nc points: E elements per thread, T = Nc / E threads, radix
+// passes.  The default favours large E (at most 512 threads: the staged,
+// allocation-free and multi-pass kernels).  The wide plan of the fused kernel
+// favours E <= 12 with up to 1024 threads (64 registers a thread, twice the
+// resident warps; its radix-8 and radix-4 passes fit) and falls back to the
+// default order.
+bool make_fft_plan(int Nc, FftSched& s, bool wide = false) {
   int p = 0, q = 0, r = Nc;
   while (r % 2 == 0) r /= 2, p++;
   while (r % 3 == 0) r /= 3, q++;
   if (r != 1) return false;
   static const int prefs[] = {16, 24, 12, 18, 9, 27, 8, 6, 4, 3, 2};
-  for (int E : prefs) {
+  static const int wprefs[] = {8, 12, 6, 9, 16, 24, 18, 27, 4, 3, 2};
+  for (int E : wide ? wprefs : prefs) {
     if (Nc % E) continue;
     if (q > 0 && E % 3) continue;
     if (p > 0 && E % 2) continue;
-    if (Nc / E > 512) continue;
+    if (Nc / E > (wide && E <= kWideMaxE ? 1024 : 512)) continue;
     s.E = E;
     s.T = Nc / E;
     s.npass = 0;
     for (int i = 0; i < q; i++) s.radix[s.npass++] = 3;
+    // 2^p as passes of the main radix RM (largest power of two dividing E, at
+    // most 16) and of RM/2, both kept inline by the kernels: p = a log2(RM) +
+    // b log2(RM/2) with the fewest passes; a single other radix only when no
+    // such split exists.
+    int lm = 0;
+    while (lm < 4 && E % (2 << lm) == 0) lm++;  // RM = 2^lm
+    int a = -1, b = 0;
+    if (lm >= 2) {
+      for (int bb = 0; bb * (lm - 1) <= p; bb++) {
+        const int restp = p - bb * (lm - 1);
+        if (restp % lm == 0) {
+          a = restp / lm;
+          b = bb;
+          break;
+        }
+      }
+    }
+    if (a >= 0) {
+      if (s.npass + a + b > kMaxPass) return false;
+      for (int i = 0; i < a; i++) s.radix[s.npass++] = 1 << lm;
+      for (int i = 0; i < b; i++) s.radix[s.npass++] = 1 << (lm - 1);
+      return true;
+    }
     int rem2 = 1 << p;
     while (rem2 > 1) {
       int R = 2;
@@ -259,15 +289,21 @@ fif_status prepare_layout(fif_plan_t p, const int64_t* offsets, const int64_t* o
     LengthTables* t = nullptr;
     fif_status st = get_tables(p, n, &t);
     if (st != FIF_OK) return st;
+    // the fused kernel's own (wide) FFT plan over the length's tables
+    FftSched fs = t->sched;
+    {
+      FftSched w = fs;
+      if (make_fft_plan(fs.Nc, w, true)) fs = w;
+    }
     if (!sched_idx.count(n)) {
       sched_idx[n] = (int)scheds.size();
-      scheds.push_back(t->sched);
+      scheds.push_back(fs);
     }
     sigs[(size_t)r] = SigDesc{offsets[i], out_offsets[i], sched_idx[n], (int)n, i, 0};
     if (r == 0 || sigs[(size_t)r - 1].n != (int)n) {
-      const int smem = (int)fused_smem_bytes(t->sched);
-      const int threads = sched_threads(t->sched);
-      l.classes.push_back(BatchLayout::Cls{(int)r, 0, smem, threads, 0, t->sched.E, (int)n});
+      const int smem = (int)fused_smem_bytes(fs);
+      const int threads = sched_threads(fs);
+      l.classes.push_back(BatchLayout::Cls{(int)r, 0, smem, threads, 0, fs.E, (int)n});
     }
     l.classes.back().count++;
   }

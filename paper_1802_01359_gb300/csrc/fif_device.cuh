@@ -354,13 +354,17 @@ __device__ __forceinline__ void fft_pass(Cx* buf, const FftSched& S,
   __syncthreads();
 }
 
-// The one pass whose radix is not the schedule's main radix (the host emits
-// at most one such pass per transform).  Kept out of line so that its
-// register needs do not add to the main loop's.
+// The one pass whose radix is neither the schedule's main radix nor half of
+// it (the host emits at most one such pass per transform, and only for
+// power-of-two parts that are not sums of those).  Kept out of line so that
+// its register needs do not add to the main loop's.
 template <class Cx, bool INV, int E>
 __device__ __noinline__ void fft_tail_pass(Cx* buf, const FftSched& S,
                                            const typename TwArg<Cx>::type& tws, int Ns, int R,
                                            int tid) {
+  if constexpr (E % 16 == 0) {
+    if (R == 16) fft_pass<Cx, INV, 16, E>(buf, S, tws, Ns, tid);
+  }
   if constexpr (E % 8 == 0) {
     if (R == 8) fft_pass<Cx, INV, 8, E>(buf, S, tws, Ns, tid);
   }
@@ -379,7 +383,8 @@ __host__ __device__ constexpr int main_radix() {
 
 // Complex FFT of S.Nc points in buf (unnormalised).  Forward: exp(-2 pi i jk/Nc).
 // Every radix of the schedule divides E; all but at most one pass use the
-// main radix (largest power of two dividing E, at most 16) or radix 3.
+// main radix (largest power of two dividing E, at most 16), half of it, or
+// radix 3 (inline); the exception runs out of line.
 // tid is the thread's index among the S.T threads of this transform (several
 // independent transforms may share a CTA); every thread of the CTA calls it.
 template <class Cx, bool INV, int E>
@@ -393,6 +398,10 @@ __device__ __forceinline__ void fft_inplace(Cx* buf, const FftSched& S,
     const int R = S.radix[p];
     if (R == RM) {
       fft_pass<Cx, INV, RM, E>(buf, S, tws, Ns, tid);
+    } else if (sizeof(Cx) == 8 && RM >= 4 && R == RM / 2) {
+      // FP32 transforms (once per IMF) keep the half-radix pass inline; the
+      // float-float forward transform (once per signal) calls it out of line
+      if constexpr (sizeof(Cx) == 8 && RM >= 4) fft_pass<Cx, INV, RM / 2, E>(buf, S, tws, Ns, tid);
     } else if (E % 3 == 0 && R == 3) {
       if constexpr (E % 3 == 0 && RM != 3) fft_pass<Cx, INV, 3, E>(buf, S, tws, Ns, tid);
     } else {

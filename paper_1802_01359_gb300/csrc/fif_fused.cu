@@ -96,7 +96,7 @@ __device__ void decompose_resident(const FftSched& S, const SigDesc& d, int sig,
 }
 
 template <int E>
-__global__ void __launch_bounds__(512, 1) fused_kernel(const SigDesc* __restrict__ sigs, int nsig,
+__global__ void __launch_bounds__(E <= kWideMaxE ? 1024 : 512, 1) fused_kernel(const SigDesc* __restrict__ sigs, int nsig,
                                                     const FftSched* __restrict__ scheds,
                                                     MethodParams mp,
                                                     const float* __restrict__ signals, Outputs out,

@@ -11,6 +11,7 @@ namespace fif {
 constexpr int kMaxPass = 24;     // radix passes per FFT
 constexpr int kEMax = 27;        // complex elements a thread holds during one FFT pass
 constexpr int kMaxImfs = 64;
+constexpr int kWideMaxE = 12;    // fused kernels with E <= kWideMaxE run up to 1024 threads
 
 // FFT and table schedule for one signal length n = 2^a 3^b.
 //   even n: the real transform is a complex FFT of Nc = n/2 points on
