@@ -199,6 +199,21 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def max_over_ranks(seconds: float, dist, device) -> float:
+    """The largest of every rank's timed seconds (each rank's own device clock)."""
+    if dist is None:
+        return seconds
+    import torch
+    t = torch.tensor([seconds], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(samples_per_rank: int, world: int, seconds: float) -> float:
+    """Samples all ranks decomposed (each rank its own batch) per second of the slowest."""
+    return samples_per_rank * world / seconds
+
+
 def oracle_sample(data, offs, idx, threads, params=None):
     """The FP64 oracle (direct method, tier B) on signals idx, one signal per task on a
     thread pool (the C oracle releases the GIL).  Returns (results, seconds)."""
@@ -292,8 +307,12 @@ def main():
     args.warmup = max(args.warmup, 3)
 
     rank = int(os.environ.get("RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", str(args.gpus)))
+    # ranks exist only under torchrun; a plain run is one GPU whatever --gpus says
+    world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.gpus != world and rank == 0:
+        print(f"bench.py: --gpus {args.gpus} but {world} rank(s) launched; timing {world}",
+              file=sys.stderr)
 
     if args.impl == "reference":
         dist = None
@@ -355,13 +374,8 @@ def main():
     if dist is not None:
         dist.barrier()
     step_ms = [a.elapsed_time(b) for a, b in ev]
-    t_total = sum(step_ms) / 1e3
-    if dist is not None:
-        tt = torch.tensor([t_total], dtype=torch.float64, device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_total = float(tt.item())
-    samples_per_step = int(offs[-1]) * world
-    value = samples_per_step * args.steps / t_total
+    t_total = max_over_ranks(sum(step_ms) / 1e3, dist, dev)
+    value = whole_job_rate(int(offs[-1]) * args.steps, world, t_total)
 
     # ---- algorithmic bytes of one step: read s, write K_i IMFs + remainder, ints
     nim = out.n_imfs.cpu().numpy().astype(np.int64)
@@ -388,7 +402,8 @@ def main():
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
                      "peak_kind": f"{peak_kind} HBM copy bandwidth",
-                     "kernel": "fused_kernel<16>" if args.workload == "batch16384" else "whole step",
+                     "kernel": "fused_kernel (one launch per step)" if fused_only
+                     else "whole step (all kernels of the graph)",
                      "alg_bytes_per_launch": alg_bytes},
         "gpu_launches": args.steps,
         "clocks": clk.summary(),
@@ -409,12 +424,9 @@ def main():
         t0 = time.perf_counter()
         for _ in range(e2e_steps):
             plan.decompose_batch_host(h_in, offs, out=h_out)
-        te = time.perf_counter() - t0
-        if dist is not None:
-            tt = torch.tensor([te], dtype=torch.float64, device=dev)
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            te = float(tt.item())
-        result["e2e"] = {"value": samples_per_step * e2e_steps / te, "unit": UNIT,
+        te = max_over_ranks(time.perf_counter() - t0, dist, dev)
+        result["e2e"] = {"value": whole_job_rate(int(offs[-1]) * e2e_steps, world, te),
+                         "unit": UNIT,
                          "h2d_bytes_per_step": int(h_in.nbytes),
                          "d2h_bytes_per_step": int(h_out["imfs"].nbytes + 4 * nsig * (2 * K + 2))}
 
