@@ -303,6 +303,7 @@ def main():
     ap.add_argument("--cpu-sample", type=int, default=48)
     ap.add_argument("--plain-signals", type=int, default=64)
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-tune", action="store_true", help="fixed schedules, no autotuning")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -348,6 +349,14 @@ def main():
     plan = fif.Plan(max_n=int(lens.max()), stream=stream, **params)
     plan.prepare(sorted(set(int(v) for v in lens)))
     out = plan.alloc_batch_outputs(lens, dev)
+    tune_s = None
+    if not args.no_tune:
+        # schedule autotuning per length class, before (and outside) the timed region
+        t0 = time.perf_counter()
+        with torch.cuda.stream(stream):
+            plan.tune(x, offs, out=out)
+        stream.synchronize()
+        tune_s = time.perf_counter() - t0
 
     def step():
         plan.decompose_batch(x, offs, out=out)
@@ -398,6 +407,8 @@ def main():
                    "path": "fused batch (one CTA per signal, shared-memory resident)" if fused_only
                    else "batch: fused for short signals, multi-pass for long ones, one CUDA graph",
                    "l2": f"flushed between steps ({L2_FLUSH_BYTES >> 20} MiB write)",
+                   "schedule": "fixed rule" if tune_s is None
+                   else f"autotuned per length class (fif_plan_tune, {tune_s:.2f} s before timing)",
                    "mean_imfs": float(nim.mean())},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,

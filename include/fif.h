@@ -133,7 +133,10 @@ fif_status fif_plan_prepare(fif_plan_t plan, const int64_t* lengths, int64_t cou
  * staged path: one kernel launch per step of the method per outer iteration
  * (R2C; m selection; multiplier and spectral remainder update; C2R with the
  * remainder update and the extrema count), the remainder spectrum and work
- * arrays staged through the plan's device scratch.
+ * arrays staged through the plan's device scratch.  Lengths whose transform
+ * does not fit one CTA's shared memory (or every length under
+ * FIF_FORCE_MULTIPASS) take the multi-pass path instead: FFTs as two passes
+ * through global memory, the m search spread over the whole GPU.
  *   signal    [n]                      input samples
  *   imfs      [(max_imfs+1) * n]       row K = IMF K, row n_imfs = final remainder;
  *                                      rows after n_imfs are not written
@@ -146,9 +149,15 @@ fif_status fif_plan_prepare(fif_plan_t plan, const int64_t* lengths, int64_t cou
 fif_status fif_decompose(fif_plan_t plan, const float* signal, int64_t n, float* imfs, int32_t* m,
                          int32_t* mask_len, int32_t* n_imfs, int32_t* sig_status, fif_imf_diag* diag);
 
-/* Decompose a batch of independent signals in one fused launch per length
- * class: each CTA keeps a whole signal's spectrum, work array and remainder
- * in shared memory and runs every outer iteration on chip.
+/* Decompose a batch of independent signals of any lengths.  Signals are
+ * grouped by length into classes: lengths up to fif_fused_max_n() run in one
+ * fused launch per class (each CTA keeps a whole signal's spectrum, work
+ * array and remainder in shared memory and runs every outer iteration on
+ * chip); longer ones run the multi-pass path, one sequence of grid-wide
+ * kernels per class.  The first call with a new layout (offsets, pointers,
+ * stream) captures every class's launches into one CUDA graph, the classes on
+ * parallel branches; later calls with the same layout replay it.  Inside a
+ * stream capture of the caller's, the launches are only enqueued.
  *   signals     packed samples; signal i is signals[offsets[i] .. offsets[i+1])
  *   offsets     HOST int64[batch+1], offsets[0] = 0, non-decreasing
  *   imfs        packed outputs; signal i's (max_imfs+1) x n_i block starts at out_offsets[i]
@@ -156,7 +165,7 @@ fif_status fif_decompose(fif_plan_t plan, const float* signal, int64_t n, float*
  *   m, mask_len [batch * max_imfs]   (row i = signal i)
  *   n_imfs, sig_status [batch]
  *   diag        [batch * (max_imfs+1)] or NULL
- * Lengths must be 2^a 3^b with 4 <= n_i <= min(max_n, fif_fused_max_n()).
+ * Lengths must be 2^a 3^b with 4 <= n_i <= max_n.
  * Errors: FIF_EINVAL, FIF_EUNSUPPORTED, FIF_ENOMEM, FIF_ECUDA. */
 fif_status fif_decompose_batch(fif_plan_t plan, const float* signals, const int64_t* offsets,
                                int64_t batch, float* imfs, const int64_t* out_offsets, int32_t* m,
@@ -172,6 +181,36 @@ fif_status fif_decompose_batch_host(fif_plan_t plan, const float* signals, const
                                     int64_t batch, float* imfs, const int64_t* out_offsets,
                                     int32_t* m, int32_t* mask_len, int32_t* n_imfs,
                                     int32_t* sig_status, fif_imf_diag* diag);
+
+/* ---- schedule autotuning per length class ---------------------------------
+ * The fused kernel's FFT schedule (elements per thread E, hence E-point
+ * register butterflies and Nc/E threads per CTA) has one to four valid
+ * choices per length; the library picks one by a fixed rule unless the plan
+ * has been tuned.
+ *
+ * fif_plan_tune runs the batch (same arguments and outputs as
+ * fif_decompose_batch) once per candidate schedule of every fused length
+ * class in it, times each class's launch with CUDA events after a warm-up,
+ * and keeps the fastest schedule per length in the plan; later calls use it.
+ * Results of the last run are left in the outputs (a valid decomposition).
+ * Blocking; not allowed during stream capture (FIF_EINVAL).
+ * Errors: as fif_decompose_batch. */
+fif_status fif_plan_tune(fif_plan_t plan, const float* signals, const int64_t* offsets,
+                         int64_t batch, float* imfs, const int64_t* out_offsets, int32_t* m,
+                         int32_t* mask_len, int32_t* n_imfs, int32_t* sig_status);
+
+/* The fused schedule the plan uses for length n: *E elements per thread,
+ * *threads per CTA, *tuned = 1 if set by tuning or loading, 0 if by the fixed
+ * rule.  FIF_EUNSUPPORTED if n does not take the fused path. */
+fif_status fif_plan_get_schedule(fif_plan_t plan, int64_t n, int32_t* E, int32_t* threads,
+                                 int32_t* tuned);
+
+/* Save the plan's tuned schedules to a text file (HOST path; one line
+ * "n E" per tuned length), or load them from one (lines for lengths or E the
+ * device cannot use are skipped).  Errors: FIF_EINVAL (NULL or unreadable /
+ * unwritable path, malformed line). */
+fif_status fif_plan_save_tuning(fif_plan_t plan, const char* path);
+fif_status fif_plan_load_tuning(fif_plan_t plan, const char* path);
 
 /* ---- allocation-free single-signal entry point ----------------------------
  * The paper has no counterpart to this; it exists for callers of this

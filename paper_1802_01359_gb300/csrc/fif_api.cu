@@ -1,6 +1,7 @@
 // Host side of libfif.so: plan lifetime, per-length schedules and tables,
 // argument validation, and the C entry points declared in include/fif.h.
 #include <math.h>
+#include <stdio.h>
 #include <string.h>
 
 #include <algorithm>
@@ -87,7 +88,9 @@ struct fif_plan_s {
   std::map<int64_t, LargeTables> large;
   std::map<int64_t, LargeBuffers> large_bufs;         // per length, batch layouts
   std::map<int64_t, LargeBuffers> large_single_bufs;  // per length, fif_decompose
-  // branches of the batch graph: one per length class, round robin
+  // fused schedules chosen by fif_plan_tune / fif_plan_load_tuning: n -> E
+  std::map<int64_t, int> fused_E;
+  // branches of the batch graph: one per length class
   static constexpr int kBranches = 8;
   cudaStream_t aux[kBranches] = {nullptr};
   cudaEvent_t ev_fork = nullptr;
@@ -103,54 +106,48 @@ bool is_smooth(int64_t n) {
   return n == 1;
 }
 
-// Pick elements-per-thread E and the radix passes for a complex FFT of Nc
-// points (Nc = 2^p 3^q).  Every radix must divide E (a thread holds E/R
-// butterflies of one pass in registers); T = Nc/E threads, at most 512.
-// FFT plan for Nc points: E elements per thread, T = Nc / E threads, radix
-// passes.  The default favours large E (at most 512 threads: the staged,
-// allocation-free and multi-pass kernels).  The wide plan of the fused kernel
-// favours E <= 12 with up to 1024 threads (64 registers a thread, twice the
-// resident warps; its radix-8 and radix-4 passes fit) and falls back to the
-// default order.
-bool make_fft_plan(int Nc, FftSched& s, bool wide = false) {
+// FFT plan with E elements per thread for a complex FFT of Nc = 2^p 3^q
+// points: T = Nc / E threads (at most max_threads), radix passes that all
+// divide E (a thread holds E/R butterflies of one pass in registers): the
+// radix-3 passes first, then 2^p as passes of the main radix RM (largest power
+// of two dividing E, at most 16) and of RM/2, both kept inline by the kernels
+// (p = a log2(RM) + b log2(RM/2) with the fewest passes); a single other
+// radix only when no such split exists.
+bool plan_with_E(int Nc, int E, int max_threads, FftSched& s) {
   int p = 0, q = 0, r = Nc;
   while (r % 2 == 0) r /= 2, p++;
   while (r % 3 == 0) r /= 3, q++;
-  if (r != 1) return false;
-  static const int prefs[] = {16, 24, 12, 18, 9, 27, 8, 6, 4, 3, 2};
-  static const int wprefs[] = {8, 12, 6, 9, 16, 24, 18, 27, 4, 3, 2};
-  for (int E : wide ? wprefs : prefs) {
-    if (Nc % E) continue;
-    if (q > 0 && E % 3) continue;
-    if (p > 0 && E % 2) continue;
-    if (Nc / E > (wide && E <= kWideMaxE ? 1024 : 512)) continue;
-    s.E = E;
-    s.T = Nc / E;
-    s.npass = 0;
-    for (int i = 0; i < q; i++) s.radix[s.npass++] = 3;
-    // 2^p as passes of the main radix RM (largest power of two dividing E, at
-    // most 16) and of RM/2, both kept inline by the kernels: p = a log2(RM) +
-    // b log2(RM/2) with the fewest passes; a single other radix only when no
-    // such split exists.
-    int lm = 0;
-    while (lm < 4 && E % (2 << lm) == 0) lm++;  // RM = 2^lm
-    int a = -1, b = 0;
-    if (lm >= 2) {
-      for (int bb = 0; bb * (lm - 1) <= p; bb++) {
-        const int restp = p - bb * (lm - 1);
-        if (restp % lm == 0) {
-          a = restp / lm;
-          b = bb;
-          break;
-        }
+  if (r != 1 || E < 2 || Nc % E) return false;
+  if (q > 0 && E % 3) return false;
+  if (p > 0 && E % 2) return false;
+  if (E % 2 && E % 3) return false;
+  if (Nc / E > max_threads) return false;
+  bool known = false;
+  for (int k : {2, 3, 4, 6, 8, 9, 12, 16, 18, 24, 27}) known |= k == E;
+  if (!known) return false;  // the kernels are instantiated for these E only
+  FftSched t = s;
+  t.E = E;
+  t.T = Nc / E;
+  t.npass = 0;
+  for (int i = 0; i < q; i++) t.radix[t.npass++] = 3;
+  int lm = 0;
+  while (lm < 4 && E % (2 << lm) == 0) lm++;  // RM = 2^lm
+  int a = -1, b = 0;
+  if (lm >= 2) {
+    for (int bb = 0; bb * (lm - 1) <= p; bb++) {
+      const int restp = p - bb * (lm - 1);
+      if (restp % lm == 0) {
+        a = restp / lm;
+        b = bb;
+        break;
       }
     }
-    if (a >= 0) {
-      if (s.npass + a + b > kMaxPass) return false;
-      for (int i = 0; i < a; i++) s.radix[s.npass++] = 1 << lm;
-      for (int i = 0; i < b; i++) s.radix[s.npass++] = 1 << (lm - 1);
-      return true;
-    }
+  }
+  if (a >= 0) {
+    if (t.npass + a + b > kMaxPass) return false;
+    for (int i = 0; i < a; i++) t.radix[t.npass++] = 1 << lm;
+    for (int i = 0; i < b; i++) t.radix[t.npass++] = 1 << (lm - 1);
+  } else {
     int rem2 = 1 << p;
     while (rem2 > 1) {
       int R = 2;
@@ -160,13 +157,42 @@ bool make_fft_plan(int Nc, FftSched& s, bool wide = false) {
           break;
         }
       }
-      if (s.npass >= kMaxPass) return false;
-      s.radix[s.npass++] = R;
+      if (t.npass >= kMaxPass) return false;
+      t.radix[t.npass++] = R;
       rem2 /= R;
     }
-    return true;
   }
+  s = t;
+  return true;
+}
+
+// Largest thread count a fused kernel with E elements per thread may run.
+int fused_max_threads(int E) { return E <= kWideMaxE ? 1024 : 512; }
+
+// Default FFT plan.  The default order favours large E (at most 512 threads:
+// the staged, allocation-free and multi-pass kernels).  The wide order of the
+// fused kernel favours E <= 12 with up to 1024 threads (64 registers a
+// thread, twice the resident warps; its radix-8 and radix-4 passes fit) and
+// falls back to the default order.
+bool make_fft_plan(int Nc, FftSched& s, bool wide = false) {
+  static const int prefs[] = {16, 24, 12, 18, 9, 27, 8, 6, 4, 3, 2};
+  static const int wprefs[] = {8, 12, 6, 9, 16, 24, 18, 27, 4, 3, 2};
+  for (int E : wide ? wprefs : prefs)
+    if (plan_with_E(Nc, E, wide ? fused_max_threads(E) : 512, s)) return true;
   return false;
+}
+
+// The fused kernel's schedule for one length: the tuned E if the plan has
+// one, else the wide default, else the length's own plan.
+bool fused_plan(const fif_plan_s* p, const FftSched& base, FftSched& out) {
+  out = base;
+  auto it = p->fused_E.find(base.n);
+  if (it != p->fused_E.end() && plan_with_E(base.Nc, it->second, fused_max_threads(it->second), out))
+    return true;
+  out = base;
+  FftSched w = base;
+  if (make_fft_plan(base.Nc, w, true)) out = w;
+  return true;
 }
 
 // smem_limit: shared memory per block the fused kernel may use; the folded
@@ -289,12 +315,9 @@ fif_status prepare_layout(fif_plan_t p, const int64_t* offsets, const int64_t* o
     LengthTables* t = nullptr;
     fif_status st = get_tables(p, n, &t);
     if (st != FIF_OK) return st;
-    // the fused kernel's own (wide) FFT plan over the length's tables
+    // the fused kernel's own FFT plan over the length's tables
     FftSched fs = t->sched;
-    {
-      FftSched w = fs;
-      if (make_fft_plan(fs.Nc, w, true)) fs = w;
-    }
+    fused_plan(p, t->sched, fs);
     if (!sched_idx.count(n)) {
       sched_idx[n] = (int)scheds.size();
       scheds.push_back(fs);
@@ -646,6 +669,28 @@ bool layout_matches(fif_plan_t p, const int64_t* offsets, const int64_t* out_off
          std::equal(l.out_offsets.begin(), l.out_offsets.end(), out_offsets);
 }
 
+// ---- schedule autotuning helpers ---------------------------------------------------
+
+// Fused schedules a length may use, the default first.
+std::vector<FftSched> fused_candidates(const LengthTables& t) {
+  std::vector<FftSched> out;
+  FftSched first = t.sched;
+  if (make_fft_plan(t.sched.Nc, first, true)) out.push_back(first);
+  for (int E : {2, 3, 4, 6, 8, 9, 12, 16, 18, 24, 27}) {
+    FftSched c = t.sched;
+    if (!plan_with_E(t.sched.Nc, E, fused_max_threads(E), c)) continue;
+    if (!out.empty() && c.E == out[0].E) continue;
+    if (fused_blocks_per_sm(c.E, (int)fused_smem_bytes(c), sched_threads(c)) <= 0) continue;
+    out.push_back(c);
+  }
+  return out;
+}
+
+void drop_layout(fif_plan_t p) {
+  free_layout(p->layout);
+  p->layout_valid = false;
+}
+
 }  // namespace
 
 extern "C" {
@@ -929,6 +974,135 @@ fif_status fif_decompose_batch_host(fif_plan_t p, const float* signals, const in
   if (e == cudaSuccess && diag) e = cudaMemcpyAsync(diag, d_diag, dg_b, cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   return cuda_status(e);
+}
+
+fif_status fif_plan_tune(fif_plan_t p, const float* signals, const int64_t* offsets, int64_t batch,
+                         float* imfs, const int64_t* out_offsets, int32_t* m, int32_t* mask_len,
+                         int32_t* n_imfs, int32_t* sig_status) {
+  fif_status st = check_batch(p, signals, offsets, batch, imfs, out_offsets, m, mask_len, n_imfs,
+                              sig_status);
+  if (st != FIF_OK || batch == 0) return st;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(p->stream, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone)
+    return FIF_EINVAL;
+  cudaGetLastError();
+  std::vector<int> fused;
+  std::map<int64_t, std::vector<FftSched>> cands;
+  for (int64_t i = 0; i < batch; i++) {
+    const int64_t n = offsets[i + 1] - offsets[i];
+    if (!fits_fused(p, n)) continue;
+    fused.push_back((int)i);
+    if (!cands.count(n)) {
+      LengthTables* t = nullptr;
+      st = get_tables(p, n, &t);
+      if (st != FIF_OK) return st;
+      cands[n] = fused_candidates(*t);
+    }
+  }
+  size_t rounds = 0;
+  for (const auto& kv : cands) rounds = std::max(rounds, kv.second.size());
+  std::map<int64_t, std::pair<float, int>> best;  // n -> (ms, E)
+  Outputs o{imfs, m, mask_len, n_imfs, sig_status, nullptr};
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  for (size_t r = 0; r < rounds && e == cudaSuccess && st == FIF_OK; r++) {
+    // round r: every length takes its r-th candidate (or keeps its last one)
+    for (const auto& kv : cands) {
+      if (kv.second.empty()) continue;
+      p->fused_E[kv.first] = kv.second[std::min(r, kv.second.size() - 1)].E;
+    }
+    drop_layout(p);
+    st = prepare_layout(p, offsets, out_offsets, batch, fused);
+    if (st != FIF_OK) break;
+    const BatchLayout& l = p->layout;
+    for (size_t c = 0; c < l.classes.size() && e == cudaSuccess; c++) {
+      const auto& cl = l.classes[c];
+      const auto& cv = cands[cl.n];
+      if (r > 0 && r >= cv.size()) continue;  // nothing new for this length
+      float best_ms = 0.f;
+      for (int rep = 0; rep < 3 && e == cudaSuccess; rep++) {  // one warm-up, two timed
+        e = cudaEventRecord(e0, p->stream);
+        if (e == cudaSuccess)
+          e = launch_fused(cl.E, l.d_sigs + cl.first, cl.count, l.d_scheds, cl.smem, cl.threads,
+                           cl.grid, p->mp, signals, o, l.d_counters + c, p->stream);
+        if (e == cudaSuccess) e = cudaEventRecord(e1, p->stream);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float ms = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (rep == 1 || (rep == 2 && ms < best_ms)) best_ms = ms;
+      }
+      auto b = best.find(cl.n);
+      if (e == cudaSuccess && (b == best.end() || best_ms < b->second.first))
+        best[cl.n] = std::make_pair(best_ms, cl.E);
+    }
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  for (const auto& kv : best) p->fused_E[kv.first] = kv.second.second;
+  drop_layout(p);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return cuda_status(e);
+  }
+  if (st != FIF_OK) return st;
+  return fif_decompose_batch(p, signals, offsets, batch, imfs, out_offsets, m, mask_len, n_imfs,
+                             sig_status, nullptr);
+}
+
+fif_status fif_plan_get_schedule(fif_plan_t p, int64_t n, int32_t* E, int32_t* threads,
+                                 int32_t* tuned) {
+  if (!p || !E || !threads || !tuned) return FIF_EINVAL;
+  if (n < 4 || n > p->desc.max_n || !is_smooth(n)) return FIF_EUNSUPPORTED;
+  if (!fits_fused(p, n)) return FIF_EUNSUPPORTED;
+  LengthTables* t = nullptr;
+  const fif_status st = get_tables(p, n, &t);
+  if (st != FIF_OK) return st;
+  FftSched fs;
+  fused_plan(p, t->sched, fs);
+  *E = fs.E;
+  *threads = sched_threads(fs);
+  *tuned = p->fused_E.count(n) ? 1 : 0;
+  return FIF_OK;
+}
+
+fif_status fif_plan_save_tuning(fif_plan_t p, const char* path) {
+  if (!p || !path) return FIF_EINVAL;
+  FILE* f = fopen(path, "w");
+  if (!f) return FIF_EINVAL;
+  for (const auto& kv : p->fused_E) fprintf(f, "%lld %d\n", (long long)kv.first, kv.second);
+  return fclose(f) == 0 ? FIF_OK : FIF_EINVAL;
+}
+
+fif_status fif_plan_load_tuning(fif_plan_t p, const char* path) {
+  if (!p || !path) return FIF_EINVAL;
+  FILE* f = fopen(path, "r");
+  if (!f) return FIF_EINVAL;
+  std::map<int64_t, int> got;
+  char line[256];
+  fif_status st = FIF_OK;
+  while (fgets(line, sizeof line, f)) {
+    long long n = 0;
+    int E = 0;
+    char extra = 0;
+    const int k = sscanf(line, " %lld %d %c", &n, &E, &extra);
+    if (k == EOF || (k <= 0 && line[strspn(line, " \t\r\n")] == 0)) continue;  // blank
+    if (k != 2) {
+      st = FIF_EINVAL;
+      break;
+    }
+    if (n < 4 || n > p->desc.max_n || !is_smooth(n) || !fits_fused(p, n)) continue;
+    FftSched base, c;
+    if (!make_sched(n, base, p->smem_optin)) continue;
+    c = base;
+    if (!plan_with_E(base.Nc, E, fused_max_threads(E), c)) continue;
+    got[(int64_t)n] = E;
+  }
+  fclose(f);
+  if (st != FIF_OK) return st;
+  for (const auto& kv : got) p->fused_E[kv.first] = kv.second;
+  drop_layout(p);
+  return FIF_OK;
 }
 
 }  // extern "C"

@@ -39,7 +39,8 @@ FORCE_MULTIPASS = 2
 # every symbol include/fif.h declares
 EXPORTS = ("fif_plan_create", "fif_plan_destroy", "fif_plan_set_stream", "fif_plan_prepare",
            "fif_decompose", "fif_decompose_batch", "fif_decompose_batch_host", "fif_fused_max_n",
-           "fif_status_string", "fif_decompose_noalloc")
+           "fif_status_string", "fif_decompose_noalloc", "fif_plan_tune", "fif_plan_get_schedule",
+           "fif_plan_save_tuning", "fif_plan_load_tuning")
 NOALLOC_MAX_N = 16384
 
 
@@ -92,8 +93,14 @@ def load_library(path: str = LIB_PATH):
     lib.fif_fused_max_n.restype = ctypes.c_int64
     lib.fif_status_string.argtypes = [ctypes.c_int]
     lib.fif_status_string.restype = ctypes.c_char_p
+    lib.fif_plan_tune.argtypes = [vp, fp, i64p, ctypes.c_int64, fp, i64p, i32p, i32p, i32p, i32p]
+    lib.fif_plan_get_schedule.argtypes = [vp, ctypes.c_int64, i32p, i32p, i32p]
+    lib.fif_plan_save_tuning.argtypes = [vp, ctypes.c_char_p]
+    lib.fif_plan_load_tuning.argtypes = [vp, ctypes.c_char_p]
     for name in ("fif_plan_create", "fif_plan_destroy", "fif_plan_set_stream", "fif_plan_prepare",
-                 "fif_decompose", "fif_decompose_batch", "fif_decompose_batch_host"):
+                 "fif_decompose", "fif_decompose_batch", "fif_decompose_batch_host",
+                 "fif_plan_tune", "fif_plan_get_schedule", "fif_plan_save_tuning",
+                 "fif_plan_load_tuning"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -277,6 +284,37 @@ class Plan:
             _ptr(out.m), _ptr(out.mask_len), _ptr(out.n_imfs), _ptr(out.status), _ptr(out.diag)),
             "fif_decompose_batch")
         return out
+
+    def tune(self, signals, offsets, out: Optional[BatchResult] = None) -> BatchResult:
+        """Autotune the fused schedule of every fused length class of this batch (see
+        fif_plan_tune); returns the outputs of the final run with the chosen schedules."""
+        import torch
+        assert signals.is_cuda and signals.dtype == torch.float32
+        offsets = np.ascontiguousarray(np.asarray(offsets, dtype=np.int64))
+        lengths = np.diff(offsets)
+        if out is None:
+            out = self.alloc_batch_outputs(lengths, signals.device)
+        oo = np.ascontiguousarray(out.out_offsets)
+        _check(load_library().fif_plan_tune(
+            self._h, _ptr(signals), _np_ptr(offsets), lengths.size, _ptr(out.imfs), _np_ptr(oo),
+            _ptr(out.m), _ptr(out.mask_len), _ptr(out.n_imfs), _ptr(out.status)), "fif_plan_tune")
+        return out
+
+    def schedule(self, n: int) -> tuple:
+        """(E, threads, tuned) of the fused schedule for length n."""
+        E, T, tuned = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+        _check(load_library().fif_plan_get_schedule(self._h, int(n), ctypes.byref(E),
+                                                    ctypes.byref(T), ctypes.byref(tuned)),
+               "fif_plan_get_schedule")
+        return E.value, T.value, bool(tuned.value)
+
+    def save_tuning(self, path: str):
+        _check(load_library().fif_plan_save_tuning(self._h, os.fsencode(path)),
+               "fif_plan_save_tuning")
+
+    def load_tuning(self, path: str):
+        _check(load_library().fif_plan_load_tuning(self._h, os.fsencode(path)),
+               "fif_plan_load_tuning")
 
     def decompose_batch_host(self, signals: np.ndarray, offsets, mask_len=None,
                              diag: bool = False, out: Optional[dict] = None) -> BatchResult:

@@ -92,3 +92,13 @@ def test_out_layout():
     import numpy as np
     assert fif.out_layout([4, 6, 8], 2).tolist() == [0, 12, 30]
     assert np.array_equal(fif.out_layout([], 3), np.zeros(0, dtype=np.int64))
+
+
+def test_tuning_entry_points_reject_null_arguments(lib):
+    i32 = ctypes.c_int32()
+    assert lib.fif_plan_tune(None, None, None, 1, None, None, None, None, None, None) == \
+        fif.FIF_EINVAL
+    assert lib.fif_plan_get_schedule(None, 4096, ctypes.byref(i32), ctypes.byref(i32),
+                                     ctypes.byref(i32)) == fif.FIF_EINVAL
+    assert lib.fif_plan_save_tuning(None, b"/nonexistent/x") == fif.FIF_EINVAL
+    assert lib.fif_plan_load_tuning(None, b"/nonexistent/x") == fif.FIF_EINVAL
