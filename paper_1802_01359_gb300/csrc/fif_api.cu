@@ -730,6 +730,7 @@ fif_status fif_plan_create(fif_plan_t* out, const fif_plan_desc* desc, void* cud
   p->desc = *desc;
   p->mp.nu = desc->nu;
   p->mp.delta = desc->delta;
+  p->mp.delta2 = (float)(desc->delta * desc->delta);
   p->mp.mask_scale = desc->mask_scale;
   p->mp.max_inner = desc->max_inner;
   p->mp.max_imfs = desc->max_imfs;

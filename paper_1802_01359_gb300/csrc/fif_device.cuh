@@ -634,6 +634,9 @@ struct Online {
 // screen before the sums are rescaled.
 constexpr float kLazyRescale = 32.f;
 
+// Bins whose loads a thread issues together in the screen and the multiplier.
+constexpr int kSdBatch = 4;
+
 __device__ __forceinline__ Online online_merge(Online a, Online b) {
   if (a.M < b.M) {
     const Online t = a;
@@ -719,7 +722,7 @@ __host__ __device__ __forceinline__ float screen_margin(const Online& r, float c
 static __device__ bool decide_sd(const Online& r, float chain, float levels, const float2* spec,
                                  const FftSched& S, int L, int j, const MethodParams& mp,
                                  MSelState& st, RedScratch* red) {
-  const float d2 = (float)(mp.delta * mp.delta);
+  const float d2 = mp.delta2;
   const float ratio = r.num / r.den;
   if (r.den >= 0.5f && ratio == ratio) {
     const float margin = screen_margin(r, chain, levels);
@@ -771,18 +774,28 @@ static __device__ bool sd_below(const float2* spec, const FftSched& S, const flo
   const int tid = threadIdx.x, nt = blockDim.x;
   const float e2 = 2.f * (float)(j - 1);
   Online o{-INFINITY, 0.f, 0.f, 0.f, 0.f};
-  for (int k = tid; k < S.P; k += nt) {
-    const float2 z = spec[k];
-    if (z.x == 0.f && z.y == 0.f) continue;
-    const float2 tv = __ldg(&row[k]);
-    const float re = z.x * st.sc, im = z.y * st.sc;
-    const float q = parseval_weight(S, k) * fmaf(re, re, im * im);
-    if (!(q > 0.f)) continue;
-    const float e = (j == 1) ? 0.f : e2 * tv.x;
-    if (e == -INFINITY) continue;  // w_hat = 1 (the DC bin): weight 0 for j > 1
-    float qm, qe;
-    q_split(q, qm, qe);
-    sd_term(qm, qe, e, tv.y * tv.y, o);
+  // kSdBatch bins per step, their loads issued together (the row lives in
+  // global memory or L2 for most callers)
+  for (int k0 = tid; k0 < S.P; k0 += kSdBatch * nt) {
+    float2 z[kSdBatch], tv[kSdBatch];
+#pragma unroll
+    for (int u = 0; u < kSdBatch; u++) {
+      const int k = k0 + u * nt;
+      z[u] = k < S.P ? spec[k] : make_float2(0.f, 0.f);
+      tv[u] = k < S.P ? row[k] : make_float2(0.f, 0.f);  // global (plan table, multi-pass row)
+    }
+#pragma unroll
+    for (int u = 0; u < kSdBatch; u++) {
+      const int k = k0 + u * nt;
+      const float re = z[u].x * st.sc, im = z[u].y * st.sc;
+      const float q = parseval_weight(S, k) * fmaf(re, re, im * im);
+      if (!(q > 0.f)) continue;  // also zero bins and bins past the end
+      const float e = (j == 1) ? 0.f : e2 * tv[u].x;
+      if (e == -INFINITY) continue;  // w_hat = 1 (the DC bin): weight 0 for j > 1
+      float qm, qe;
+      q_split(q, qm, qe);
+      sd_term(qm, qe, e, tv[u].y * tv[u].y, o);
+    }
   }
   const Online r = online_block_reduce(o, red);
   // chain: bins per thread; levels: the warp and CTA trees
@@ -862,12 +875,24 @@ __device__ __forceinline__ void multiplier(int m, float hl, float& g, float& omg
 // (Algorithm 2: s = s - s_m).
 static __device__ void apply_multiplier(float2* spec, float2* work, const FftSched& S, int L, int m) {
   const float2* row = wrow(S, L);
-  for (int k = threadIdx.x; k < S.P; k += blockDim.x) {
-    const float2 z = spec[k];
-    float g, omg;
-    multiplier(m, __ldg(&row[k]).x, g, omg);
-    work[k] = make_float2(g * z.x, g * z.y);
-    spec[k] = make_float2(omg * z.x, omg * z.y);
+  const int nt = blockDim.x;
+  for (int k0 = threadIdx.x; k0 < S.P; k0 += kSdBatch * nt) {
+    float hl[kSdBatch];
+#pragma unroll
+    for (int u = 0; u < kSdBatch; u++) {
+      const int k = k0 + u * nt;
+      hl[u] = k < S.P ? __ldg(&row[k].x) : 0.f;
+    }
+#pragma unroll
+    for (int u = 0; u < kSdBatch; u++) {
+      const int k = k0 + u * nt;
+      if (k >= S.P) break;
+      const float2 z = spec[k];
+      float g, omg;
+      multiplier(m, hl[u], g, omg);
+      work[k] = make_float2(g * z.x, g * z.y);
+      spec[k] = make_float2(omg * z.x, omg * z.y);
+    }
   }
   __syncthreads();
 }
@@ -976,15 +1001,45 @@ static __device__ EpiOut epilogue_extrema_even(const float2* work, float* rem, f
     const float r3 = rem[s0 + 3 >= n ? s0 + 3 - n : s0 + 3];
     pair_terms(rm1, r0, r1, r2, r3, tau, ext, zc, tie);
   }
-  tie = __syncthreads_or(tie);
+  // one block-wide merge of the five results (two barriers)
   float fe = (float)ext, fz = (float)zc;  // exact: counts < 2^24
-  block_reduce2(fe, fz, OpAdd(), 0.f, red);
-  block_reduce2(imax, rmax, OpMax(), 0.f, red);
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    fe += __shfl_xor_sync(0xffffffffu, fe, off);
+    fz += __shfl_xor_sync(0xffffffffu, fz, off);
+    imax = fmaxf(imax, __shfl_xor_sync(0xffffffffu, imax, off));
+    rmax = fmaxf(rmax, __shfl_xor_sync(0xffffffffu, rmax, off));
+  }
+  tie = __any_sync(0xffffffffu, tie);
+  float* sm = reinterpret_cast<float*>(red->d);
+  const int wid = tid >> 5, nw = (nt + 31) >> 5;
+  __syncthreads();
+  if (lane == 0) {
+    sm[5 * wid] = fe;
+    sm[5 * wid + 1] = fz;
+    sm[5 * wid + 2] = imax;
+    sm[5 * wid + 3] = rmax;
+    sm[5 * wid + 4] = tie ? 1.f : 0.f;
+  }
+  __syncthreads();
+  fe = lane < nw ? sm[5 * lane] : 0.f;
+  fz = lane < nw ? sm[5 * lane + 1] : 0.f;
+  imax = lane < nw ? sm[5 * lane + 2] : 0.f;
+  rmax = lane < nw ? sm[5 * lane + 3] : 0.f;
+  float ft = lane < nw ? sm[5 * lane + 4] : 0.f;
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    fe += __shfl_xor_sync(0xffffffffu, fe, off);
+    fz += __shfl_xor_sync(0xffffffffu, fz, off);
+    imax = fmaxf(imax, __shfl_xor_sync(0xffffffffu, imax, off));
+    rmax = fmaxf(rmax, __shfl_xor_sync(0xffffffffu, rmax, off));
+    ft = fmaxf(ft, __shfl_xor_sync(0xffffffffu, ft, off));
+  }
   EpiOut o;
   o.imax = imax;
   o.k = (int)fe;
   o.zc = (int)fz;
-  o.tie = tie;
+  o.tie = ft > 0.f;
   o.rmax = rmax;
   return o;
 }

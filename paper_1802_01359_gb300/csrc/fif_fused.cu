@@ -10,6 +10,7 @@ struct FusedShared {
   FftSched S;
   RedScratch red;
   int sig;
+  int ot[3];  // outer test result broadcast: reason, L, flags
 };
 static_assert(sizeof(FusedShared) + 16 <= 1024, "fused_smem_bytes reserves 1 KiB for the header");
 
@@ -19,7 +20,7 @@ template <int E>
 __device__ void decompose_resident(const FftSched& S, const SigDesc& d, int sig,
                                    const MethodParams& mp, const float* __restrict__ signals,
                                    const Outputs& out, float2* spec, float2* work, float* rem,
-                                   ffc* zf, float2* smtw, RedScratch* red) {
+                                   ffc* zf, float2* smtw, RedScratch* red, int* ot) {
   const int n = S.n, tid = threadIdx.x, nt = blockDim.x;
   const float* x = signals + d.in_off;
   float* orow = out.imfs + d.out_off;
@@ -50,8 +51,17 @@ __device__ void decompose_resident(const FftSched& S, const SigDesc& d, int sig,
   e.tie = 0;  // the input itself is exact on both sides
   int K = 0, flags = 0, reason = 0;
   for (;;) {
+    // the outer test (binary64 division) on one thread, broadcast
     int L = 0, iflags = e.tie ? FIF_FLAG_EXTREMA_TIE : 0;
-    reason = outer_test(e.k, K, n, mp, L_io, L, iflags);
+    if (tid == 0) {
+      ot[0] = outer_test(e.k, K, n, mp, L_io, L, iflags);
+      ot[1] = L;
+      ot[2] = iflags;
+    }
+    __syncthreads();
+    reason = ot[0];
+    L = ot[1];
+    iflags = ot[2];
     if (dg && tid == 0) {
       dg[K].k_extrema = e.k;
       dg[K].zero_crossings = e.zc;
@@ -118,7 +128,7 @@ __global__ void __launch_bounds__(E <= kWideMaxE ? 1024 : 512, 1) fused_kernel(c
     float2* spec = work + work_points(S);
     ffc* zf = reinterpret_cast<ffc*>(dyn);
     float2* smtw = S.tw_shared ? spec + S.P : nullptr;
-    decompose_resident<E>(S, d, d.idx, mp, signals, out, spec, work, rem, zf, smtw, &sh->red);
+    decompose_resident<E>(S, d, d.idx, mp, signals, out, spec, work, rem, zf, smtw, &sh->red, sh->ot);
     __syncthreads();
   }
 }

@@ -42,6 +42,7 @@ struct FftSched {
 struct MethodParams {
   double nu;
   double delta;
+  float delta2;                // (float)(delta * delta), set on the host
   int mask_scale;
   int max_inner;
   int max_imfs;

@@ -620,7 +620,7 @@ __global__ void __launch_bounds__(kSelThreads) lg_sel32(const LgSig* __restrict_
   // chain: bins per thread, then the warps of a CTA and the CTAs per lane of
   // the final merge; levels: two warp trees
   const float chain = (float)((S.P + stride - 1) / stride + kSelThreads / 32 + (nb + 31) / 32);
-  const float d2 = (float)(mp.delta * mp.delta);
+  const float d2 = mp.delta2;
   unsigned stat = 0;
   for (int i = 0; i < c; i++) {
     const Online& r = fin[i];

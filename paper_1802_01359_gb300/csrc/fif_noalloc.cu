@@ -372,6 +372,7 @@ extern "C" fif_status fif_decompose_noalloc(const fif_plan_desc* d, const float*
   MethodParams mp;
   mp.nu = d->nu;
   mp.delta = d->delta;
+  mp.delta2 = (float)(d->delta * d->delta);
   mp.mask_scale = d->mask_scale;
   mp.max_inner = d->max_inner;
   mp.max_imfs = d->max_imfs;
