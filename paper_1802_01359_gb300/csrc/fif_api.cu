@@ -64,6 +64,7 @@ struct LargeBuffers {
   float2* work = nullptr;
   float2* work2 = nullptr;
   float* rem = nullptr;
+  float* rem2 = nullptr;
   float2* row = nullptr;
   int* st = nullptr;
   unsigned char* part = nullptr;
@@ -512,6 +513,7 @@ fif_status large_buffers(fif_plan_t p, const LgSched& G, int nsig, LargeBuffers*
   b.work = (float2*)alloc(8 * (Nc + 1) * S);
   b.work2 = (float2*)alloc(8 * (Nc + 1) * S);
   b.rem = (float*)alloc(4 * n * S);
+  b.rem2 = (float*)alloc(4 * n * S);
   b.row = (float2*)alloc(8 * P * S);
   b.st = (int*)alloc(sizeof(int) * kLgStateWords * S);
   b.part = (unsigned char*)alloc((size_t)G.sel_blocks * kSelCand * kSelPartBytes * S);
@@ -548,6 +550,7 @@ fif_status upload_large_class(fif_plan_t p, const LgSched& G, LargeBuffers* b,
     g.work = b->work + (Nc + 1) * q;
     g.work2 = b->work2 + (Nc + 1) * q;
     g.rem = b->rem + (size_t)G.S.n * q;
+    g.rem2 = b->rem2 + (size_t)G.S.n * q;
     g.row = b->row + P * q;
     g.st = b->st + (size_t)kLgStateWords * q;
     g.part = b->part + (size_t)G.sel_blocks * kSelCand * kSelPartBytes * q;

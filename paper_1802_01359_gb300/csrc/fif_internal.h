@@ -129,7 +129,8 @@ struct LgSig {
   float2* spec;
   float2* work;
   float2* work2;
-  float* rem;
+  float* rem;             // remainder of even iterations (and the input copy)
+  float* rem2;            // remainder of odd iterations
   float2* row;
   int* st;                // kLgStateWords state words, zeroed before each run
   unsigned char* part;    // sel_blocks * kSelCand * kSelPartBytes

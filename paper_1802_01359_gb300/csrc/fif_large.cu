@@ -9,7 +9,8 @@
 //             Stockham factorisation with radices R1 and R2)
 //   split     real-transform split, rounded once to the FP32 spectrum
 // then per outer iteration:
-//   extrema   extrema and zero-crossing count of r over the whole grid
+//   extrema   (first iteration only) extrema and zero-crossing count of the
+//             input over the whole grid; later counts come from the epilogue
 //   ctl       one thread per signal: bookkeeping of the last IMF, outer-loop
 //             test (Algorithm 2)
 //   row       window eigenvalues {log2(1-w_hat_k), w_hat_k} for this L, in
@@ -20,10 +21,11 @@
 //             binary64 pass for the values the screen cannot decide; the last
 //             CTA to finish a pass merges the partials and takes the decision
 //             (classes of 8 or more signals: one CTA per signal, bisection)
-//   multiply  IMF_hat = (1-w_hat)^m r_hat, r_hat <- (1 - (1-w_hat)^m) r_hat
-//   presplit  inverse real-transform split
+//   multiply  IMF_hat = (1-w_hat)^m r_hat, r_hat <- (1 - (1-w_hat)^m) r_hat,
+//             fused with the inverse real-transform split
 //   level 1/2 inverse complex FFT
-//   epilogue  IMF row = C2R / n, r <- r - IMF
+//   epilogue  IMF row = C2R / n, r <- r - IMF (into the other remainder
+//             buffer), fused with the extrema count of the new remainder
 #include <map>
 
 #include "fif_device.cuh"
@@ -91,6 +93,10 @@ __device__ __forceinline__ int first_signal_point(int& step) {
   step = gridDim.x * blockDim.x;
   return blockIdx.x * blockDim.x + threadIdx.x;
 }
+
+// The remainder of iteration it (buffers alternate: the epilogue of iteration
+// it reads one and writes the other).
+__device__ __forceinline__ float* rem_buf(const LgSig& sg, int it) { return (it & 1) ? sg.rem2 : sg.rem; }
 
 // ------------------------------------------------------------ forward
 
@@ -347,7 +353,8 @@ __global__ void lg_row(const LgSig* __restrict__ sigs, LgSched G, int it, float*
   if (done) {
     if (done == it + 1) {
       float* orow = imfs + sg.out_off + (size_t)sg.st[LG_K] * n;
-      for (int i = first_signal_point(step); i < n; i += step) orow[i] = sg.rem[i];
+      const float* r = rem_buf(sg, it);
+      for (int i = first_signal_point(step); i < n; i += step) orow[i] = r[i];
     }
     return;
   }
@@ -744,30 +751,27 @@ __global__ void __launch_bounds__(512, 1) lg_select_cta(const LgSig* __restrict_
   }
 }
 
-__global__ void lg_multiply(const LgSig* __restrict__ sigs, LgSched G) {
+// IMF_hat = (1-w_hat)^m r_hat (eq. One step_algo), r_hat <- (1 - (1-w_hat)^m)
+// r_hat, and the inverse real-transform split of IMF_hat (same formulas as
+// inverse_real) into work2, in one pass: the thread of k (even n) owns the
+// bins k and Nc - k (Nyquist for k = 0), which the split combines.
+__global__ void lg_multiply_split(const LgSig* __restrict__ sigs, LgSched G) {
   const LgSig sg = sigs[blockIdx.y];
   if (sg.st[LG_DONE]) return;
   const int m = sg.st[LG_M];
-  int step;
-  for (int k = first_signal_point(step); k < G.S.P; k += step) {
-    const float2 z = sg.spec[k];
-    float g, omg;
-    multiplier(m, sg.row[k].x, g, omg);
-    sg.work[k] = make_float2(g * z.x, g * z.y);
-    sg.spec[k] = make_float2(omg * z.x, omg * z.y);
-  }
-}
-
-// Inverse real-transform split (same formulas as inverse_real), work -> work2.
-__global__ void lg_presplit(const LgSig* __restrict__ sigs, LgSched G) {
-  const LgSig sg = sigs[blockIdx.y];
-  if (sg.st[LG_DONE]) return;
   const int Nc = G.S.Nc, n = G.S.n;
   int step;
   if (!G.S.odd) {
     for (int k = first_signal_point(step); k <= Nc / 2; k += step) {
-      const float2 xk = sg.work[k];
-      const float2 xc = sg.work[Nc - k];
+      const int kc = Nc - k;
+      const float2 zk = sg.spec[k], zc = sg.spec[kc];
+      float gk, ok, gc, oc;
+      multiplier(m, sg.row[k].x, gk, ok);
+      multiplier(m, sg.row[kc].x, gc, oc);
+      const float2 xk = make_float2(gk * zk.x, gk * zk.y);
+      const float2 xc = make_float2(gc * zc.x, gc * zc.y);
+      sg.spec[k] = make_float2(ok * zk.x, ok * zk.y);
+      if (kc != k) sg.spec[kc] = make_float2(oc * zc.x, oc * zc.y);
       const float2 f = make_float2(xk.x + xc.x, xk.y - xc.y);
       const float2 g = make_float2(xk.x - xc.x, xk.y + xc.y);
       const float2 wg = cmul(cconj(__ldg(&G.S.tw[k])), g);
@@ -777,43 +781,96 @@ __global__ void lg_presplit(const LgSig* __restrict__ sigs, LgSched G) {
     }
   } else {
     for (int k = first_signal_point(step); k < G.S.P; k += step) {
-      const float2 v = sg.work[k];
-      sg.work2[k] = v;
-      if (k != 0) sg.work2[n - k] = cconj(v);
+      const float2 z = sg.spec[k];
+      float g, omg;
+      multiplier(m, sg.row[k].x, g, omg);
+      const float2 x = make_float2(g * z.x, g * z.y);
+      sg.spec[k] = make_float2(omg * z.x, omg * z.y);
+      sg.work2[k] = x;
+      if (k != 0) sg.work2[n - k] = cconj(x);
     }
   }
 }
 
-__global__ void lg_epilogue(const LgSig* __restrict__ sigs, LgSched G, float* __restrict__ imfs) {
+// New remainder sample j (0 <= j < n): old remainder minus the IMF sample
+// (C2R output / n), recomputed from the inputs for the neighbours a thread
+// does not own.
+__device__ __forceinline__ float new_rem(const float* ro, const float2* w2, int j, bool odd,
+                                         float inv_n) {
+  if (odd) return ro[j] - w2[j].x * inv_n;
+  const float2 z = w2[j >> 1];
+  return ro[j] - ((j & 1) ? z.y : z.x) * inv_n;
+}
+
+// Time-domain epilogue of one IMF fused with the extrema count of the new
+// remainder (same definitions as count_extrema): IMF row = C2R / n to the
+// output, new remainder = old - IMF into the other buffer, and per sample the
+// extrema, zero-crossing and tie terms from the new values of its neighbours
+// (taken from the old buffer and work2, so no CTA waits for another); CTA
+// sums go to the state words by atomics, with max |IMF| and max |r|.
+__global__ void lg_epilogue_ext(const LgSig* __restrict__ sigs, LgSched G, int it,
+                                float* __restrict__ imfs) {
   __shared__ RedScratch red;
   const LgSig sg = sigs[blockIdx.y];
-  if (sg.st[LG_DONE]) return;
-  const int n = G.S.n, K = sg.st[LG_K];
+  int* st = sg.st;
+  if (st[LG_DONE]) return;
+  const int n = G.S.n, K = st[LG_K];
+  const bool odd = G.S.odd;
   const float inv_n = 1.f / (float)n;
+  const float tau = tie_tau(__int_as_float(st[LG_SMAX]));
+  const float* ro = rem_buf(sg, it);
+  float* rn = rem_buf(sg, it + 1);
+  const float2* w2 = sg.work2;
   float* orow = imfs + sg.out_off + (size_t)K * n;
-  float imax = 0.f;
-  int step;
-  if (!G.S.odd) {
+  float imax = 0.f, rmax = 0.f;
+  int ext = 0, zc = 0, tie = 0, step;
+  if (!odd) {
     for (int t = first_signal_point(step); t < G.S.Nc; t += step) {
-      const float2 z = sg.work2[t];
+      const float2 z = w2[t];
       const float a = z.x * inv_n, b = z.y * inv_n;
       orow[2 * t] = a;
       orow[2 * t + 1] = b;
-      sg.rem[2 * t] -= a;
-      sg.rem[2 * t + 1] -= b;
+      const float r0 = ro[2 * t] - a, r1 = ro[2 * t + 1] - b;
+      rn[2 * t] = r0;
+      rn[2 * t + 1] = r1;
       imax = fmaxf(imax, fmaxf(fabsf(a), fabsf(b)));
+      rmax = fmaxf(rmax, fmaxf(fabsf(r0), fabsf(r1)));
+      const int s0 = 2 * t;
+      const float rm1 = new_rem(ro, w2, s0 == 0 ? n - 1 : s0 - 1, false, inv_n);
+      const float r2 = new_rem(ro, w2, s0 + 2 >= n ? s0 + 2 - n : s0 + 2, false, inv_n);
+      const float r3 = new_rem(ro, w2, s0 + 3 >= n ? s0 + 3 - n : s0 + 3, false, inv_n);
+      pair_terms(rm1, r0, r1, r2, r3, tau, ext, zc, tie);
     }
   } else {
-    for (int t = first_signal_point(step); t < n; t += step) {
-      const float a = sg.work2[t].x * inv_n;
-      orow[t] = a;
-      sg.rem[t] -= a;
+    for (int i = first_signal_point(step); i < n; i += step) {
+      const float a = w2[i].x * inv_n;
+      orow[i] = a;
+      const float b = ro[i] - a;
+      rn[i] = b;
       imax = fmaxf(imax, fabsf(a));
+      rmax = fmaxf(rmax, fabsf(b));
+      const int im1 = i == 0 ? n - 1 : i - 1;
+      const int ip1 = i + 1 == n ? 0 : i + 1;
+      const int ip2 = ip1 + 1 == n ? 0 : ip1 + 1;
+      const float ra = new_rem(ro, w2, im1, true, inv_n), c = new_rem(ro, w2, ip1, true, inv_n);
+      const float d = new_rem(ro, w2, ip2, true, inv_n);
+      const float dm = b - ra, d0 = c - b, dp = d - c;
+      ext += (dm > 0.f && d0 < 0.f) || (dm < 0.f && d0 > 0.f);
+      zc += (b > 0.f && c < 0.f) || (b < 0.f && c > 0.f);
+      tie |= fabsf(d0) <= tau && (fabsf(dm) <= tau || fabsf(dp) <= tau || ((dm > 0.f) == (dp > 0.f)));
     }
   }
-  float dummy = 0.f;
-  block_reduce2(imax, dummy, OpMax(), 0.f, &red);
-  if (threadIdx.x == 0) atomicMax(&sg.st[LG_IMAX], __float_as_int(imax));
+  tie = __syncthreads_or(tie);
+  float fe = (float)ext, fz = (float)zc;  // exact: a CTA counts far fewer than 2^24
+  block_reduce2(fe, fz, OpAdd(), 0.f, &red);
+  block_reduce2(imax, rmax, OpMax(), 0.f, &red);
+  if (threadIdx.x == 0) {
+    atomicAdd(&st[LG_EXT], (int)fe);
+    atomicAdd(&st[LG_ZC], (int)fz);
+    if (tie) atomicOr(&st[LG_TIE], 1);
+    atomicMax(&st[LG_RMAX], __float_as_int(rmax));
+    atomicMax(&st[LG_IMAX], __float_as_int(imax));
+  }
 }
 
 // ------------------------------------------------------------ tables
@@ -945,7 +1002,8 @@ cudaError_t large_run(const LgSched& G, const LgSig* d_sigs, int nsig, const Met
     e = cudaGetLastError();
   }
   for (int it = 0; e == cudaSuccess && it <= mp.max_imfs; it++) {
-    lg_extrema<<<dim3(bx_n, nsig), 256, 0, st>>>(d_sigs, G);
+    // the extrema of the input; later iterations count in the epilogue
+    if (it == 0) lg_extrema<<<dim3(bx_n, nsig), 256, 0, st>>>(d_sigs, G);
     lg_ctl<<<nsig, 1, 0, st>>>(d_sigs, G, mp, it, signals, out);
     lg_row<<<dim3(bx_bins, nsig), 256, 0, st>>>(d_sigs, G, it, out.imfs);
     if (cta_select) {
@@ -956,13 +1014,12 @@ cudaError_t large_run(const LgSched& G, const LgSig* d_sigs, int nsig, const Met
         lg_sel64<<<dim3(G.sel_blocks, nsig), kSelThreads, 0, st>>>(d_sigs, G, mp, r);
       }
     }
-    lg_multiply<<<dim3(bx_bins, nsig), 256, 0, st>>>(d_sigs, G);
-    lg_presplit<<<dim3(bx_split, nsig), 256, 0, st>>>(d_sigs, G);
+    lg_multiply_split<<<dim3(bx_split, nsig), 256, 0, st>>>(d_sigs, G);
     e = cudaGetLastError();
     if (e == cudaSuccess) e = launch_level<float2, true, 1>(G, d_sigs, nsig, st);
     if (e == cudaSuccess) e = launch_level<float2, true, 2>(G, d_sigs, nsig, st);
     if (e == cudaSuccess) {
-      lg_epilogue<<<dim3(bx_pts, nsig), 256, 0, st>>>(d_sigs, G, out.imfs);
+      lg_epilogue_ext<<<dim3(bx_pts, nsig), 256, 0, st>>>(d_sigs, G, it, out.imfs);
       e = cudaGetLastError();
     }
   }
