@@ -369,6 +369,9 @@ bool make_sub_sched(int R, FftSched& s) {
   s.tw_fold = R % 8 == 0 ? 3 : R % 4 == 0 ? 2 : R % 2 == 0 ? 1 : 0;
   s.tw_entries = s.tw_fold == 0 ? R : (R >> s.tw_fold) + 1;
   s.tw_shared = 1;
+  // eight elements a thread where possible: the level kernels then fit 64
+  // registers (two CTAs an SM) without spilling
+  if (plan_with_E(R, 8, 512, s)) return true;
   return make_fft_plan(R, s);
 }
 

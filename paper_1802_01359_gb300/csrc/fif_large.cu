@@ -138,7 +138,7 @@ __global__ void lg_pack(const LgSig* __restrict__ sigs, LgSched G, const float* 
 // read x[j + r Nc/R1], write y[j R1 + r].  LV 2: butterflies j = k < R1
 // (Ns = R1) read y[j + r R1] times W^(r j), write z[j + r R1].
 template <class Cx, bool INV, int E, int LV>
-__global__ void __launch_bounds__(512, 1) lg_level(const LgSig* __restrict__ sigs, LgSched G) {
+__global__ void __launch_bounds__(512, sizeof(Cx) == 8 ? 2 : 1) lg_level(const LgSig* __restrict__ sigs, LgSched G) {
   extern __shared__ __align__(16) unsigned char smem[];
   const LgSig sg = sigs[blockIdx.y];
   if (INV && sg.st[LG_DONE]) return;
@@ -159,11 +159,28 @@ __global__ void __launch_bounds__(512, 1) lg_level(const LgSig* __restrict__ sig
   Cx* buf = reinterpret_cast<Cx*>(smem);
   const int tid = threadIdx.x, nt = blockDim.x;
   const int j0 = blockIdx.x * TJ;
-  for (int f = tid; f < TJ * R; f += nt) {
-    const int r = f / TJ, g = f - r * TJ;
-    Cx v = in[j0 + g + r * stride_in];
-    if (LV == 2) v = cmul(v, inter_twiddle<Cx, INV>(G, r * (j0 + g)));
-    buf[g * R + r] = v;
+  const int tile = TJ * R;  // at most E elements per thread (nt >= TJ R / E)
+  {
+    // all of this thread's loads in flight together, then the transposed
+    // stores to shared memory
+    Cx v[E];
+#pragma unroll
+    for (int u = 0; u < E; u++) {
+      const int f = tid + u * nt;
+      if (f < tile) {
+        const int r = f / TJ, g = f - r * TJ;
+        v[u] = in[j0 + g + r * stride_in];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < E; u++) {
+      const int f = tid + u * nt;
+      if (f < tile) {
+        const int r = f / TJ, g = f - r * TJ;
+        if (LV == 2) v[u] = cmul(v[u], inter_twiddle<Cx, INV>(G, r * (j0 + g)));
+        buf[g * R + r] = v[u];
+      }
+    }
   }
   float2* q = nullptr;
   if constexpr (!FF) {
@@ -184,14 +201,22 @@ __global__ void __launch_bounds__(512, 1) lg_level(const LgSig* __restrict__ sig
     fft_inplace<Cx, INV, E>(mine, SR, ts, lt);
   }
   if (LV == 1) {
-    for (int f = tid; f < TJ * R; f += nt) {
-      const int gg = f / R, r = f - gg * R;
-      out[(size_t)(j0 + gg) * R + r] = buf[f];
+#pragma unroll
+    for (int u = 0; u < E; u++) {
+      const int f = tid + u * nt;
+      if (f < tile) {
+        const int gg = f / R, r = f - gg * R;
+        out[(size_t)(j0 + gg) * R + r] = buf[f];
+      }
     }
   } else {
-    for (int f = tid; f < TJ * R; f += nt) {
-      const int r = f / TJ, gg = f - r * TJ;
-      out[j0 + gg + r * G.R1] = buf[gg * R + r];
+#pragma unroll
+    for (int u = 0; u < E; u++) {
+      const int f = tid + u * nt;
+      if (f < tile) {
+        const int r = f / TJ, gg = f - r * TJ;
+        out[j0 + gg + r * G.R1] = buf[gg * R + r];
+      }
     }
   }
 }
