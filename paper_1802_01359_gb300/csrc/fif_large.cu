@@ -413,20 +413,18 @@ __global__ void lg_row(const LgSig* __restrict__ sigs, LgSched G, int it, float*
 
 // Candidates of round `round` of the search for m = the first j in
 // [1, max_inner] with SD_j < delta (eq. SD, Sec. 4).  Round 0 tests
-// ceil((i+1) max_inner / c), i < c = min(kSelCand, max_inner), which includes
-// max_inner itself; a later round tests the j strictly inside the bracket
-// (lo, hi) left by the one before: all of them if there are at most kSelCand,
-// else kSelCand evenly spaced ones.  Candidates are strictly increasing.
+// max_inner alone (which decides m = max_inner when SD_max_inner >= delta,
+// the common case), or every j when max_inner <= kSelCand; a later round
+// tests the j strictly inside the bracket (lo, hi) left by the one before:
+// all of them if there are at most kSelCand, else kSelCand evenly spaced
+// ones.  Candidates are strictly increasing.
 __host__ __device__ __forceinline__ int sel_count(int lo, int hi, int jmax, int round) {
-  if (round == 0) return jmax < kSelCand ? jmax : kSelCand;
+  if (round == 0) return jmax <= kSelCand ? jmax : 1;
   const int u = hi - lo - 1;
   return u <= 0 ? 0 : (u < kSelCand ? u : kSelCand);
 }
 __host__ __device__ __forceinline__ int sel_cand(int lo, int hi, int jmax, int round, int i) {
-  if (round == 0) {
-    const int c = jmax < kSelCand ? jmax : kSelCand;
-    return (int)(((long long)(i + 1) * jmax + c - 1) / c);
-  }
+  if (round == 0) return jmax <= kSelCand ? i + 1 : jmax;
   const int u = hi - lo - 1;
   if (u <= kSelCand) return lo + 1 + i;
   return lo + (int)(((long long)(i + 1) * (u + 1) + kSelCand) / (kSelCand + 1));
@@ -452,16 +450,9 @@ static int sel_rounds_after(int u, int jmax, std::map<int, int>& memo) {
 }
 
 int large_sel_rounds(int jmax) {
+  // round 0 leaves (0, jmax) open (max_inner tested alone) or closes it
   std::map<int, int> memo;
-  const int c0 = sel_count(0, jmax + 1, jmax, 0);
-  int prev = 0, w = 0;
-  for (int i = 0; i < c0; i++) {
-    const int j = sel_cand(0, jmax + 1, jmax, 0, i);
-    const int r = sel_rounds_after(j - prev - 1, jmax, memo);
-    if (r > w) w = r;
-    prev = j;
-  }
-  return 1 + w;
+  return 1 + (jmax <= kSelCand ? 0 : sel_rounds_after(jmax - 1, jmax, memo));
 }
 
 enum { SEL_F = 0, SEL_T = 1, SEL_AMB = 2 };  // SD_j >= delta, SD_j < delta, undecided
