@@ -468,8 +468,10 @@ struct OpMax {
 //   spec receives the n/2+1 (even n) or (n+1)/2 (odd n) bins, rounded
 //   rem  receives x (written after the transform)
 // Returns max |x| (every thread), or -1 if x holds a NaN or Inf.
+// Out of line: once per signal, and inlined it raised the register need (and
+// the spills) of the per-IMF loop of the kernels that call it.
 template <int E>
-__device__ float forward_real(const float* __restrict__ x, float* rem, ffc* zf, float2* spec,
+__device__ __noinline__ float forward_real(const float* __restrict__ x, float* rem, ffc* zf, float2* spec,
                               const FftSched& S, RedScratch* red) {
   const int tid = threadIdx.x, nt = blockDim.x, n = S.n;
   float amax = 0.f;
