@@ -62,7 +62,8 @@ def build(force: bool = False) -> str:
 class _Params(ctypes.Structure):
     _fields_ = [("nu", ctypes.c_double), ("mask_scale", ctypes.c_int), ("delta", ctypes.c_double),
                 ("max_inner", ctypes.c_int), ("max_imfs", ctypes.c_int),
-                ("L_in", ctypes.POINTER(ctypes.c_int)), ("absolute", ctypes.c_int)]
+                ("L_in", ctypes.POINTER(ctypes.c_int)), ("absolute", ctypes.c_int),
+                ("apriori", ctypes.c_int)]
 
 
 class _Outputs(ctypes.Structure):
@@ -91,6 +92,10 @@ def _load():
             lib.fifo_count_zero_crossings.restype = ctypes.c_long
             lib.fifo_mask_length.argtypes = [ctypes.c_long, ctypes.c_long, ctypes.c_double, ctypes.c_int]
             lib.fifo_mask_length.restype = ctypes.c_int
+            lib.fifo_apriori_n0.argtypes = [ctypes.c_double, ctypes.c_long, ctypes.c_long,
+                                            ctypes.c_double, ctypes.c_int,
+                                            ctypes.POINTER(ctypes.c_int)]
+            lib.fifo_apriori_n0.restype = ctypes.c_int
             _lib = lib
     return _lib
 
@@ -149,18 +154,26 @@ def count_zero_crossings(r) -> int:
     return int(_load().fifo_count_zero_crossings(_dptr(r), r.size))
 
 
+def apriori_n0(snorm: float, n: int, kzero: int, delta: float, max_inner: int):
+    """(N0, near_tie) of eq. N0_discrete (Theorem 5); N0 = max_inner + 1 if none <= max_inner."""
+    tie = ctypes.c_int()
+    N0 = _load().fifo_apriori_n0(float(snorm), int(n), int(kzero), float(delta), int(max_inner),
+                                 ctypes.byref(tie))
+    return int(N0), bool(tie.value)
+
+
 def mask_length(n: int, k: int, nu: float = 1.6, mask_scale: int = 1) -> int:
     return int(_load().fifo_mask_length(n, k, nu, mask_scale))
 
 
 def _run(fn_name, s, *, nu=1.6, mask_scale=1, delta=1e-3, max_inner=200, max_imfs=10,
-         force_L=None, absolute=False, trace=False):
+         force_L=None, absolute=False, apriori=False, trace=False):
     lib = _load()
     s = _as_f64(s)
     n = s.size
     keep = []
     p = _Params(nu=nu, mask_scale=mask_scale, delta=delta, max_inner=max_inner, max_imfs=max_imfs,
-                L_in=None, absolute=1 if absolute else 0)
+                L_in=None, absolute=1 if absolute else 0, apriori=1 if apriori else 0)
     if force_L is not None:
         Lin = np.zeros(max(max_imfs, 1), dtype=np.int32)
         fl = np.asarray(force_L, dtype=np.int32)[:max_imfs]

@@ -222,6 +222,51 @@ static int all_finite(const double* s, long n) {
   return 1;
 }
 
+int fifo_apriori_n0(double snorm, long n, long kzero, double delta, int max_inner, int* near_tie) {
+  const long dof = n - 1 - kzero;
+  *near_tie = 0;
+  if (!(snorm > 0.0) || dof <= 0) return 1; /* the right side is +inf */
+  /* both sides in logs: log(N^N / (N+1)^(N+1)) = N log N - (N+1) log(N+1) */
+  const double rhs = log(delta) - log(snorm) - 0.5 * log((double)dof);
+  double prev = 0.0; /* N = 0: 0^0 / 1 = 1 */
+  for (int N = 1; N <= max_inner; N++) {
+    const double lhs = (double)N * log((double)N) - (double)(N + 1) * log((double)(N + 1));
+    if (lhs < rhs) {
+      if (fabs(lhs - rhs) <= 1e-6 || (N > 1 && fabs(prev - rhs) <= 1e-6)) *near_tie = 1;
+      return N;
+    }
+    prev = lhs;
+  }
+  if (max_inner >= 1 && fabs(prev - rhs) <= 1e-6) *near_tie = 1;
+  return max_inner + 1;
+}
+
+/* ||U^T r||_inf of the unitary DFT: max_k |DFT(r)_k| / sqrt(n). */
+static double unitary_inf_norm(const double* Rre, const double* Rim, long n) {
+  double mx = 0.0;
+  for (long k = 0; k < n; k++) {
+    const double a = sqrt(Rre[k] * Rre[k] + Rim[k] * Rim[k]);
+    if (a > mx) mx = a;
+  }
+  return mx / sqrt((double)n);
+}
+
+/* m in the a-priori mode for the remainder spectrum R and window spectrum w. */
+static int apriori_m(const double* Rre, const double* Rim, const double* w, long n,
+                     const fifo_params* p, int* flags) {
+  long kzero = 0;
+  for (long k = 1; k < n; k++) kzero += w[k] == 0.0;
+  int tie = 0;
+  const int N0 = fifo_apriori_n0(unitary_inf_norm(Rre, Rim, n), n, kzero, p->delta, p->max_inner,
+                                 &tie);
+  if (tie) *flags |= FIFO_FLAG_NEAR_DELTA_TIE;
+  if (N0 > p->max_inner) {
+    *flags |= FIFO_FLAG_MAX_INNER_HIT;
+    return p->max_inner;
+  }
+  return N0;
+}
+
 /* Tier A: Algorithm 2 with a fixed mask length per inner loop (eq.
  * First_IMF_fixed_length), u_j = u_{j-1} - W u_{j-1} by direct periodic
  * convolution with the circulant W of eq. W_m (first column = the taps),
@@ -250,6 +295,23 @@ int fifo_iterative(const double* s, long n, const fifo_params* p, const fifo_out
     fifo_triangle_taps(n, L, c);
     memcpy(u, r, (size_t)n * sizeof(double));
     double sd = INFINITY, sd_prev = INFINITY;
+    int n0 = 0; /* a-priori mode: exactly n0 applications of (I - W) */
+    if (p->apriori) {
+      double* Xre = malloc((size_t)n * sizeof(double));
+      double* Xim = malloc((size_t)n * sizeof(double));
+      double* wk = malloc((size_t)n * sizeof(double));
+      if (!Xre || !Xim || !wk) {
+        free(Xre), free(Xim), free(wk);
+        free(r), free(u), free(v), free(c);
+        return -2;
+      }
+      memcpy(Xre, r, (size_t)n * sizeof(double));
+      for (long i = 0; i < n; i++) Xim[i] = 0.0;
+      fifo_fft(Xre, Xim, n, -1);
+      fifo_window_spectrum(n, L, wk);
+      n0 = apriori_m(Xre, Xim, wk, n, p, &flags);
+      free(Xre), free(Xim), free(wk);
+    }
     int j;
     for (j = 1; j <= p->max_inner; j++) {
       /* v = W u, (W u)_i = sum_d c[d mod n] u[(i-d) mod n] */
@@ -274,12 +336,14 @@ int fifo_iterative(const double* s, long n, const fifo_params* p, const fifo_out
       else
         sd = den > 0.0 ? sqrt(num / den) : 0.0;
       if (o->sd_trace) o->sd_trace[(size_t)K * (size_t)p->max_inner + (size_t)(j - 1)] = sd;
-      if (sd < p->delta) break;
+      if (p->apriori ? j == n0 : sd < p->delta) break;
     }
     int m = j > p->max_inner ? p->max_inner : j;
-    if (j > p->max_inner) flags |= FIFO_FLAG_MAX_INNER_HIT;
-    if (near_tie(sd, p->delta) || (m > 1 && near_tie(sd_prev, p->delta)))
-      flags |= FIFO_FLAG_NEAR_DELTA_TIE;
+    if (!p->apriori) {
+      if (j > p->max_inner) flags |= FIFO_FLAG_MAX_INNER_HIT;
+      if (near_tie(sd, p->delta) || (m > 1 && near_tie(sd_prev, p->delta)))
+        flags |= FIFO_FLAG_NEAR_DELTA_TIE;
+    }
     o->m[K] = m;
     o->L[K] = L;
     o->sd_m[K] = sd;
@@ -337,7 +401,8 @@ int fifo_direct(const double* s, long n, const fifo_params* p, const fifo_output
     for (long k = 0; k < n; k++) E[k] = Rre[k] * Rre[k] + Rim[k] * Rim[k];
     double sd = INFINITY, sd_prev = INFINITY;
     int j;
-    for (j = 1; j <= p->max_inner; j++) {
+    const int n0 = p->apriori ? apriori_m(Rre, Rim, w, n, p, &flags) : 0;
+    for (j = p->apriori ? p->max_inner + 1 : 1; j <= p->max_inner; j++) {
       double num = 0.0, den = 0.0;
       for (long k = 0; k < n; k++) {
         num += E[k] * w[k] * w[k];
@@ -353,9 +418,13 @@ int fifo_direct(const double* s, long n, const fifo_params* p, const fifo_output
       for (long k = 0; k < n; k++) E[k] *= (1.0 - w[k]) * (1.0 - w[k]);
     }
     int m = j > p->max_inner ? p->max_inner : j;
-    if (j > p->max_inner) flags |= FIFO_FLAG_MAX_INNER_HIT;
-    if (near_tie(sd, p->delta) || (m > 1 && near_tie(sd_prev, p->delta)))
-      flags |= FIFO_FLAG_NEAR_DELTA_TIE;
+    if (p->apriori) {
+      m = n0;
+    } else {
+      if (j > p->max_inner) flags |= FIFO_FLAG_MAX_INNER_HIT;
+      if (near_tie(sd, p->delta) || (m > 1 && near_tie(sd_prev, p->delta)))
+        flags |= FIFO_FLAG_NEAR_DELTA_TIE;
+    }
     for (long k = 0; k < n; k++) {
       double g = pow(1.0 - w[k], (double)m);
       double keep = -expm1((double)m * log1p(-w[k]));

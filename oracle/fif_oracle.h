@@ -51,6 +51,7 @@ typedef struct {
   int max_imfs;       /* cap on the number of IMFs (remainder not counted) */
   const int* L_in;    /* if non-NULL: forced half-support per IMF, <= 0 ends the loop */
   int absolute;       /* 0: relative SD (eq. SD); 1: absolute ||u_j-u_{j-1}||_2 (eq. Discrete_Abs_StopCond) */
+  int apriori;        /* 1: m = the a-priori N0 of Theorem 5 (eq. N0_discrete), no SD loop */
 } fifo_params;
 
 /* Per-call outputs.  imfs: (max_imfs+1)*n doubles, row K = IMF K, row n_imfs
@@ -76,6 +77,12 @@ int fifo_direct(const double* s, long n, const fifo_params* p, const fifo_output
 /* building blocks, exported for the pins */
 void fifo_dft_bruteforce(const double* re, const double* im, long n, int sign, double* ore, double* oim);
 int fifo_fft(double* re, double* im, long n, int sign); /* in place, any n >= 1 */
+/* Theorem 5, eq. N0_discrete: the smallest natural N >= 1 with
+ * N^N / (N+1)^(N+1) < delta / (snorm sqrt(n-1-kzero)), snorm = ||U^T r||_inf
+ * (U^T the unitary DFT), kzero the number of zero eigenvalues of W; returns
+ * max_inner+1 if no N <= max_inner qualifies.  *near_tie is set if the left
+ * side at the returned N or at N-1 lies within 1e-6 (relative) of the right. */
+int fifo_apriori_n0(double snorm, long n, long kzero, double delta, int max_inner, int* near_tie);
 void fifo_triangle_taps(long n, int L, double* c);   /* c[d mod n], normalized by the sum */
 void fifo_window_spectrum(long n, int L, double* w); /* closed form, k = 0..n-1 */
 long fifo_count_extrema(const double* r, long n);

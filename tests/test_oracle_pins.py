@@ -399,3 +399,102 @@ def test_exactly_zero_window_bins_stay_empty(oracle_mod):
     I = np.fft.fft(b["imfs"][0])
     S = np.fft.fft(s)
     assert np.allclose(I[zero], S[zero], rtol=1e-12, atol=1e-12 * np.abs(S).max())
+
+
+# ---------------------------------------------------------------- a-priori N0 mode
+# Theorem 5, eq. N0_discrete: m = the least natural N0 with
+# N0^N0 / (N0+1)^(N0+1) < delta / (||U^T r||_inf sqrt(n - 1 - k)).
+
+def _n0_exact(snorm, n, kzero, delta, cap):
+    """Least N >= 1 (or cap + 1) with f(N) < delta / (snorm sqrt(dof)), decided in exact
+    rational arithmetic on the squared inequality f(N)^2 snorm^2 dof < delta^2."""
+    from fractions import Fraction
+    dof = n - 1 - kzero
+    sn, de = Fraction(snorm), Fraction(delta)
+    for N in range(1, cap + 1):
+        f = Fraction(N ** N, (N + 1) ** (N + 1))
+        if f * f * sn * sn * dof < de * de:
+            return N
+    return cap + 1
+
+
+@pytest.mark.parametrize("seed", range(12))
+def test_apriori_n0_is_the_least_solution(oracle_mod, seed):
+    rng = np.random.default_rng(seed)
+    n = int(rng.choice([16, 64, 100, 256, 1024]))
+    kzero = int(rng.integers(0, 4))
+    snorm = float(10.0 ** rng.uniform(-1, 1.5))
+    delta = float(10.0 ** rng.uniform(-2, 0))
+    N0, tie = oracle_mod.apriori_n0(snorm, n, kzero, delta, 250)
+    if tie:
+        pytest.skip("boundary within 1e-6: either integer is admissible")
+    assert N0 == _n0_exact(snorm, n, kzero, delta, 250)
+
+
+def test_apriori_n0_degenerate_right_sides(oracle_mod):
+    assert oracle_mod.apriori_n0(0.0, 64, 0, 1e-3, 200) == (1, False)   # zero remainder
+    assert oracle_mod.apriori_n0(5.0, 8, 7, 1e-3, 200) == (1, False)    # n - 1 - k = 0
+    assert oracle_mod.apriori_n0(1e9, 64, 0, 1e-9, 200)[0] == 201       # beyond the cap
+
+
+@pytest.mark.parametrize("n,L", [(64, 8), (64, 6), (96, 12), (243, 27), (100, 10), (128, 7)])
+def test_zero_eigenvalue_count_is_gcd_minus_one(oracle_mod, n, L):
+    """w_hat_k = 0 exactly for k in [1, n-1] with kL = 0 mod n: gcd(n, L) - 1 of them."""
+    import math
+    w = oracle_mod.window_spectrum(n, L)
+    assert int(np.sum(w[1:] == 0.0)) == math.gcd(n, L) - 1
+
+
+def _apply_i_minus_w(u, L):
+    """u - W u with W the periodic convolution by the sampled triangle c_d = (L-|d|)/L^2."""
+    n = u.size
+    out = u.copy()
+    for d in range(-(L - 1), L):
+        out -= (L - abs(d)) / L ** 2 * np.roll(u, d)
+    return out
+
+
+@pytest.mark.parametrize("seed,n", [(0, 64), (1, 96), (2, 128)])
+def test_apriori_mode_meets_theorem5(oracle_mod, seed, n):
+    """With m = N0 every IMF satisfies the absolute criterion of Theorem 5 at the next step:
+    ||(I-W)^(N0+1) r - (I-W)^N0 r||_2 < delta, r the remainder it was taken from."""
+    rng = np.random.default_rng(seed)
+    x = np.arange(n) / n
+    s = np.sin(2 * np.pi * 3 * x) + 0.4 * np.sin(2 * np.pi * 11 * x) + 0.05 * rng.standard_normal(n)
+    delta = 0.05
+    res = oracle_mod.iterative(s, apriori=True, delta=delta, max_inner=2000, max_imfs=3)
+    K = int(res["n_imfs"])
+    assert K >= 1
+    import math
+    r = s.copy()
+    for k in range(K):
+        imf = res["imfs"][k]
+        L = int(res["L"][k])
+        nxt = _apply_i_minus_w(imf, L)
+        assert np.linalg.norm(nxt - imf) < delta
+        # and m is the least N0 for this remainder: ||U^T r||_inf from numpy's FFT
+        # (unitary: / sqrt(n)), k = gcd(n, L) - 1 zero eigenvalues, exact comparison
+        snorm = np.abs(np.fft.fft(r)).max() / math.sqrt(n)
+        if not res["status"] & oracle_mod.FLAG_NEAR_DELTA_TIE:
+            assert int(res["m"][k]) == _n0_exact(snorm, n, math.gcd(n, L) - 1, delta, 2000)
+        r = r - imf
+
+
+@pytest.mark.parametrize("seed,n", [(3, 64), (4, 72), (5, 81), (6, 128)])
+def test_apriori_direct_equals_iterative(oracle_mod, seed, n):
+    rng = np.random.default_rng(seed)
+    x = np.arange(n) / n
+    s = np.sin(2 * np.pi * 2 * x) + 0.5 * np.sin(2 * np.pi * 9 * x) + 0.02 * rng.standard_normal(n)
+    kw = dict(apriori=True, delta=0.02, max_inner=5000, max_imfs=4)
+    a, b = oracle_mod.iterative(s, **kw), oracle_mod.direct(s, **kw)
+    K = int(a["n_imfs"])
+    assert K == int(b["n_imfs"]) and a["status"] == b["status"]
+    assert np.array_equal(a["m"][:K], b["m"][:K]) and np.array_equal(a["L"][:K], b["L"][:K])
+    assert np.abs(a["imfs"][:K + 1] - b["imfs"][:K + 1]).max() < 1e-10 * np.abs(s).max()
+
+
+def test_apriori_caps_at_max_inner(oracle_mod):
+    n = 64
+    s = np.cos(2 * np.pi * 5 * np.arange(n) / n) * 100.0
+    r = oracle_mod.direct(s, apriori=True, delta=1e-9, max_inner=50, max_imfs=1)
+    assert r["m"][0] == 50 and r["status"] & oracle_mod.FLAG_MAX_INNER_HIT
