@@ -84,6 +84,13 @@ typedef enum {
 #define FIF_FORCE_MULTIPASS 2  /* run every signal through the multi-pass path that long signals
                                   take (FFT passes through global memory), whatever its length;
                                   for tests that compare the two paths */
+#define FIF_APRIORI_N0 4  /* m = the a-priori bound of Theorem 5 (eq. N0_discrete) instead of the
+                             search of eq. SD: the least natural N0 with
+                             N0^N0 / (N0+1)^(N0+1) < delta / (||U^T r||_inf sqrt(n-1-k)),
+                             U^T the unitary DFT, r the current remainder, k = gcd(n, L) - 1
+                             zero eigenvalues of W; capped at max_inner (MAX_INNER_HIT).  delta
+                             is then the absolute threshold of eq. Discrete_Abs_StopCond.
+                             NEAR_DELTA_TIE marks a bound within 1e-6 of the threshold. */
 
 typedef struct {
   fif_window window;        /* FIF_WIN_TRIANGLE */
@@ -95,7 +102,7 @@ typedef struct {
   int32_t max_imfs;         /* cap on the number of IMFs (remainder not counted), 0 .. 64 */
   fif_precision precision;  /* FIF_PREC_FP32 */
   int64_t max_n;            /* largest signal length this plan accepts */
-  int32_t flags;            /* 0 or FIF_FORCE_L | FIF_FORCE_MULTIPASS */
+  int32_t flags;            /* 0 or FIF_FORCE_L | FIF_FORCE_MULTIPASS | FIF_APRIORI_N0 */
 } fif_plan_desc;
 
 /* Optional per-IMF diagnostics, one record per outer step: record K < n_imfs

@@ -805,12 +805,81 @@ static __device__ bool sd_below(const float2* spec, const FftSched& S, const flo
   return decide_sd(r, chain, 10.f, spec, S, L, j, mp, st, red);
 }
 
+// A-priori mode (Theorem 5, eq. N0_discrete): m = the least natural N0 with
+// N0^N0 / (N0+1)^(N0+1) < delta / (||U^T r||_inf sqrt(n - 1 - k)), capped at
+// max_inner.  ||U^T r||_inf = max_k |r_hat_k| / sqrt(n) over the half spectrum
+// (a real signal's other bins mirror it); k = gcd(n, L) - 1 is the number of
+// zero eigenvalues of W (w_hat_k = 0 exactly where kL = 0 mod n, k != 0).
+// The bound is decided in binary64 on one thread, in logs
+// (log f(N) = N log N - (N+1) log(N+1), decreasing: bisection); a left side
+// within 1e-6 of the right at N0 or N0 - 1 is flagged NEAR_DELTA_TIE.
+__device__ __forceinline__ double n0_lhs(int N) {
+  return (double)N * log((double)N) - (double)(N + 1) * log((double)(N + 1));
+}
+
+static __device__ int apriori_m(const float2* spec, const FftSched& S, int L, const MethodParams& mp,
+                                int& flags, RedScratch* red) {
+  float mx = 0.f;
+  for (int k = threadIdx.x; k < S.P; k += blockDim.x) {
+    const float2 z = spec[k];
+    mx = fmaxf(mx, fmaf(z.x, z.x, z.y * z.y));
+  }
+  float dummy = 0.f;
+  block_reduce2(mx, dummy, OpMax(), 0.f, red);
+  __syncthreads();  // every thread has read red before thread 0 reuses it
+  int* out = reinterpret_cast<int*>(red->d);
+  if (threadIdx.x == 0) {
+    int a = S.n, b = L;
+    while (b) {
+      const int t = a % b;
+      a = b;
+      b = t;
+    }
+    const long long dof = (long long)S.n - 1 - (a - 1);
+    const double snorm = sqrt((double)mx) / sqrt((double)S.n);
+    const int jmax = mp.max_inner;
+    int N0 = 1, f = 0;
+    if (snorm > 0.0 && dof > 0) {
+      const double rhs = log(mp.delta) - log(snorm) - 0.5 * log((double)dof);
+      if (n0_lhs(jmax) >= rhs) {
+        N0 = jmax + 1;
+        if (fabs(n0_lhs(jmax) - rhs) <= 1e-6) f |= FIF_FLAG_NEAR_DELTA_TIE;
+      } else {
+        int lo = 0, hi = jmax;  // lhs(lo) >= rhs (lhs(0) = 0 >= rhs here), lhs(hi) < rhs
+        if (n0_lhs(1) < rhs) hi = 1;
+        while (hi - lo > 1) {
+          const int mid = lo + (hi - lo) / 2;
+          if (n0_lhs(mid) < rhs)
+            hi = mid;
+          else
+            lo = mid;
+        }
+        N0 = hi;
+        if (fabs(n0_lhs(N0) - rhs) <= 1e-6 || (N0 > 1 && fabs(n0_lhs(N0 - 1) - rhs) <= 1e-6))
+          f |= FIF_FLAG_NEAR_DELTA_TIE;
+      }
+    }
+    if (N0 > jmax) {
+      N0 = jmax;
+      f |= FIF_FLAG_MAX_INNER_HIT;
+    }
+    out[0] = N0;
+    out[1] = f;
+  }
+  __syncthreads();
+  const int m = out[0];
+  flags |= out[1];
+  __syncthreads();  // before red is reused
+  return m;
+}
+
 // m = first j in [1, max_inner] with SD_j < delta, else max_inner (eq. SD,
 // Sec. 4).  SD_j is non-increasing in j (raising j reweights towards bins
 // with small w_hat, where w_hat^2 is small), so the first crossing is found by
 // testing j = max_inner, then bisecting.
 static __device__ int select_m(const float2* spec, const FftSched& S, int L, const MethodParams& mp,
                                float sc, int& flags, RedScratch* red) {
+  if (mp.apriori) return apriori_m(spec, S, L, mp, flags, red);
   const float2* row = wrow(S, L);
   MSelState st;
   st.sc = sc;
@@ -841,6 +910,7 @@ static __device__ int select_m(const float2* spec, const FftSched& S, int L, con
 static __device__ int select_m_on_row(const float2* spec, const FftSched& S, const float2* row,
                                       int L, const MethodParams& mp, float sc, int& flags,
                                       RedScratch* red) {
+  if (mp.apriori) return apriori_m(spec, S, L, mp, flags, red);
   MSelState st;
   st.sc = sc;
   st.flags = 0;

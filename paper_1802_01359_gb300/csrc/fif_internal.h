@@ -47,6 +47,7 @@ struct MethodParams {
   int max_inner;
   int max_imfs;
   int force_L;
+  int apriori;                 // m = the a-priori N0 of Theorem 5 instead of the search
 };
 
 // One signal of a batch launch.

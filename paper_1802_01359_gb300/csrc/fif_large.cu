@@ -1008,7 +1008,7 @@ cudaError_t large_run(const LgSched& G, const LgSig* d_sigs, int nsig, const Met
   // The grid-wide search does about three times the work of one bisection
   // per signal but spreads one signal over the whole GPU: it pays off for
   // classes of few signals.
-  const bool cta_select = nsig >= kSelCtaMinSignals;
+  const bool cta_select = nsig >= kSelCtaMinSignals || mp.apriori;  // a-priori m: one CTA
   lg_pack<<<dim3(bx_pts, nsig), 256, 0, st>>>(d_sigs, G, signals);
   cudaError_t e = cudaGetLastError();
   if (e == cudaSuccess) e = launch_level<ffc, false, 1>(G, d_sigs, nsig, st);

@@ -136,26 +136,8 @@ __global__ void __launch_bounds__(512, 1) na_select(FftSched S, NaScratch scr, M
   if (st[NA_DONE]) return;
   const int L = st[NA_L];
   int iflags = st[NA_IFLAGS];
-  MSelState ms;
-  ms.sc = spectrum_scale(S.n, __int_as_float(st[NA_SMAX]));
-  ms.flags = 0;
-  int m;
-  const int jmax = mp.max_inner;
-  if (!sd_below(scr.spec, S, scr.row, L, jmax, mp, ms, &red)) {
-    m = jmax;
-    ms.flags |= FIF_FLAG_MAX_INNER_HIT;
-  } else {
-    int lo = 0, hi = jmax;
-    while (hi - lo > 1) {
-      const int mid = lo + (hi - lo) / 2;
-      if (sd_below(scr.spec, S, scr.row, L, mid, mp, ms, &red))
-        hi = mid;
-      else
-        lo = mid;
-    }
-    m = hi;
-  }
-  iflags |= ms.flags;
+  const float sc = spectrum_scale(S.n, __int_as_float(st[NA_SMAX]));
+  const int m = select_m_on_row(scr.spec, S, scr.row, L, mp, sc, iflags, &red);
   if (threadIdx.x == 0) {
     st[NA_M] = m;
     st[NA_IFLAGS] = iflags;
@@ -293,7 +275,7 @@ extern "C" fif_status fif_decompose_noalloc(const fif_plan_desc* d, const float*
   if (!d || !signal || !imfs || !n_imfs || !sig_status) return FIF_EINVAL;
   if (d->window != FIF_WIN_TRIANGLE || !(d->delta > 0.0) || !isfinite(d->delta) ||
       d->max_inner < 1 || d->max_inner > (1 << 20) || d->max_imfs < 0 || d->max_imfs > kMaxImfs ||
-      (d->flags & ~FIF_FORCE_L))
+      (d->flags & ~(FIF_FORCE_L | FIF_APRIORI_N0)))
     return FIF_EINVAL;
   if (!(d->flags & FIF_FORCE_L) &&
       (!(d->nu > 0.0) || !isfinite(d->nu) || d->mask_scale < 1 || d->mask_scale > 2))
@@ -377,6 +359,7 @@ extern "C" fif_status fif_decompose_noalloc(const fif_plan_desc* d, const float*
   mp.max_inner = d->max_inner;
   mp.max_imfs = d->max_imfs;
   mp.force_L = (d->flags & FIF_FORCE_L) ? 1 : 0;
+  mp.apriori = (d->flags & FIF_APRIORI_N0) ? 1 : 0;
   Outputs out{imfs, m, mask_len, n_imfs, sig_status, diag};
   cudaStream_t st = (cudaStream_t)cuda_stream;
 
