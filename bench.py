@@ -53,6 +53,9 @@ WORKLOADS = {
     "batch4096": dict(desc="65536 float32 signals, n=4096, 2-5 chirped AM components + noise; "
                            "delta=1e-3, max_imfs=12"),
     "batch4096_d1e-4": dict(desc="65536 float32 signals, n=4096, as batch4096 with delta=1e-4"),
+    "batch16384_n0": dict(desc="the batch16384 signals with m from the a-priori bound of "
+                               "Theorem 5 (eq. N0_discrete; absolute delta=2.0, "
+                               "max_inner=65536, max_imfs=10)"),
 }
 
 
@@ -88,8 +91,10 @@ def make_workload(name, rank=0):
     """(data, offsets, params) of a named workload."""
     from paper_1802_01359_gb300 import signals
     params = dict(PARAMS)
-    if name == "batch16384":
+    if name in ("batch16384", "batch16384_n0"):
         data, offs = generate(signals.W_BATCH_16384, np.full(BATCH, N), first=rank * BATCH)
+        if name == "batch16384_n0":
+            params.update(delta=2.0, max_inner=1 << 16, apriori_n0=True)
     elif name == "single4096":
         s = signals.single_4096()
         data, offs = s, np.array([0, s.size], dtype=np.int64)
@@ -222,7 +227,9 @@ def oracle_sample(data, offs, idx, threads, params=None):
     import oracle
     oracle.build()
 
-    prm = params or PARAMS
+    prm = dict(params or PARAMS)
+    if prm.pop("apriori_n0", False):
+        prm["apriori"] = True
 
     def one(i):
         return oracle.direct(data[offs[i]:offs[i + 1]].astype(np.float64), **prm)

@@ -810,12 +810,31 @@ static __device__ bool sd_below(const float2* spec, const FftSched& S, const flo
 // max_inner.  ||U^T r||_inf = max_k |r_hat_k| / sqrt(n) over the half spectrum
 // (a real signal's other bins mirror it); k = gcd(n, L) - 1 is the number of
 // zero eigenvalues of W (w_hat_k = 0 exactly where kL = 0 mod n, k != 0).
-// The bound is decided in binary64 on one thread, in logs
-// (log f(N) = N log N - (N+1) log(N+1), decreasing: bisection); a left side
-// within 1e-6 of the right at N0 or N0 - 1 is flagged NEAR_DELTA_TIE.
+// The bound is decided on one thread, in logs (log f(N) = N log N -
+// (N+1) log(N+1), decreasing in N), every comparison with the binary64
+// answer (N0Test); a left side within 1e-6 of the right at a tested N is
+// flagged NEAR_DELTA_TIE.
 __device__ __forceinline__ double n0_lhs(int N) {
   return (double)N * log((double)N) - (double)(N + 1) * log((double)(N + 1));
 }
+
+// The comparison lhs(N) < rhs of the bound: in FP32 (stable form
+// -log1p(N) - N log1p(1/N), absolute error below 1e-5 on both sides) when the
+// two sides are more than 1e-4 apart, else re-taken in binary64 (where a
+// difference within 1e-6 raises the tie flag).  Same answer as binary64.
+struct N0Test {
+  float rhs_f;
+  double rhs_d;
+  int flags;
+  __device__ bool below(int N) {
+    const float x = (float)N;
+    const float lf = -log1pf(x) - x * log1pf(1.f / x);
+    if (fabsf(lf - rhs_f) > 1e-4f) return lf < rhs_f;
+    const double ld = n0_lhs(N);
+    if (fabs(ld - rhs_d) <= 1e-6) flags |= FIF_FLAG_NEAR_DELTA_TIE;
+    return ld < rhs_d;
+  }
+};
 
 static __device__ int apriori_m(const float2* spec, const FftSched& S, int L, const MethodParams& mp,
                                 int& flags, RedScratch* red) {
@@ -836,29 +855,39 @@ static __device__ int apriori_m(const float2* spec, const FftSched& S, int L, co
       b = t;
     }
     const long long dof = (long long)S.n - 1 - (a - 1);
-    const double snorm = sqrt((double)mx) / sqrt((double)S.n);
     const int jmax = mp.max_inner;
-    int N0 = 1, f = 0;
-    if (snorm > 0.0 && dof > 0) {
-      const double rhs = log(mp.delta) - log(snorm) - 0.5 * log((double)dof);
-      if (n0_lhs(jmax) >= rhs) {
+    int N0 = 1;
+    N0Test t{0.f, 0.0, 0};
+    if (mx > 0.f && dof > 0) {
+      // rhs = log delta - log ||U^T r||_inf - log sqrt(dof), ||U^T r||_inf = sqrt(mx / n)
+      t.rhs_d = log(mp.delta) - 0.5 * (log((double)mx) - log((double)S.n)) - 0.5 * log((double)dof);
+      t.rhs_f = (float)t.rhs_d;
+      if (!t.below(jmax)) {
         N0 = jmax + 1;
-        if (fabs(n0_lhs(jmax) - rhs) <= 1e-6) f |= FIF_FLAG_NEAR_DELTA_TIE;
       } else {
-        int lo = 0, hi = jmax;  // lhs(lo) >= rhs (lhs(0) = 0 >= rhs here), lhs(hi) < rhs
-        if (n0_lhs(1) < rhs) hi = 1;
-        while (hi - lo > 1) {
-          const int mid = lo + (hi - lo) / 2;
-          if (n0_lhs(mid) < rhs)
-            hi = mid;
-          else
-            lo = mid;
+        // log f(N) = -log(N+1) - 1 + O(1/N): start from N + 1 = exp(-rhs - 1),
+        // step to the least N that passes, bisect if the estimate is far off
+        const float est = expf(-t.rhs_f - 1.f) - 1.f;
+        int g = est >= (float)jmax ? jmax : (est <= 1.f ? 1 : (int)est);
+        int steps = 0;
+        while (g > 1 && t.below(g - 1) && steps < 8) g--, steps++;
+        while (!t.below(g) && steps < 16) g++, steps++;
+        if (!(t.below(g) && (g == 1 || !t.below(g - 1)))) {
+          int lo = 0, hi = jmax;  // lhs(lo) >= rhs (lhs(0) = 0 >= rhs here), lhs(hi) < rhs
+          if (t.below(1)) hi = 1;
+          while (hi - lo > 1) {
+            const int mid = lo + (hi - lo) / 2;
+            if (t.below(mid))
+              hi = mid;
+            else
+              lo = mid;
+          }
+          g = hi;
         }
-        N0 = hi;
-        if (fabs(n0_lhs(N0) - rhs) <= 1e-6 || (N0 > 1 && fabs(n0_lhs(N0 - 1) - rhs) <= 1e-6))
-          f |= FIF_FLAG_NEAR_DELTA_TIE;
+        N0 = g;
       }
     }
+    int f = t.flags;
     if (N0 > jmax) {
       N0 = jmax;
       f |= FIF_FLAG_MAX_INNER_HIT;
