@@ -63,7 +63,7 @@ class _Params(ctypes.Structure):
     _fields_ = [("nu", ctypes.c_double), ("mask_scale", ctypes.c_int), ("delta", ctypes.c_double),
                 ("max_inner", ctypes.c_int), ("max_imfs", ctypes.c_int),
                 ("L_in", ctypes.POINTER(ctypes.c_int)), ("absolute", ctypes.c_int),
-                ("apriori", ctypes.c_int)]
+                ("apriori", ctypes.c_int), ("gamma", ctypes.c_double)]
 
 
 class _Outputs(ctypes.Structure):
@@ -167,13 +167,14 @@ def mask_length(n: int, k: int, nu: float = 1.6, mask_scale: int = 1) -> int:
 
 
 def _run(fn_name, s, *, nu=1.6, mask_scale=1, delta=1e-3, max_inner=200, max_imfs=10,
-         force_L=None, absolute=False, apriori=False, trace=False):
+         force_L=None, absolute=False, apriori=False, gamma=0.0, trace=False):
     lib = _load()
     s = _as_f64(s)
     n = s.size
     keep = []
     p = _Params(nu=nu, mask_scale=mask_scale, delta=delta, max_inner=max_inner, max_imfs=max_imfs,
-                L_in=None, absolute=1 if absolute else 0, apriori=1 if apriori else 0)
+                L_in=None, absolute=1 if absolute else 0, apriori=1 if apriori else 0,
+                gamma=float(gamma))
     if force_L is not None:
         Lin = np.zeros(max(max_imfs, 1), dtype=np.int32)
         fl = np.asarray(force_L, dtype=np.int32)[:max_imfs]

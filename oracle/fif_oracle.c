@@ -273,6 +273,7 @@ static int apriori_m(const double* Rre, const double* Rim, const double* w, long
  * stopping rule eq. SD. */
 int fifo_iterative(const double* s, long n, const fifo_params* p, const fifo_outputs* o) {
   if (check_args(s, n, p, o)) return -1;
+  if (p->gamma != 0.0) return -1; /* thresholding is a spectral operation (direct method) */
   double* r = malloc((size_t)n * sizeof(double));
   double* u = malloc((size_t)n * sizeof(double));
   double* v = malloc((size_t)n * sizeof(double));
@@ -428,6 +429,11 @@ int fifo_direct(const double* s, long n, const fifo_params* p, const fifo_output
     for (long k = 0; k < n; k++) {
       double g = pow(1.0 - w[k], (double)m);
       double keep = -expm1((double)m * log1p(-w[k]));
+      if (p->gamma > 0.0 && g >= 1.0 - p->gamma) {
+        /* k in I_{w,gamma,m}: w_hat_k taken as 0, the bin passes whole */
+        g = 1.0;
+        keep = 0.0;
+      }
       Ire[k] = g * Rre[k];
       Iim[k] = g * Rim[k];
       Rre[k] *= keep;

@@ -52,6 +52,9 @@ typedef struct {
   const int* L_in;    /* if non-NULL: forced half-support per IMF, <= 0 ends the loop */
   int absolute;       /* 0: relative SD (eq. SD); 1: absolute ||u_j-u_{j-1}||_2 (eq. Discrete_Abs_StopCond) */
   int apriori;        /* 1: m = the a-priori N0 of Theorem 5 (eq. N0_discrete), no SD loop */
+  double gamma;       /* 0, or the threshold of eq. I_gamma (0 < gamma < 1): bins with
+                         (1 - w_hat)^m >= 1 - gamma pass whole into the IMF
+                         (eq. IMF_cont_stop_threshold; direct method only) */
 } fifo_params;
 
 /* Per-call outputs.  imfs: (max_imfs+1)*n doubles, row K = IMF K, row n_imfs

@@ -498,3 +498,68 @@ def test_apriori_caps_at_max_inner(oracle_mod):
     s = np.cos(2 * np.pi * 5 * np.arange(n) / n) * 100.0
     r = oracle_mod.direct(s, apriori=True, delta=1e-9, max_inner=50, max_imfs=1)
     assert r["m"][0] == 50 and r["status"] & oracle_mod.FLAG_MAX_INNER_HIT
+
+
+# ---------------------------------------------------------------- thresholded IMF
+# eq. I_gamma / eq. IMF_cont_stop_threshold: with m fixed by the stopping rule, every bin
+# with (1 - w_hat_k)^m >= 1 - gamma passes whole into the IMF (w_hat_k taken as 0).
+
+def _what_closed_form(n, L):
+    k = np.arange(n)
+    with np.errstate(invalid="ignore", divide="ignore"):
+        w = (np.sin(np.pi * k * L / n) / (L * np.sin(np.pi * k / n))) ** 2
+    w[0] = 1.0
+    w[(k * L) % n == 0] = np.where(k[(k * L) % n == 0] == 0, 1.0, 0.0)
+    return w
+
+
+@pytest.mark.parametrize("k0,L,m", [(3, 8, 5), (6, 10, 40)])
+def test_threshold_pure_tone_passes_whole_or_scales(oracle_mod, k0, L, m):
+    n = 128
+    x = np.arange(n) / n
+    s = np.cos(2 * np.pi * k0 * x + 0.4)
+    w = _what_closed_form(n, L)[k0]
+    g = (1.0 - w) ** m
+    for gamma, expect_whole in ((1.0 - g + 1e-3, True), (max(1.0 - g - 1e-3, 1e-9), False)):
+        # force L and m: a tone's SD is w_hat for every j, so delta above it stops at j = 1;
+        # take m through the a-priori mode's cap instead
+        r = oracle_mod.direct(s, force_L=[L], max_imfs=1, apriori=True, delta=1e-300,
+                              max_inner=m, gamma=gamma)
+        assert r["m"][0] == m
+        ref = s if expect_whole else g * s
+        assert np.abs(r["imfs"][0] - ref).max() < 1e-12
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_threshold_bins_follow_the_definition(oracle_mod, seed):
+    rng = np.random.default_rng(seed)
+    n, L, m, gamma = 96, 7, 9, 0.2
+    s = rng.standard_normal(n)
+    r = oracle_mod.direct(s, force_L=[L], max_imfs=1, apriori=True, delta=1e-300, max_inner=m,
+                          gamma=gamma)
+    assert r["m"][0] == m
+    S = np.fft.fft(s)
+    G = (1.0 - _what_closed_form(n, L)) ** m
+    passing = G >= 1.0 - gamma
+    assert passing.any() and (~passing).any()
+    want = np.where(passing, S, G * S)
+    got = np.fft.fft(r["imfs"][0])
+    assert np.abs(got - want).max() < 1e-10 * np.abs(S).max()
+    # the remainder keeps the rest; IMF + remainder = s
+    assert np.abs(r["imfs"][0] + r["remainder"] - s).max() < 1e-12
+
+
+def test_threshold_reconstruction_and_zero_gamma(oracle_mod):
+    n = 256
+    x = np.arange(n) / n
+    s = np.sin(2 * np.pi * 3 * x) + 0.5 * np.sin(2 * np.pi * 17 * x) + 0.2 * np.cos(2 * np.pi * 41 * x)
+    r = oracle_mod.direct(s, gamma=0.05, max_imfs=5)
+    assert np.abs(r["imfs"].sum(0) + r["remainder"] - s).max() < 1e-12
+    a = oracle_mod.direct(s, max_imfs=5)
+    b = oracle_mod.direct(s, gamma=0.0, max_imfs=5)
+    assert np.array_equal(a["imfs"], b["imfs"])
+
+
+def test_threshold_rejected_by_the_time_domain_tier(oracle_mod):
+    with pytest.raises(Exception):
+        oracle_mod.iterative(np.ones(16), gamma=0.1)
