@@ -56,6 +56,8 @@ WORKLOADS = {
     "batch16384_n0": dict(desc="the batch16384 signals with m from the a-priori bound of "
                                "Theorem 5 (eq. N0_discrete; absolute delta=2.0, "
                                "max_inner=65536, max_imfs=10)"),
+    "batch16384_th": dict(desc="the batch16384 signals, thresholded IMFs (eq. I_gamma, "
+                               "gamma=0.05; delta=1e-3, max_inner=200, max_imfs=10)"),
 }
 
 
@@ -91,10 +93,12 @@ def make_workload(name, rank=0):
     """(data, offsets, params) of a named workload."""
     from paper_1802_01359_gb300 import signals
     params = dict(PARAMS)
-    if name in ("batch16384", "batch16384_n0"):
+    if name in ("batch16384", "batch16384_n0", "batch16384_th"):
         data, offs = generate(signals.W_BATCH_16384, np.full(BATCH, N), first=rank * BATCH)
         if name == "batch16384_n0":
             params.update(delta=2.0, max_inner=1 << 16, apriori_n0=True)
+        if name == "batch16384_th":
+            params.update(gamma=0.05)
     elif name == "single4096":
         s = signals.single_4096()
         data, offs = s, np.array([0, s.size], dtype=np.int64)

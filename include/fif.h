@@ -103,6 +103,10 @@ typedef struct {
   fif_precision precision;  /* FIF_PREC_FP32 */
   int64_t max_n;            /* largest signal length this plan accepts */
   int32_t flags;            /* 0 or FIF_FORCE_L | FIF_FORCE_MULTIPASS | FIF_APRIORI_N0 */
+  double gamma;             /* 0, or 0 < gamma < 1: thresholded IMF (eq. I_gamma,
+                               eq. IMF_cont_stop_threshold): with m chosen as usual, every bin
+                               with (1 - w_hat_k)^m >= 1 - gamma passes whole into the IMF
+                               (w_hat_k taken as 0) and leaves the remainder */
 } fif_plan_desc;
 
 /* Optional per-IMF diagnostics, one record per outer step: record K < n_imfs

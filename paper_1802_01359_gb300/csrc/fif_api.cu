@@ -288,6 +288,7 @@ fif_status validate_desc(const fif_plan_desc* d) {
   if (d->max_imfs < 0 || d->max_imfs > kMaxImfs) return FIF_EINVAL;
   if (d->max_n < 4 || d->max_n > (1 << 24)) return FIF_EINVAL;
   if (d->flags & ~(FIF_FORCE_L | FIF_FORCE_MULTIPASS | FIF_APRIORI_N0)) return FIF_EINVAL;
+  if (!(d->gamma >= 0.0 && d->gamma < 1.0)) return FIF_EINVAL;
   if (!(d->flags & FIF_FORCE_L)) {
     if (!(d->nu > 0.0) || !isfinite(d->nu)) return FIF_EINVAL;
     if (d->mask_scale < 1 || d->mask_scale > 2) return FIF_EINVAL;
@@ -742,6 +743,9 @@ fif_status fif_plan_create(fif_plan_t* out, const fif_plan_desc* desc, void* cud
   p->mp.max_imfs = desc->max_imfs;
   p->mp.force_L = (desc->flags & FIF_FORCE_L) ? 1 : 0;
   p->mp.apriori = (desc->flags & FIF_APRIORI_N0) ? 1 : 0;
+  p->mp.threshold = desc->gamma > 0.0 ? 1 : 0;
+  p->mp.gamma = desc->gamma;
+  p->mp.log2_keep = desc->gamma > 0.0 ? (float)log2(1.0 - desc->gamma) : 0.f;
   p->stream = (cudaStream_t)cuda_stream;
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);

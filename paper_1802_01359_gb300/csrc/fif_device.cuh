@@ -971,10 +971,36 @@ __device__ __forceinline__ void multiplier(int m, float hl, float& g, float& omg
   omg = e > -1.f ? -expm1f(e * 0.693147180559945309f) : 1.f - g;
 }
 
+// Thresholded IMF (eq. I_gamma, eq. IMF_cont_stop_threshold): bin k passes
+// whole (w_hat_k taken as 0) when (1 - w_hat_k)^m >= 1 - gamma.  Decided in
+// FP32 on m log2(1 - w_hat_k) against log2(1 - gamma) outside the rounding
+// band of both sides (table value good to 4u, the product u/2, the rounded
+// log2(1 - gamma) u/2: band 8u (|x| + |c|)), else in binary64 from the sine
+// table, as the binary64 definition decides.
+__device__ __forceinline__ bool passes_whole(int m, float hl, const FftSched& S, int L, int k,
+                                             const MethodParams& mp) {
+  const float x = (float)m * hl, c = mp.log2_keep;
+  if (x == -INFINITY) return false;  // w_hat = 1
+  const float band = 8.f * 5.9604645e-8f * (fabsf(x) + fabsf(c)) + 1e-30f;
+  if (x > c + band) return true;
+  if (x < c - band) return false;
+  return pow(1.0 - what64(S, L, k), (double)m) >= 1.0 - mp.gamma;
+}
+
+__device__ __forceinline__ void multiplier_th(int m, float hl, const FftSched& S, int L, int k,
+                                              const MethodParams& mp, float& g, float& omg) {
+  multiplier(m, hl, g, omg);
+  if (mp.threshold && passes_whole(m, hl, S, L, k, mp)) {
+    g = 1.f;
+    omg = 0.f;
+  }
+}
+
 // IMF spectrum work = (1 - w_hat)^m r_hat (eq. One step_algo) and the
 // spectral remainder update r_hat <- r_hat - IMF_hat = (1 - g) r_hat
 // (Algorithm 2: s = s - s_m).
-static __device__ void apply_multiplier(float2* spec, float2* work, const FftSched& S, int L, int m) {
+static __device__ void apply_multiplier(float2* spec, float2* work, const FftSched& S, int L, int m,
+                                        const MethodParams& mp) {
   const float2* row = wrow(S, L);
   const int nt = blockDim.x;
   for (int k0 = threadIdx.x; k0 < S.P; k0 += kSdBatch * nt) {
@@ -990,7 +1016,7 @@ static __device__ void apply_multiplier(float2* spec, float2* work, const FftSch
       if (k >= S.P) break;
       const float2 z = spec[k];
       float g, omg;
-      multiplier(m, hl[u], g, omg);
+      multiplier_th(m, hl[u], S, L, k, mp, g, omg);
       work[k] = make_float2(g * z.x, g * z.y);
       spec[k] = make_float2(omg * z.x, omg * z.y);
     }

@@ -75,7 +75,7 @@ __device__ void decompose_resident(const FftSched& S, const SigDesc& d, int sig,
       break;
     }
     const int m = select_m(spec, S, L, mp, sc, iflags, red);
-    apply_multiplier(spec, work, S, L, m);
+    apply_multiplier(spec, work, S, L, m, mp);
     inverse_real<E>(work, S, ts);
     float imax;
     if (!S.odd) {

@@ -48,6 +48,9 @@ struct MethodParams {
   int max_imfs;
   int force_L;
   int apriori;                 // m = the a-priori N0 of Theorem 5 instead of the search
+  int threshold;               // gamma > 0: thresholded IMF (eq. I_gamma)
+  double gamma;
+  float log2_keep;             // (float) log2(1 - gamma), set on the host
 };
 
 // One signal of a batch launch.

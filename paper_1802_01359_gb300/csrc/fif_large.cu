@@ -771,10 +771,10 @@ __global__ void __launch_bounds__(512, 1) lg_select_cta(const LgSig* __restrict_
 // r_hat, and the inverse real-transform split of IMF_hat (same formulas as
 // inverse_real) into work2, in one pass: the thread of k (even n) owns the
 // bins k and Nc - k (Nyquist for k = 0), which the split combines.
-__global__ void lg_multiply_split(const LgSig* __restrict__ sigs, LgSched G) {
+__global__ void lg_multiply_split(const LgSig* __restrict__ sigs, LgSched G, MethodParams mp) {
   const LgSig sg = sigs[blockIdx.y];
   if (sg.st[LG_DONE]) return;
-  const int m = sg.st[LG_M];
+  const int m = sg.st[LG_M], L = sg.st[LG_L];
   const int Nc = G.S.Nc, n = G.S.n;
   int step;
   if (!G.S.odd) {
@@ -782,8 +782,8 @@ __global__ void lg_multiply_split(const LgSig* __restrict__ sigs, LgSched G) {
       const int kc = Nc - k;
       const float2 zk = sg.spec[k], zc = sg.spec[kc];
       float gk, ok, gc, oc;
-      multiplier(m, sg.row[k].x, gk, ok);
-      multiplier(m, sg.row[kc].x, gc, oc);
+      multiplier_th(m, sg.row[k].x, G.S, L, k, mp, gk, ok);
+      multiplier_th(m, sg.row[kc].x, G.S, L, kc, mp, gc, oc);
       const float2 xk = make_float2(gk * zk.x, gk * zk.y);
       const float2 xc = make_float2(gc * zc.x, gc * zc.y);
       sg.spec[k] = make_float2(ok * zk.x, ok * zk.y);
@@ -799,7 +799,7 @@ __global__ void lg_multiply_split(const LgSig* __restrict__ sigs, LgSched G) {
     for (int k = first_signal_point(step); k < G.S.P; k += step) {
       const float2 z = sg.spec[k];
       float g, omg;
-      multiplier(m, sg.row[k].x, g, omg);
+      multiplier_th(m, sg.row[k].x, G.S, L, k, mp, g, omg);
       const float2 x = make_float2(g * z.x, g * z.y);
       sg.spec[k] = make_float2(omg * z.x, omg * z.y);
       sg.work2[k] = x;
@@ -1030,7 +1030,7 @@ cudaError_t large_run(const LgSched& G, const LgSig* d_sigs, int nsig, const Met
         lg_sel64<<<dim3(G.sel_blocks, nsig), kSelThreads, 0, st>>>(d_sigs, G, mp, r);
       }
     }
-    lg_multiply_split<<<dim3(bx_split, nsig), 256, 0, st>>>(d_sigs, G);
+    lg_multiply_split<<<dim3(bx_split, nsig), 256, 0, st>>>(d_sigs, G, mp);
     e = cudaGetLastError();
     if (e == cudaSuccess) e = launch_level<float2, true, 1>(G, d_sigs, nsig, st);
     if (e == cudaSuccess) e = launch_level<float2, true, 2>(G, d_sigs, nsig, st);

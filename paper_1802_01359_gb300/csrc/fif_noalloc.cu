@@ -144,15 +144,15 @@ __global__ void __launch_bounds__(512, 1) na_select(FftSched S, NaScratch scr, M
   }
 }
 
-__global__ void na_multiply(FftSched S, NaScratch scr) {
+__global__ void na_multiply(FftSched S, NaScratch scr, MethodParams mp) {
   const int* st = scr.state;
   if (st[NA_DONE]) return;
-  const int m = st[NA_M];
+  const int m = st[NA_M], L = st[NA_L];
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k < S.P) {
     const float2 z = scr.spec[k];
     float g, omg;
-    multiplier(m, __ldg(&scr.row[k]).x, g, omg);
+    multiplier_th(m, __ldg(&scr.row[k]).x, S, L, k, mp, g, omg);
     scr.work[k] = make_float2(g * z.x, g * z.y);
     scr.spec[k] = make_float2(omg * z.x, omg * z.y);
   }
@@ -227,7 +227,7 @@ static cudaError_t na_launch(const FftSched& s, const MethodParams& mp, const fl
     na_outer<<<1, threads, 0, st>>>(s, scr, out, mp);
     na_row<<<pblocks, 256, 0, st>>>(s, scr);
     na_select<<<1, threads, 0, st>>>(s, scr, mp);
-    na_multiply<<<pblocks, 256, 0, st>>>(s, scr);
+    na_multiply<<<pblocks, 256, 0, st>>>(s, scr, mp);
     na_inverse<E><<<1, threads, work_bytes, st>>>(s, scr, out, mp);
     e = cudaGetLastError();
   }
@@ -275,7 +275,7 @@ extern "C" fif_status fif_decompose_noalloc(const fif_plan_desc* d, const float*
   if (!d || !signal || !imfs || !n_imfs || !sig_status) return FIF_EINVAL;
   if (d->window != FIF_WIN_TRIANGLE || !(d->delta > 0.0) || !isfinite(d->delta) ||
       d->max_inner < 1 || d->max_inner > (1 << 20) || d->max_imfs < 0 || d->max_imfs > kMaxImfs ||
-      (d->flags & ~(FIF_FORCE_L | FIF_APRIORI_N0)))
+      (d->flags & ~(FIF_FORCE_L | FIF_APRIORI_N0)) || !(d->gamma >= 0.0 && d->gamma < 1.0))
     return FIF_EINVAL;
   if (!(d->flags & FIF_FORCE_L) &&
       (!(d->nu > 0.0) || !isfinite(d->nu) || d->mask_scale < 1 || d->mask_scale > 2))
@@ -360,6 +360,9 @@ extern "C" fif_status fif_decompose_noalloc(const fif_plan_desc* d, const float*
   mp.max_imfs = d->max_imfs;
   mp.force_L = (d->flags & FIF_FORCE_L) ? 1 : 0;
   mp.apriori = (d->flags & FIF_APRIORI_N0) ? 1 : 0;
+  mp.threshold = d->gamma > 0.0 ? 1 : 0;
+  mp.gamma = d->gamma;
+  mp.log2_keep = d->gamma > 0.0 ? (float)log2(1.0 - d->gamma) : 0.f;
   Outputs out{imfs, m, mask_len, n_imfs, sig_status, diag};
   cudaStream_t st = (cudaStream_t)cuda_stream;
 

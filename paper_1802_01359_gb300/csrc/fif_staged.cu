@@ -85,7 +85,7 @@ __global__ void __launch_bounds__(512, 1) staged_select(FftSched S, StagedScratc
   }
 }
 
-__global__ void staged_multiply(FftSched S, StagedScratch scr) {
+__global__ void staged_multiply(FftSched S, StagedScratch scr, MethodParams mp) {
   const int* st = scr.state;
   if (st[ST_DONE]) return;
   const int L = st[ST_L], m = st[ST_M];
@@ -94,7 +94,7 @@ __global__ void staged_multiply(FftSched S, StagedScratch scr) {
   if (k < S.P) {
     const float2 z = scr.spec[k];
     float g, omg;
-    multiplier(m, __ldg(&row[k]).x, g, omg);
+    multiplier_th(m, __ldg(&row[k]).x, S, L, k, mp, g, omg);
     scr.work[k] = make_float2(g * z.x, g * z.y);
     scr.spec[k] = make_float2(omg * z.x, omg * z.y);
   }
@@ -167,7 +167,7 @@ static cudaError_t launch_staged_e(const FftSched& s, const MethodParams& mp, co
   const int mblocks = (s.P + 255) / 256;
   for (int it = 0; it <= mp.max_imfs; it++) {
     staged_select<<<1, threads, 0, st>>>(s, scr, out, mp);
-    staged_multiply<<<mblocks, 256, 0, st>>>(s, scr);
+    staged_multiply<<<mblocks, 256, 0, st>>>(s, scr, mp);
     staged_inverse<E><<<1, threads, work_bytes, st>>>(s, scr, out, mp);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;

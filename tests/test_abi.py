@@ -40,17 +40,18 @@ def test_status_strings(lib):
 
 def _desc(**kw):
     d = dict(window=0, nu=1.6, mask_scale=1, delta=1e-3, max_inner=200, max_imfs=10, precision=0,
-             max_n=4096, flags=0)
+             max_n=4096, flags=0, gamma=0.0)
     d.update(kw)
     return fif.PlanDesc(d["window"], d["nu"], d["mask_scale"], d["delta"], d["max_inner"],
-                        d["max_imfs"], d["precision"], d["max_n"], d["flags"])
+                        d["max_imfs"], d["precision"], d["max_n"], d["flags"], d["gamma"])
 
 
 @pytest.mark.parametrize("bad", [dict(delta=0.0), dict(delta=-1.0), dict(max_inner=0),
                                  dict(max_imfs=-1), dict(max_imfs=65), dict(max_n=3),
                                  dict(max_n=(1 << 24) + 1), dict(window=7), dict(mask_scale=0),
                                  dict(mask_scale=3), dict(nu=0.0), dict(flags=8), dict(flags=16),
-                                 dict(delta=float("nan"))])
+                                 dict(delta=float("nan")), dict(gamma=1.0), dict(gamma=-0.1),
+                                 dict(gamma=float("nan"))])
 def test_plan_descriptor_validation(lib, bad):
     """Invalid descriptors are rejected before any CUDA call."""
     h = ctypes.c_void_p()
