@@ -40,6 +40,7 @@ STOP_MAX_IMFS = 3
 STOP_FORCED_END = 4
 STOP_NONFINITE = 5
 FLAG_NEAR_DELTA_TIE = 1 << 8
+FLAG_MASK_TIE = 1 << 9
 FLAG_MAX_INNER_HIT = 1 << 10
 FLAG_L_CLAMPED = 1 << 12
 
@@ -63,7 +64,7 @@ class _Params(ctypes.Structure):
     _fields_ = [("nu", ctypes.c_double), ("mask_scale", ctypes.c_int), ("delta", ctypes.c_double),
                 ("max_inner", ctypes.c_int), ("max_imfs", ctypes.c_int),
                 ("L_in", ctypes.POINTER(ctypes.c_int)), ("absolute", ctypes.c_int),
-                ("apriori", ctypes.c_int), ("gamma", ctypes.c_double)]
+                ("apriori", ctypes.c_int), ("gamma", ctypes.c_double), ("peak_mask", ctypes.c_int)]
 
 
 class _Outputs(ctypes.Structure):
@@ -96,6 +97,8 @@ def _load():
                                             ctypes.c_double, ctypes.c_int,
                                             ctypes.POINTER(ctypes.c_int)]
             lib.fifo_apriori_n0.restype = ctypes.c_int
+            lib.fifo_spectral_peak.argtypes = [dp, dp, ctypes.c_long, ctypes.POINTER(ctypes.c_int)]
+            lib.fifo_spectral_peak.restype = ctypes.c_long
             _lib = lib
     return _lib
 
@@ -162,19 +165,29 @@ def apriori_n0(snorm: float, n: int, kzero: int, delta: float, max_inner: int):
     return int(N0), bool(tie.value)
 
 
+def spectral_peak(x):
+    """(k*, tie) of fifo_spectral_peak for the real signal x (spectrum by the oracle's FFT)."""
+    x = _as_f64(x)
+    re, im = x.copy(), np.zeros_like(x)
+    _load().fifo_fft(_dptr(re), _dptr(im), x.size, -1)
+    tie = ctypes.c_int()
+    k = _load().fifo_spectral_peak(_dptr(re), _dptr(im), x.size, ctypes.byref(tie))
+    return int(k), bool(tie.value)
+
+
 def mask_length(n: int, k: int, nu: float = 1.6, mask_scale: int = 1) -> int:
     return int(_load().fifo_mask_length(n, k, nu, mask_scale))
 
 
 def _run(fn_name, s, *, nu=1.6, mask_scale=1, delta=1e-3, max_inner=200, max_imfs=10,
-         force_L=None, absolute=False, apriori=False, gamma=0.0, trace=False):
+         force_L=None, absolute=False, apriori=False, gamma=0.0, peak_mask=False, trace=False):
     lib = _load()
     s = _as_f64(s)
     n = s.size
     keep = []
     p = _Params(nu=nu, mask_scale=mask_scale, delta=delta, max_inner=max_inner, max_imfs=max_imfs,
                 L_in=None, absolute=1 if absolute else 0, apriori=1 if apriori else 0,
-                gamma=float(gamma))
+                gamma=float(gamma), peak_mask=1 if peak_mask else 0)
     if force_L is not None:
         Lin = np.zeros(max(max_imfs, 1), dtype=np.int32)
         fl = np.asarray(force_L, dtype=np.int32)[:max_imfs]

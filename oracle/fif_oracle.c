@@ -186,8 +186,22 @@ static int check_args(const double* s, long n, const fifo_params* p, const fifo_
 /* Outer-loop test shared by both tiers (Algorithm 2 "while #extrema >= 2",
  * the max_imfs cap, the window-length limit).  Returns 0 to continue with
  * *L set, else the stop reason. */
+long fifo_spectral_peak(const double* re, const double* im, long n, int* tie) {
+  long best = 0;
+  double bv = 0.0;
+  for (long k = 1; k <= n / 2; k++) {
+    const double v = re[k] * re[k] + im[k] * im[k];
+    if (v > bv) bv = v, best = k;
+  }
+  *tie = 0;
+  for (long k = 1; k <= n / 2 && best; k++)
+    if (k != best && re[k] * re[k] + im[k] * im[k] >= bv * (1.0 - 1e-5)) *tie = 1;
+  return best;
+}
+
+/* peak: the spectral peak k* of r when p->peak_mask (from the caller's spectrum). */
 static int outer_test(const double* r, long n, int K, const fifo_params* p, int* kext, int* L,
-                      int* flags) {
+                      int* flags, long peak, int peak_tie) {
   long k = fifo_count_extrema(r, n);
   kext[K] = (int)k;
   if (p->L_in) {
@@ -198,7 +212,13 @@ static int outer_test(const double* r, long n, int K, const fifo_params* p, int*
     return 0;
   }
   if (k < 2) return FIFO_STOP_EXTREMA;
-  *L = fifo_mask_length(n, k, p->nu, p->mask_scale);
+  if (p->peak_mask) {
+    /* a tone of k* cycles has 2 k* extrema: the same rule at that count */
+    *L = fifo_mask_length(n, 2 * (peak > 0 ? peak : 1), p->nu, p->mask_scale);
+    if (peak_tie) *flags |= FIFO_FLAG_MASK_TIE;
+  } else {
+    *L = fifo_mask_length(n, k, p->nu, p->mask_scale);
+  }
   if (*L < 2) {
     *L = 2;
     *flags |= FIFO_FLAG_L_CLAMPED;
@@ -291,7 +311,23 @@ int fifo_iterative(const double* s, long n, const fifo_params* p, const fifo_out
   }
   for (;;) {
     int L = 0;
-    reason = outer_test(r, n, K, p, o->kext, &L, &flags);
+    long peak = 0;
+    int ptie = 0;
+    if (p->peak_mask) {
+      double* Xre = malloc((size_t)n * sizeof(double));
+      double* Xim = malloc((size_t)n * sizeof(double));
+      if (!Xre || !Xim) {
+        free(Xre), free(Xim);
+        free(r), free(u), free(v), free(c);
+        return -2;
+      }
+      memcpy(Xre, r, (size_t)n * sizeof(double));
+      for (long i = 0; i < n; i++) Xim[i] = 0.0;
+      fifo_fft(Xre, Xim, n, -1);
+      peak = fifo_spectral_peak(Xre, Xim, n, &ptie);
+      free(Xre), free(Xim);
+    }
+    reason = outer_test(r, n, K, p, o->kext, &L, &flags, peak, ptie);
     if (reason) break;
     fifo_triangle_taps(n, L, c);
     memcpy(u, r, (size_t)n * sizeof(double));
@@ -396,7 +432,9 @@ int fifo_direct(const double* s, long n, const fifo_params* p, const fifo_output
   fifo_fft(Rre, Rim, n, -1);
   for (;;) {
     int L = 0;
-    reason = outer_test(r, n, K, p, o->kext, &L, &flags);
+    int ptie = 0;
+    const long peak = p->peak_mask ? fifo_spectral_peak(Rre, Rim, n, &ptie) : 0;
+    reason = outer_test(r, n, K, p, o->kext, &L, &flags, peak, ptie);
     if (reason) break;
     fifo_window_spectrum(n, L, w);
     for (long k = 0; k < n; k++) E[k] = Rre[k] * Rre[k] + Rim[k] * Rim[k];

@@ -40,6 +40,7 @@ extern "C" {
 #define FIFO_STOP_NONFINITE   5  /* NaN or Inf in the input */
 /* flags (OR-ed above the low byte) */
 #define FIFO_FLAG_NEAR_DELTA_TIE (1 << 8)  /* |SD_m - delta| or |SD_{m-1} - delta| <= 1e-6 delta */
+#define FIFO_FLAG_MASK_TIE       (1 << 9)  /* peak mask rule: another bin within 1e-5 of the peak */
 #define FIFO_FLAG_MAX_INNER_HIT  (1 << 10) /* no j <= max_inner had SD_j < delta */
 #define FIFO_FLAG_L_CLAMPED      (1 << 12) /* mask length rule gave L < 2; clamped to 2 */
 
@@ -55,6 +56,8 @@ typedef struct {
   double gamma;       /* 0, or the threshold of eq. I_gamma (0 < gamma < 1): bins with
                          (1 - w_hat)^m >= 1 - gamma pass whole into the IMF
                          (eq. IMF_cont_stop_threshold; direct method only) */
+  int peak_mask;      /* 1: L from the largest spectral peak k* of r (end of Sec. 2):
+                         the mask rule with k = 2 k*; the extrema count still stops */
 } fifo_params;
 
 /* Per-call outputs.  imfs: (max_imfs+1)*n doubles, row K = IMF K, row n_imfs
@@ -86,6 +89,10 @@ int fifo_fft(double* re, double* im, long n, int sign); /* in place, any n >= 1 
  * max_inner+1 if no N <= max_inner qualifies.  *near_tie is set if the left
  * side at the returned N or at N-1 lies within 1e-6 (relative) of the right. */
 int fifo_apriori_n0(double snorm, long n, long kzero, double delta, int max_inner, int* near_tie);
+/* The largest bin k* of |X_k| over 1 <= k <= n/2 (smallest k among equal
+ * magnitudes); *tie is set if another bin in that range is within 1e-5
+ * (relative) of it.  0 if every such bin is zero. */
+long fifo_spectral_peak(const double* re, const double* im, long n, int* tie);
 void fifo_triangle_taps(long n, int L, double* c);   /* c[d mod n], normalized by the sum */
 void fifo_window_spectrum(long n, int L, double* w); /* closed form, k = 0..n-1 */
 long fifo_count_extrema(const double* r, long n);

@@ -563,3 +563,55 @@ def test_threshold_reconstruction_and_zero_gamma(oracle_mod):
 def test_threshold_rejected_by_the_time_domain_tier(oracle_mod):
     with pytest.raises(Exception):
         oracle_mod.iterative(np.ones(16), gamma=0.1)
+
+
+# ---------------------------------------------------------------- Fourier-peak mask length
+# End of Sec. 2: L from the spectrum's peak instead of the extrema count.  Reading: the
+# largest |r_hat_k|, 1 <= k <= n/2 (smallest k on ties), with the extrema rule at the
+# count a tone of k* cycles has (2 k*).
+
+@pytest.mark.parametrize("n,k0", [(256, 7), (243, 11), (1024, 100)])
+def test_peak_mask_pure_tone_matches_the_extrema_rule(oracle_mod, n, k0):
+    x = np.arange(n) / n
+    s = np.cos(2 * np.pi * k0 * x + 0.3)
+    assert oracle_mod.spectral_peak(s) == (k0, False)
+    a = oracle_mod.direct(s, peak_mask=True, max_imfs=1)
+    b = oracle_mod.direct(s, max_imfs=1)
+    assert oracle_mod.count_extrema(s) == 2 * k0
+    assert a["L"][0] == b["L"][0] == oracle_mod.mask_length(n, 2 * k0)
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_spectral_peak_is_the_argmax_of_numpys_spectrum(oracle_mod, seed):
+    rng = np.random.default_rng(seed)
+    n = int(rng.choice([64, 100, 243, 512]))
+    s = rng.standard_normal(n)
+    mag = np.abs(np.fft.fft(s))[1:n // 2 + 1]
+    k, tie = oracle_mod.spectral_peak(s)
+    order = np.sort(mag)[::-1]
+    if order[1] >= order[0] * (1 - 1e-5):
+        assert tie
+    else:
+        assert k == 1 + int(np.argmax(mag)) and not tie
+
+
+def test_spectral_peak_tie_flag(oracle_mod):
+    n = 128
+    x = np.arange(n) / n
+    s = np.cos(2 * np.pi * 5 * x) + np.cos(2 * np.pi * 9 * x)
+    k, tie = oracle_mod.spectral_peak(s)
+    assert tie and k in (5, 9)               # equal up to round-off: either, flagged
+    r = oracle_mod.direct(s, peak_mask=True, max_imfs=1)
+    assert r["status"] & oracle_mod.FLAG_MASK_TIE
+
+
+@pytest.mark.parametrize("seed,n", [(7, 64), (8, 96), (9, 81)])
+def test_peak_mask_direct_equals_iterative(oracle_mod, seed, n):
+    rng = np.random.default_rng(seed)
+    x = np.arange(n) / n
+    s = np.sin(2 * np.pi * 2 * x) + 0.6 * np.sin(2 * np.pi * 13 * x) + 0.05 * rng.standard_normal(n)
+    kw = dict(peak_mask=True, delta=1e-3, max_inner=300, max_imfs=3)
+    a, b = oracle_mod.iterative(s, **kw), oracle_mod.direct(s, **kw)
+    K = int(a["n_imfs"])
+    assert K == int(b["n_imfs"]) and np.array_equal(a["L"], b["L"]) and np.array_equal(a["m"], b["m"])
+    assert np.abs(a["imfs"] - b["imfs"]).max() < 1e-10 * np.abs(s).max()
