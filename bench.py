@@ -58,6 +58,8 @@ WORKLOADS = {
                                "max_inner=65536, max_imfs=10)"),
     "batch16384_th": dict(desc="the batch16384 signals, thresholded IMFs (eq. I_gamma, "
                                "gamma=0.05; delta=1e-3, max_inner=200, max_imfs=10)"),
+    "batch16384_pk": dict(desc="the batch16384 signals, mask length from the spectral peak "
+                               "(end of Sec. 2; delta=1e-3, max_inner=200, max_imfs=10)"),
 }
 
 
@@ -93,12 +95,14 @@ def make_workload(name, rank=0):
     """(data, offsets, params) of a named workload."""
     from paper_1802_01359_gb300 import signals
     params = dict(PARAMS)
-    if name in ("batch16384", "batch16384_n0", "batch16384_th"):
+    if name in ("batch16384", "batch16384_n0", "batch16384_th", "batch16384_pk"):
         data, offs = generate(signals.W_BATCH_16384, np.full(BATCH, N), first=rank * BATCH)
         if name == "batch16384_n0":
             params.update(delta=2.0, max_inner=1 << 16, apriori_n0=True)
         if name == "batch16384_th":
             params.update(gamma=0.05)
+        if name == "batch16384_pk":
+            params.update(peak_mask=True)
     elif name == "single4096":
         s = signals.single_4096()
         data, offs = s, np.array([0, s.size], dtype=np.int64)

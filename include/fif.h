@@ -91,6 +91,11 @@ typedef enum {
                              zero eigenvalues of W; capped at max_inner (MAX_INNER_HIT).  delta
                              is then the absolute threshold of eq. Discrete_Abs_StopCond.
                              NEAR_DELTA_TIE marks a bound within 1e-6 of the threshold. */
+#define FIF_PEAK_MASK 8  /* mask length from the spectrum (end of Sec. 2): L = mask_scale *
+                            floor(nu n / (2 k*)), k* the largest |r_hat_k| over 1 <= k <= n/2
+                            (smallest k among equal magnitudes) of the current remainder; the
+                            extrema count still decides the stop.  EXTREMA_TIE also marks a
+                            second bin within 1e-5 (relative) of the peak. */
 
 typedef struct {
   fif_window window;        /* FIF_WIN_TRIANGLE */
@@ -102,7 +107,8 @@ typedef struct {
   int32_t max_imfs;         /* cap on the number of IMFs (remainder not counted), 0 .. 64 */
   fif_precision precision;  /* FIF_PREC_FP32 */
   int64_t max_n;            /* largest signal length this plan accepts */
-  int32_t flags;            /* 0 or FIF_FORCE_L | FIF_FORCE_MULTIPASS | FIF_APRIORI_N0 */
+  int32_t flags;            /* 0 or FIF_FORCE_L | FIF_FORCE_MULTIPASS | FIF_APRIORI_N0 |
+                               FIF_PEAK_MASK */
   double gamma;             /* 0, or 0 < gamma < 1: thresholded IMF (eq. I_gamma,
                                eq. IMF_cont_stop_threshold): with m chosen as usual, every bin
                                with (1 - w_hat_k)^m >= 1 - gamma passes whole into the IMF

@@ -287,7 +287,8 @@ fif_status validate_desc(const fif_plan_desc* d) {
   if (d->max_inner < 1 || d->max_inner > (1 << 20)) return FIF_EINVAL;
   if (d->max_imfs < 0 || d->max_imfs > kMaxImfs) return FIF_EINVAL;
   if (d->max_n < 4 || d->max_n > (1 << 24)) return FIF_EINVAL;
-  if (d->flags & ~(FIF_FORCE_L | FIF_FORCE_MULTIPASS | FIF_APRIORI_N0)) return FIF_EINVAL;
+  if (d->flags & ~(FIF_FORCE_L | FIF_FORCE_MULTIPASS | FIF_APRIORI_N0 | FIF_PEAK_MASK))
+    return FIF_EINVAL;
   if (!(d->gamma >= 0.0 && d->gamma < 1.0)) return FIF_EINVAL;
   if (!(d->flags & FIF_FORCE_L)) {
     if (!(d->nu > 0.0) || !isfinite(d->nu)) return FIF_EINVAL;
@@ -743,6 +744,7 @@ fif_status fif_plan_create(fif_plan_t* out, const fif_plan_desc* desc, void* cud
   p->mp.max_imfs = desc->max_imfs;
   p->mp.force_L = (desc->flags & FIF_FORCE_L) ? 1 : 0;
   p->mp.apriori = (desc->flags & FIF_APRIORI_N0) ? 1 : 0;
+  p->mp.peak_mask = (desc->flags & FIF_PEAK_MASK) ? 1 : 0;
   p->mp.threshold = desc->gamma > 0.0 ? 1 : 0;
   p->mp.gamma = desc->gamma;
   p->mp.log2_keep = desc->gamma > 0.0 ? (float)log2(1.0 - desc->gamma) : 0.f;

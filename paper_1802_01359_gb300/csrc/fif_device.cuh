@@ -1062,6 +1062,16 @@ struct EpiOut {
   float rmax;   // ||r||_inf of the new remainder
 };
 
+// Whether the extrema count could change when r moves by tau/2 around the
+// difference d0 (neighbours dm, dp): d0 within tau of zero and either exactly
+// zero (a plateau between a rise and a fall holds no extremum, and either
+// sign of d0 makes one: a change of one), or a neighbour also within tau, or
+// both neighbours of one sign (a flip of d0 adds or removes two).
+__device__ __forceinline__ bool diff_tie(float dm, float d0, float dp, float tau) {
+  return fabsf(d0) <= tau &&
+         (d0 == 0.f || fabsf(dm) <= tau || fabsf(dp) <= tau || ((dm > 0.f) == (dp > 0.f)));
+}
+
 // Extrema, zero-crossing and tie terms owned by the sample pair (2t, 2t+1),
 // given r[2t-1 .. 2t+3]: samples 2t and 2t+1, differences d_2t and d_2t+1,
 // crossings (2t, 2t+1) and (2t+1, 2t+2).  Same definitions as count_extrema.
@@ -1072,8 +1082,8 @@ __device__ __forceinline__ void pair_terms(float rm1, float r0, float r1, float 
   ext += (d0 > 0.f && d1 < 0.f) || (d0 < 0.f && d1 > 0.f);
   zc += (r0 > 0.f && r1 < 0.f) || (r0 < 0.f && r1 > 0.f);
   zc += (r1 > 0.f && r2 < 0.f) || (r1 < 0.f && r2 > 0.f);
-  tie |= fabsf(d0) <= tau && (fabsf(dm1) <= tau || fabsf(d1) <= tau || ((dm1 > 0.f) == (d1 > 0.f)));
-  tie |= fabsf(d1) <= tau && (fabsf(d0) <= tau || fabsf(d2) <= tau || ((d0 > 0.f) == (d2 > 0.f)));
+  tie |= diff_tie(dm1, d0, d1, tau);
+  tie |= diff_tie(d0, d1, d2, tau);
 }
 
 // Time-domain epilogue of one IMF (even n) fused with the extrema count of
@@ -1193,7 +1203,7 @@ static __device__ ExtremaInfo count_extrema(const float* rem, int n, float tau, 
     const float dm = b - a, d0 = c - b, dp = d - c;
     ext += (dm > 0.f && d0 < 0.f) || (dm < 0.f && d0 > 0.f);
     zc += (b > 0.f && c < 0.f) || (b < 0.f && c > 0.f);
-    tie |= fabsf(d0) <= tau && (fabsf(dm) <= tau || fabsf(dp) <= tau || ((dm > 0.f) == (dp > 0.f)));
+    tie |= diff_tie(dm, d0, dp, tau);
     rmax = fmaxf(rmax, fabsf(b));
   }
   tie = __syncthreads_or(tie);
@@ -1212,8 +1222,61 @@ static __device__ ExtremaInfo count_extrema(const float* rem, int n, float tau, 
 // Outer-loop test before IMF K (Algorithm 2 "while #extrema >= 2", the
 // max_imfs cap, the window limit 2L-1 <= n).  Returns 0 and sets L to
 // continue, else the stop reason.  Same value in every thread.
+// Fourier-peak mask length (end of Sec. 2): k* = the largest |r_hat_k| over
+// 1 <= k <= n/2 (smallest k among equal magnitudes) and whether another bin
+// lies within 1e-5 (relative, on |r_hat|^2) of it.  One CTA over the half
+// spectrum; every thread gets the result.  The key packs the FP32 magnitude
+// (non-negative: its bits order as integers) above the complemented index.
+struct SpecPeak {
+  int k;
+  int tie;
+};
+
+__device__ __forceinline__ unsigned long long peak_key(float v, int k) {
+  return ((unsigned long long)__float_as_uint(v) << 32) | (unsigned)(0xffffffffu - (unsigned)k);
+}
+
+static __device__ SpecPeak spectral_peak(const float2* spec, const FftSched& S, RedScratch* red) {
+  unsigned long long best = 0ull;
+  for (int k = 1 + threadIdx.x; k < S.P; k += blockDim.x) {
+    const float2 z = spec[k];
+    const unsigned long long key = peak_key(fmaf(z.x, z.x, z.y * z.y), k);
+    best = key > best ? key : best;
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    const unsigned long long o = __shfl_xor_sync(0xffffffffu, best, off);
+    best = o > best ? o : best;
+  }
+  unsigned long long* sm = reinterpret_cast<unsigned long long*>(red->d);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  __syncthreads();
+  if (lane == 0) sm[wid] = best;
+  __syncthreads();
+  best = lane < nw ? sm[lane] : 0ull;
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    const unsigned long long o = __shfl_xor_sync(0xffffffffu, best, off);
+    best = o > best ? o : best;
+  }
+  SpecPeak r;
+  r.k = best ? (int)(0xffffffffu - (unsigned)(best & 0xffffffffull)) : 0;
+  const float vmax = __uint_as_float((unsigned)(best >> 32));
+  int tie = 0;
+  for (int k = 1 + threadIdx.x; k < S.P; k += blockDim.x) {
+    const float2 z = spec[k];
+    tie |= k != r.k && fmaf(z.x, z.x, z.y * z.y) >= vmax * (1.f - 1e-5f) && vmax > 0.f;
+  }
+  r.tie = __syncthreads_or(tie);
+  return r;
+}
+
+// Under FIF_PEAK_MASK, L comes from the spectral peak k* (peak >= 1): the same
+// rule at the count of extrema a tone of k* cycles has, 2 k*; the extrema
+// count k still decides the stop.
 __device__ __forceinline__ int outer_test(int k, int K, int n, const MethodParams& mp,
-                                          const int32_t* forced_L, int& L, int& flags) {
+                                          const int32_t* forced_L, int& L, int& flags,
+                                          int peak = 0) {
   if (mp.force_L) {
     if (K == mp.max_imfs) return FIF_STOP_MAX_IMFS;
     L = forced_L[K];
@@ -1222,8 +1285,9 @@ __device__ __forceinline__ int outer_test(int k, int K, int n, const MethodParam
     return 0;
   }
   if (k < 2) return FIF_STOP_EXTREMA;
+  const int kk = mp.peak_mask ? 2 * (peak > 0 ? peak : 1) : k;
   double t = mp.nu * (double)n;
-  t = t / (double)k;
+  t = t / (double)kk;
   L = mp.mask_scale * (int)floor(t);
   if (L < 2) {
     L = 2;

@@ -53,8 +53,11 @@ __device__ void decompose_resident(const FftSched& S, const SigDesc& d, int sig,
   for (;;) {
     // the outer test (binary64 division) on one thread, broadcast
     int L = 0, iflags = e.tie ? FIF_FLAG_EXTREMA_TIE : 0;
+    SpecPeak pk{0, 0};
+    if (mp.peak_mask) pk = spectral_peak(spec, S, red);
+    if (pk.tie) iflags |= FIF_FLAG_EXTREMA_TIE;
     if (tid == 0) {
-      ot[0] = outer_test(e.k, K, n, mp, L_io, L, iflags);
+      ot[0] = outer_test(e.k, K, n, mp, L_io, L, iflags, pk.k);
       ot[1] = L;
       ot[2] = iflags;
     }

@@ -51,6 +51,7 @@ struct MethodParams {
   int threshold;               // gamma > 0: thresholded IMF (eq. I_gamma)
   double gamma;
   float log2_keep;             // (float) log2(1 - gamma), set on the host
+  int peak_mask;               // L from the spectral peak instead of the extrema count
 };
 
 // One signal of a batch launch.

@@ -37,8 +37,11 @@ enum {
   LG_K = 0, LG_FLAGS, LG_DONE, LG_L, LG_M, LG_IFLAGS, LG_SMAX, LG_BAD, LG_IMAX,
   LG_EXT, LG_ZC, LG_TIE, LG_RMAX,         // extrema count of the remainder (atomics)
   LG_LO, LG_HI, LG_STAT, LG_AMB, LG_CNT,  // m search: bracket, statuses, arrivals
+  LG_PTIE, LG_PAD,                        // spectral peak: tie flag
+  LG_PK, LG_PK_HI,                        // spectral peak key (8-byte aligned word pair)
   LG_NWORDS
 };
+static_assert(LG_PK % 2 == 0, "64-bit atomics on the peak key");
 static_assert(LG_NWORDS <= kLgStateWords, "state words");
 
 // The caller's arrays of one signal.
@@ -267,7 +270,7 @@ __global__ void lg_extrema(const LgSig* __restrict__ sigs, LgSched G) {
     const float dm = b - a, d0 = c - b, dp = d - c;
     ext += (dm > 0.f && d0 < 0.f) || (dm < 0.f && d0 > 0.f);
     zc += (b > 0.f && c < 0.f) || (b < 0.f && c > 0.f);
-    tie |= fabsf(d0) <= tau && (fabsf(dm) <= tau || fabsf(dp) <= tau || ((dm > 0.f) == (dp > 0.f)));
+    tie |= diff_tie(dm, d0, dp, tau);
     rmax = fmaxf(rmax, fabsf(b));
   }
   tie = __syncthreads_or(tie);
@@ -281,6 +284,51 @@ __global__ void lg_extrema(const LgSig* __restrict__ sigs, LgSched G) {
     if (tie) atomicOr(&st[LG_TIE], 1);
     atomicMax(&st[LG_RMAX], __float_as_int(rmax));
   }
+}
+
+// Spectral peak of the remainder over the grid (FIF_PEAK_MASK): the largest
+// key (magnitude bits above the complemented index, as spectral_peak) by a
+// 64-bit atomic max, then whether another bin lies within 1e-5 of it.
+__global__ void lg_peak(const LgSig* __restrict__ sigs, LgSched G) {
+  __shared__ unsigned long long wmax[32];
+  const LgSig sg = sigs[blockIdx.y];
+  if (sg.st[LG_DONE]) return;
+  unsigned long long best = 0ull;
+  int step;
+  for (int k = first_signal_point(step); k < G.S.P; k += step) {
+    if (k == 0) continue;
+    const float2 z = sg.spec[k];
+    const unsigned long long key = peak_key(fmaf(z.x, z.x, z.y * z.y), k);
+    best = key > best ? key : best;
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    const unsigned long long o = __shfl_xor_sync(0xffffffffu, best, off);
+    best = o > best ? o : best;
+  }
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) wmax[wid] = best;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < (int)(blockDim.x >> 5); w++) best = wmax[w] > best ? wmax[w] : best;
+    atomicMax(reinterpret_cast<unsigned long long*>(&sg.st[LG_PK]), best);
+  }
+}
+
+__global__ void lg_peak_tie(const LgSig* __restrict__ sigs, LgSched G) {
+  const LgSig sg = sigs[blockIdx.y];
+  if (sg.st[LG_DONE]) return;
+  const unsigned long long key = *reinterpret_cast<const unsigned long long*>(&sg.st[LG_PK]);
+  const int kp = key ? (int)(0xffffffffu - (unsigned)(key & 0xffffffffull)) : 0;
+  const float vmax = __uint_as_float((unsigned)(key >> 32));
+  int tie = 0, step;
+  for (int k = first_signal_point(step); k < G.S.P; k += step) {
+    if (k == 0) continue;
+    const float2 z = sg.spec[k];
+    tie |= k != kp && fmaf(z.x, z.x, z.y * z.y) >= vmax * (1.f - 1e-5f) && vmax > 0.f;
+  }
+  tie = __syncthreads_or(tie);
+  if (tie && threadIdx.x == 0) atomicOr(&sg.st[LG_PTIE], 1);
 }
 
 // Bookkeeping of the IMF extracted in the previous iteration and the outer
@@ -325,7 +373,16 @@ __global__ void lg_ctl(const LgSig* __restrict__ sigs, LgSched G, MethodParams m
     e.tie = 0;  // the input itself is exact on both sides
   }
   int L = 0, iflags = e.tie ? FIF_FLAG_EXTREMA_TIE : 0;
-  const int reason = outer_test(e.k, K, n, mp, io.mask_len, L, iflags);
+  int peak = 0;
+  if (mp.peak_mask) {
+    const unsigned long long key = *reinterpret_cast<const unsigned long long*>(&st[LG_PK]);
+    peak = key ? (int)(0xffffffffu - (unsigned)(key & 0xffffffffull)) : 0;
+    if (st[LG_PTIE]) iflags |= FIF_FLAG_EXTREMA_TIE;
+    st[LG_PK] = 0;
+    st[LG_PK_HI] = 0;
+    st[LG_PTIE] = 0;
+  }
+  const int reason = outer_test(e.k, K, n, mp, io.mask_len, L, iflags, peak);
   if (io.diag) {
     io.diag[K].k_extrema = e.k;
     io.diag[K].zero_crossings = e.zc;
@@ -873,7 +930,7 @@ __global__ void lg_epilogue_ext(const LgSig* __restrict__ sigs, LgSched G, int i
       const float dm = b - ra, d0 = c - b, dp = d - c;
       ext += (dm > 0.f && d0 < 0.f) || (dm < 0.f && d0 > 0.f);
       zc += (b > 0.f && c < 0.f) || (b < 0.f && c > 0.f);
-      tie |= fabsf(d0) <= tau && (fabsf(dm) <= tau || fabsf(dp) <= tau || ((dm > 0.f) == (dp > 0.f)));
+      tie |= diff_tie(dm, d0, dp, tau);
     }
   }
   tie = __syncthreads_or(tie);
@@ -1020,6 +1077,10 @@ cudaError_t large_run(const LgSched& G, const LgSig* d_sigs, int nsig, const Met
   for (int it = 0; e == cudaSuccess && it <= mp.max_imfs; it++) {
     // the extrema of the input; later iterations count in the epilogue
     if (it == 0) lg_extrema<<<dim3(bx_n, nsig), 256, 0, st>>>(d_sigs, G);
+    if (mp.peak_mask) {
+      lg_peak<<<dim3(bx_bins, nsig), 256, 0, st>>>(d_sigs, G);
+      lg_peak_tie<<<dim3(bx_bins, nsig), 256, 0, st>>>(d_sigs, G);
+    }
     lg_ctl<<<nsig, 1, 0, st>>>(d_sigs, G, mp, it, signals, out);
     lg_row<<<dim3(bx_bins, nsig), 256, 0, st>>>(d_sigs, G, it, out.imfs);
     if (cta_select) {

@@ -86,11 +86,15 @@ __global__ void __launch_bounds__(512, 1) na_forward(FftSched S, const float* __
 
 // Outer-loop test; on a stop, writes the remainder row and the status.
 __global__ void na_outer(FftSched S, NaScratch scr, Outputs out, MethodParams mp) {
+  __shared__ RedScratch red;
   int* st = scr.state;
   if (st[NA_DONE]) return;
   const int K = st[NA_K], k = st[NA_K_EXT];
   int L = 0, iflags = st[NA_TIE] ? FIF_FLAG_EXTREMA_TIE : 0;
-  const int reason = outer_test(k, K, S.n, mp, out.mask_len, L, iflags);
+  SpecPeak pk{0, 0};
+  if (mp.peak_mask) pk = spectral_peak(scr.spec, S, &red);
+  if (pk.tie) iflags |= FIF_FLAG_EXTREMA_TIE;
+  const int reason = outer_test(k, K, S.n, mp, out.mask_len, L, iflags, pk.k);
   if (out.diag && threadIdx.x == 0) {
     out.diag[K].k_extrema = k;
     out.diag[K].zero_crossings = st[NA_ZC];
@@ -275,7 +279,8 @@ extern "C" fif_status fif_decompose_noalloc(const fif_plan_desc* d, const float*
   if (!d || !signal || !imfs || !n_imfs || !sig_status) return FIF_EINVAL;
   if (d->window != FIF_WIN_TRIANGLE || !(d->delta > 0.0) || !isfinite(d->delta) ||
       d->max_inner < 1 || d->max_inner > (1 << 20) || d->max_imfs < 0 || d->max_imfs > kMaxImfs ||
-      (d->flags & ~(FIF_FORCE_L | FIF_APRIORI_N0)) || !(d->gamma >= 0.0 && d->gamma < 1.0))
+      (d->flags & ~(FIF_FORCE_L | FIF_APRIORI_N0 | FIF_PEAK_MASK)) ||
+      !(d->gamma >= 0.0 && d->gamma < 1.0))
     return FIF_EINVAL;
   if (!(d->flags & FIF_FORCE_L) &&
       (!(d->nu > 0.0) || !isfinite(d->nu) || d->mask_scale < 1 || d->mask_scale > 2))
@@ -360,6 +365,7 @@ extern "C" fif_status fif_decompose_noalloc(const fif_plan_desc* d, const float*
   mp.max_imfs = d->max_imfs;
   mp.force_L = (d->flags & FIF_FORCE_L) ? 1 : 0;
   mp.apriori = (d->flags & FIF_APRIORI_N0) ? 1 : 0;
+  mp.peak_mask = (d->flags & FIF_PEAK_MASK) ? 1 : 0;
   mp.threshold = d->gamma > 0.0 ? 1 : 0;
   mp.gamma = d->gamma;
   mp.log2_keep = d->gamma > 0.0 ? (float)log2(1.0 - d->gamma) : 0.f;

@@ -56,7 +56,10 @@ __global__ void __launch_bounds__(512, 1) staged_select(FftSched S, StagedScratc
   if (st[ST_DONE]) return;
   const int K = st[ST_K], k = st[ST_K_EXT], tie = st[ST_TIE];
   int L = 0, iflags = tie ? FIF_FLAG_EXTREMA_TIE : 0;
-  const int reason = outer_test(k, K, S.n, mp, out.mask_len, L, iflags);
+  SpecPeak pk{0, 0};
+  if (mp.peak_mask) pk = spectral_peak(scr.spec, S, &red);
+  if (pk.tie) iflags |= FIF_FLAG_EXTREMA_TIE;
+  const int reason = outer_test(k, K, S.n, mp, out.mask_len, L, iflags, pk.k);
   if (out.diag && threadIdx.x == 0) {
     out.diag[K].k_extrema = k;
     out.diag[K].zero_crossings = st[ST_ZC];

@@ -36,6 +36,7 @@ FLAG_L_CLAMPED = 1 << 12
 FORCE_L = 1
 FORCE_MULTIPASS = 2
 APRIORI_N0 = 4
+PEAK_MASK = 8
 
 # every symbol include/fif.h declares
 EXPORTS = ("fif_plan_create", "fif_plan_destroy", "fif_plan_set_stream", "fif_plan_prepare",
@@ -182,7 +183,7 @@ class Plan:
     def __init__(self, *, nu: float = 1.6, mask_scale: int = 1, delta: float = 1e-3,
                  max_inner: int = 200, max_imfs: int = 10, max_n: int = 16384,
                  force_L: bool = False, multipass: bool = False, apriori_n0: bool = False,
-                 gamma: float = 0.0, stream=None):
+                 gamma: float = 0.0, peak_mask: bool = False, stream=None):
         import torch
         lib = load_library()
         self.max_imfs = max_imfs
@@ -190,7 +191,8 @@ class Plan:
         self.force_L = force_L
         self.desc = PlanDesc(0, nu, mask_scale, delta, max_inner, max_imfs, 0, max_n,
                              (FORCE_L if force_L else 0) | (FORCE_MULTIPASS if multipass else 0)
-                             | (APRIORI_N0 if apriori_n0 else 0), float(gamma))
+                             | (APRIORI_N0 if apriori_n0 else 0) | (PEAK_MASK if peak_mask else 0),
+                             float(gamma))
         if stream is None:
             stream = torch.cuda.current_stream()
         self._stream = stream
@@ -346,7 +348,8 @@ class Plan:
 
 def decompose_noalloc(signal, *, nu: float = 1.6, mask_scale: int = 1, delta: float = 1e-3,
                       max_inner: int = 200, max_imfs: int = 10, mask_len=None, diag: bool = False,
-                      apriori_n0: bool = False, gamma: float = 0.0, stream=None) -> Decomposition:
+                      apriori_n0: bool = False, gamma: float = 0.0, peak_mask: bool = False,
+                      stream=None) -> Decomposition:
     """fif_decompose_noalloc on one float32 CUDA tensor (no plan, no device allocation
     inside the library; the output tensors are allocated here by PyTorch)."""
     import torch
@@ -356,8 +359,8 @@ def decompose_noalloc(signal, *, nu: float = 1.6, mask_scale: int = 1, delta: fl
     dev = signal.device
     K = max_imfs
     desc = PlanDesc(0, nu, mask_scale, delta, max_inner, max_imfs, 0, n,
-                    (FORCE_L if mask_len is not None else 0) | (APRIORI_N0 if apriori_n0 else 0),
-                    float(gamma))
+                    (FORCE_L if mask_len is not None else 0) | (APRIORI_N0 if apriori_n0 else 0)
+                    | (PEAK_MASK if peak_mask else 0), float(gamma))
     imfs = torch.zeros((K + 1, n), dtype=torch.float32, device=dev)
     m = torch.zeros(max(K, 1), dtype=torch.int32, device=dev)
     L = torch.zeros(max(K, 1), dtype=torch.int32, device=dev)

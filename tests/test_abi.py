@@ -49,7 +49,7 @@ def _desc(**kw):
 @pytest.mark.parametrize("bad", [dict(delta=0.0), dict(delta=-1.0), dict(max_inner=0),
                                  dict(max_imfs=-1), dict(max_imfs=65), dict(max_n=3),
                                  dict(max_n=(1 << 24) + 1), dict(window=7), dict(mask_scale=0),
-                                 dict(mask_scale=3), dict(nu=0.0), dict(flags=8), dict(flags=16),
+                                 dict(mask_scale=3), dict(nu=0.0), dict(flags=16), dict(flags=32),
                                  dict(delta=float("nan")), dict(gamma=1.0), dict(gamma=-0.1),
                                  dict(gamma=float("nan"))])
 def test_plan_descriptor_validation(lib, bad):
