@@ -64,7 +64,8 @@ class _Params(ctypes.Structure):
     _fields_ = [("nu", ctypes.c_double), ("mask_scale", ctypes.c_int), ("delta", ctypes.c_double),
                 ("max_inner", ctypes.c_int), ("max_imfs", ctypes.c_int),
                 ("L_in", ctypes.POINTER(ctypes.c_int)), ("absolute", ctypes.c_int),
-                ("apriori", ctypes.c_int), ("gamma", ctypes.c_double), ("peak_mask", ctypes.c_int)]
+                ("apriori", ctypes.c_int), ("gamma", ctypes.c_double), ("peak_mask", ctypes.c_int),
+                ("shape", ctypes.POINTER(ctypes.c_double)), ("shape_len", ctypes.c_int)]
 
 
 class _Outputs(ctypes.Structure):
@@ -99,6 +100,11 @@ def _load():
             lib.fifo_apriori_n0.restype = ctypes.c_int
             lib.fifo_spectral_peak.argtypes = [dp, dp, ctypes.c_long, ctypes.POINTER(ctypes.c_int)]
             lib.fifo_spectral_peak.restype = ctypes.c_long
+            for f in ("fifo_shape_taps", "fifo_shape_spectrum"):
+                getattr(lib, f).argtypes = [ctypes.c_long, ctypes.c_int, dp, ctypes.c_int, dp]
+                getattr(lib, f).restype = ctypes.c_int
+            lib.fifo_shape_filter.argtypes = [dp, ctypes.c_int, ctypes.c_int, dp]
+            lib.fifo_shape_filter.restype = ctypes.c_int
             _lib = lib
     return _lib
 
@@ -147,6 +153,34 @@ def window_spectrum(n: int, L: int) -> np.ndarray:
     return w
 
 
+def _shape_call(fn, n, L, g):
+    g = _as_f64(g)
+    out = np.empty(n)
+    rc = getattr(_load(), fn)(n, L, _dptr(g), g.size, _dptr(out))
+    if rc != 0:
+        raise ValueError(f"{fn}: invalid shape or length (rc={rc})")
+    return out
+
+
+def shape_filter(L: int, g) -> np.ndarray:
+    """The generating filter h_i = g((i + 1/2)/L), i < L, of a shape window."""
+    g = _as_f64(g)
+    h = np.empty(L)
+    if _load().fifo_shape_filter(_dptr(g), g.size, L, _dptr(h)) != 0:
+        raise ValueError("fifo_shape_filter: invalid shape or length")
+    return h
+
+
+def shape_taps(n: int, L: int, g) -> np.ndarray:
+    """Taps (h * h normalised, at d mod n) of the window generated by shape g."""
+    return _shape_call("fifo_shape_taps", n, L, g)
+
+
+def shape_spectrum(n: int, L: int, g) -> np.ndarray:
+    """w_hat_k, k < n, of the window generated by shape g (DFT of its taps)."""
+    return _shape_call("fifo_shape_spectrum", n, L, g)
+
+
 def count_extrema(r) -> int:
     r = _as_f64(r)
     return int(_load().fifo_count_extrema(_dptr(r), r.size))
@@ -180,14 +214,20 @@ def mask_length(n: int, k: int, nu: float = 1.6, mask_scale: int = 1) -> int:
 
 
 def _run(fn_name, s, *, nu=1.6, mask_scale=1, delta=1e-3, max_inner=200, max_imfs=10,
-         force_L=None, absolute=False, apriori=False, gamma=0.0, peak_mask=False, trace=False):
+         force_L=None, absolute=False, apriori=False, gamma=0.0, peak_mask=False, shape=None,
+         trace=False):
     lib = _load()
     s = _as_f64(s)
     n = s.size
     keep = []
     p = _Params(nu=nu, mask_scale=mask_scale, delta=delta, max_inner=max_inner, max_imfs=max_imfs,
                 L_in=None, absolute=1 if absolute else 0, apriori=1 if apriori else 0,
-                gamma=float(gamma), peak_mask=1 if peak_mask else 0)
+                gamma=float(gamma), peak_mask=1 if peak_mask else 0, shape=None, shape_len=0)
+    if shape is not None:
+        g = _as_f64(shape).copy()
+        keep.append(g)
+        p.shape = _dptr(g)
+        p.shape_len = g.size
     if force_L is not None:
         Lin = np.zeros(max(max_imfs, 1), dtype=np.int32)
         fl = np.asarray(force_L, dtype=np.int32)[:max_imfs]

@@ -17,7 +17,12 @@
  *    period, Sec. 3.1 asks l <= (n-1)/2);
  *  - m counts applications of (I-W); SD_j compares iterates j and j-1;
  *    m = first j in [1, max_inner] with SD_j < delta, else max_inner;
- *  - 0^0 = 1 (the DC bin keeps weight 1 at j = 1).
+ *  - 0^0 = 1 (the DC bin keeps weight 1 at j = 1);
+ *  - a shape window takes the double-convolution construction of Theorem 4
+ *    discretely: the filter h samples the shape at the cell midpoints
+ *    (i + 1/2)/L, i < L, and the window is h * h divided by its sum, so its
+ *    half-support is L like the triangle's, and a constant shape gives back
+ *    the triangle (box * box) exactly.
  */
 #include "fif_oracle.h"
 
@@ -145,6 +150,123 @@ void fifo_window_spectrum(long n, int L, double* w) {
   }
 }
 
+/* A shape g is usable when its samples are finite and >= 0 and its linear
+ * interpolant is > 0 on the open interval (0, 1): every h_i is then > 0 and
+ * the window has a positive sum. */
+static int shape_valid(const double* g, int glen) {
+  if (!g || glen < 1) return 0;
+  for (int j = 0; j < glen; j++)
+    if (!isfinite(g[j]) || g[j] < 0.0) return 0;
+  if (glen == 1) return g[0] > 0.0;
+  if (glen == 2) return g[0] + g[1] > 0.0;
+  for (int j = 1; j < glen - 1; j++)
+    if (!(g[j] > 0.0)) return 0;
+  return 1;
+}
+
+/* Generating filter of half-support L: h_i = g((i + 1/2)/L), i = 0..L-1,
+ * with g the piecewise-linear interpolant of glen equispaced samples on
+ * [0, 1] (a constant when glen = 1).  The window of eq. W_m is then the
+ * autocorrelation of h (the double-convolution construction of Theorem 4),
+ * so its spectrum is |DFT(h)|^2 / (sum h)^2, inside [0, 1]. */
+int fifo_shape_filter(const double* g, int glen, int L, double* h) {
+  if (!shape_valid(g, glen) || L < 1 || !h) return -1;
+  for (int i = 0; i < L; i++) {
+    if (glen == 1) {
+      h[i] = g[0];
+      continue;
+    }
+    const double t = ((double)i + 0.5) / (double)L * (double)(glen - 1);
+    int j = (int)floor(t);
+    if (j > glen - 2) j = glen - 2;
+    const double f = t - (double)j;
+    h[i] = (1.0 - f) * g[j] + f * g[j + 1];
+  }
+  return 0;
+}
+
+/* a[d] = sum_i h_i h_{i+d}, d = 0..L-1 (the autocorrelation of h, even in d). */
+static int shape_autocorrelation(const double* g, int glen, int L, double* a) {
+  double* h = malloc((size_t)L * sizeof(double));
+  if (!h) return -2;
+  const int rc = fifo_shape_filter(g, glen, L, h);
+  if (rc == 0)
+    for (int d = 0; d < L; d++) {
+      double v = 0.0;
+      for (int i = 0; i + d < L; i++) v += h[i] * h[i + d];
+      a[d] = v;
+    }
+  free(h);
+  return rc;
+}
+
+/* Taps of the shape window at the offsets |d| < L, stored circularly at
+ * index d mod n and divided by their sum (row-stochastic W, as for the
+ * triangle). */
+int fifo_shape_taps(long n, int L, const double* g, int glen, double* c) {
+  if (L < 1 || n < 1 || !c) return -1;
+  double* a = malloc((size_t)L * sizeof(double));
+  if (!a) return -2;
+  const int rc = shape_autocorrelation(g, glen, L, a);
+  if (rc == 0) {
+    for (long i = 0; i < n; i++) c[i] = 0.0;
+    double sum = 0.0;
+    for (long d = -(L - 1); d <= L - 1; d++) {
+      const double v = a[d < 0 ? -d : d];
+      c[((d % n) + n) % n] += v;
+      sum += v;
+    }
+    for (long i = 0; i < n; i++) c[i] /= sum;
+  }
+  free(a);
+  return rc;
+}
+
+/* cos(2 pi q / n) for an integer q, with the argument reduced exactly. */
+static double cos2pi_ratio(long long q, long n) {
+  long long t = q % (long long)n;
+  if (t < 0) t += n;
+  return cos(2.0 * M_PI * (double)t / (double)n);
+}
+
+/* Eigenvalues of the circulant W of the shape window (eq. Lambdas): the DFT
+ * of its even taps, w_hat_k = (a_0 + 2 sum_{d>=1} a_d cos(2 pi k d/n)) /
+ * (a_0 + 2 sum_{d>=1} a_d), by the definition; clamped to [0, 1]. */
+int fifo_shape_spectrum(long n, int L, const double* g, int glen, double* w) {
+  if (L < 1 || n < 1 || !w) return -1;
+  double* a = malloc((size_t)L * sizeof(double));
+  if (!a) return -2;
+  const int rc = shape_autocorrelation(g, glen, L, a);
+  if (rc == 0) {
+    double sum = a[0];
+    for (int d = 1; d < L; d++) sum += 2.0 * a[d];
+    for (long k = 0; k < n; k++) {
+      double v = a[0];
+      for (int d = 1; d < L; d++) v += 2.0 * a[d] * cos2pi_ratio((long long)k * d, n);
+      v /= sum;
+      if (v > 1.0) v = 1.0;
+      if (v < 0.0) v = 0.0;
+      w[k] = v;
+    }
+    w[0] = 1.0;
+  }
+  free(a);
+  return rc;
+}
+
+/* The window the parameters select: taps (tier A) and spectrum (tier B). */
+static int window_taps(long n, int L, const fifo_params* p, double* c) {
+  if (p->shape) return fifo_shape_taps(n, L, p->shape, p->shape_len, c);
+  fifo_triangle_taps(n, L, c);
+  return 0;
+}
+
+static int window_spectrum(long n, int L, const fifo_params* p, double* w) {
+  if (p->shape) return fifo_shape_spectrum(n, L, p->shape, p->shape_len, w);
+  fifo_window_spectrum(n, L, w);
+  return 0;
+}
+
 long fifo_count_extrema(const double* r, long n) {
   long count = 0;
   for (long i = 0; i < n; i++) {
@@ -180,6 +302,7 @@ static int check_args(const double* s, long n, const fifo_params* p, const fifo_
     return -1;
   if (!(p->delta > 0.0) || p->max_inner < 1 || p->max_imfs < 0) return -1;
   if (!p->L_in && (!(p->nu > 0.0) || p->mask_scale < 1)) return -1;
+  if (p->shape && (!shape_valid(p->shape, p->shape_len) || p->apriori)) return -1;
   return 0;
 }
 
@@ -329,7 +452,10 @@ int fifo_iterative(const double* s, long n, const fifo_params* p, const fifo_out
     }
     reason = outer_test(r, n, K, p, o->kext, &L, &flags, peak, ptie);
     if (reason) break;
-    fifo_triangle_taps(n, L, c);
+    if (window_taps(n, L, p, c)) { /* the shape was checked: out of memory */
+      free(r), free(u), free(v), free(c);
+      return -2;
+    }
     memcpy(u, r, (size_t)n * sizeof(double));
     double sd = INFINITY, sd_prev = INFINITY;
     int n0 = 0; /* a-priori mode: exactly n0 applications of (I - W) */
@@ -436,7 +562,10 @@ int fifo_direct(const double* s, long n, const fifo_params* p, const fifo_output
     const long peak = p->peak_mask ? fifo_spectral_peak(Rre, Rim, n, &ptie) : 0;
     reason = outer_test(r, n, K, p, o->kext, &L, &flags, peak, ptie);
     if (reason) break;
-    fifo_window_spectrum(n, L, w);
+    if (window_spectrum(n, L, p, w)) { /* the shape was checked: out of memory */
+      free(r), free(Rre), free(Rim), free(Ire), free(Iim), free(w), free(E);
+      return -2;
+    }
     for (long k = 0; k < n; k++) E[k] = Rre[k] * Rre[k] + Rim[k] * Rim[k];
     double sd = INFINITY, sd_prev = INFINITY;
     int j;

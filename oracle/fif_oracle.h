@@ -58,6 +58,13 @@ typedef struct {
                          (eq. IMF_cont_stop_threshold; direct method only) */
   int peak_mask;      /* 1: L from the largest spectral peak k* of r (end of Sec. 2):
                          the mask rule with k = 2 k*; the extrema count still stops */
+  const double* shape; /* NULL: the triangle.  Else the generating filter's shape g on [0, 1],
+                          shape_len >= 1 equispaced samples (linear interpolation; one sample
+                          = a constant): the window of half-support L is the autocorrelation
+                          h * h of h_i = g((i + 1/2)/L), i < L (Theorem 4 setting, eq. W_m),
+                          divided by its sum.  g >= 0 with g > 0 inside (0, 1).  Not with
+                          apriori (its zero-eigenvalue count is the triangle's closed form). */
+  int shape_len;
 } fifo_params;
 
 /* Per-call outputs.  imfs: (max_imfs+1)*n doubles, row K = IMF K, row n_imfs
@@ -95,6 +102,13 @@ int fifo_apriori_n0(double snorm, long n, long kzero, double delta, int max_inne
 long fifo_spectral_peak(const double* re, const double* im, long n, int* tie);
 void fifo_triangle_taps(long n, int L, double* c);   /* c[d mod n], normalized by the sum */
 void fifo_window_spectrum(long n, int L, double* w); /* closed form, k = 0..n-1 */
+/* Shape-generated window (see fifo_params.shape): the generating filter
+ * h_0..h_{L-1}, its autocorrelation taps c[d mod n] (normalized by the sum)
+ * and their DFT w_hat_k, k = 0..n-1, by the definition (clamped to [0, 1]).
+ * Each returns -1 for an invalid shape or L < 1, -2 if out of memory. */
+int fifo_shape_filter(const double* g, int glen, int L, double* h);
+int fifo_shape_taps(long n, int L, const double* g, int glen, double* c);
+int fifo_shape_spectrum(long n, int L, const double* g, int glen, double* w);
 long fifo_count_extrema(const double* r, long n);
 long fifo_count_zero_crossings(const double* r, long n);
 int fifo_mask_length(long n, long k, double nu, int mask_scale);

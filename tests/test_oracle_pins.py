@@ -615,3 +615,117 @@ def test_peak_mask_direct_equals_iterative(oracle_mod, seed, n):
     K = int(a["n_imfs"])
     assert K == int(b["n_imfs"]) and np.array_equal(a["L"], b["L"]) and np.array_equal(a["m"], b["m"])
     assert np.abs(a["imfs"] - b["imfs"]).max() < 1e-10 * np.abs(s).max()
+
+
+# ------------------------------------------- shape-generated windows (f4)
+
+SHAPES = {
+    "sine": np.sin(np.pi * np.linspace(0.0, 1.0, 33)),          # zero ends, positive inside
+    "ramp": np.array([0.2, 1.0]),                               # skewed: h is not symmetric
+    "hat": np.array([0.0, 1.0, 0.0]),
+    "rough": np.random.default_rng(11).uniform(0.1, 1.0, 7),
+}
+
+
+@pytest.mark.parametrize("g", [[1.0], [2.5], [1.0, 1.0], [3.0, 3.0, 3.0]])
+@pytest.mark.parametrize("n,L", [(64, 5), (65, 9), (128, 30), (243, 121)])
+def test_constant_shape_gives_the_triangle(oracle_mod, g, n, L):
+    """A constant shape generates a box, and box * box is the triangle
+    (Theorem 4's construction): taps and spectrum equal the triangle's closed
+    form (eq. triangular, eq. eig2)."""
+    assert np.abs(oracle_mod.shape_taps(n, L, g) - oracle_mod.taps(n, L)).max() < 1e-16
+    assert np.abs(oracle_mod.shape_spectrum(n, L, g) - _what_closed_form(n, L)).max() < 2e-14
+
+
+def test_constant_shape_decomposition_is_the_triangles(oracle_mod):
+    s = signals.component_signal(98, 2, 384).astype(np.float64)
+    for tier in ("direct", "iterative"):
+        a = getattr(oracle_mod, tier)(s, max_imfs=4, max_inner=80)
+        b = getattr(oracle_mod, tier)(s, max_imfs=4, max_inner=80, shape=[1.0])
+        assert a["status"] == b["status"] and np.array_equal(a["m"], b["m"])
+        assert np.array_equal(a["L"], b["L"])
+        assert np.abs(a["imfs"] - b["imfs"]).max() < 1e-12 * np.abs(s).max()
+
+
+@pytest.mark.parametrize("L", [1, 2, 7, 40])
+def test_shape_filter_samples_cell_midpoints(oracle_mod, L):
+    x = (np.arange(L) + 0.5) / L
+    assert np.array_equal(oracle_mod.shape_filter(L, [0.7]), np.full(L, 0.7))
+    assert np.allclose(oracle_mod.shape_filter(L, [0.2, 1.0]), 0.2 + 0.8 * x, rtol=0, atol=1e-15)
+    assert np.allclose(oracle_mod.shape_filter(L, [0.0, 1.0, 0.0]), 1.0 - np.abs(2 * x - 1),
+                       rtol=0, atol=1e-15)
+
+
+@pytest.mark.parametrize("name", sorted(SHAPES))
+@pytest.mark.parametrize("n,L", [(96, 11), (97, 30), (256, 100), (60, 1)])
+def test_shape_spectrum_is_the_squared_filter_spectrum(oracle_mod, name, n, L):
+    """The window is h * h, so w_hat = |DFT(h)|^2 / (sum h)^2 (the
+    autocorrelation theorem; numpy's FFT of h, an independent route), in
+    [0, 1] with w_hat_0 = 1.  The taps are even, sum to 1 and vanish for
+    |d| >= L."""
+    g = SHAPES[name]
+    h = oracle_mod.shape_filter(L, g)
+    assert (h > 0).all()
+    ref = np.abs(np.fft.fft(h, n)) ** 2 / h.sum() ** 2
+    w = oracle_mod.shape_spectrum(n, L, g)
+    assert np.abs(w - ref).max() < 1e-13
+    assert w[0] == 1.0 and (w >= 0).all() and (w <= 1).all()
+    c = oracle_mod.shape_taps(n, L, g)
+    assert abs(c.sum() - 1) < 1e-14
+    d = np.arange(n)
+    assert np.allclose(c, c[(-d) % n], rtol=0, atol=1e-17)
+    support = (d < L) | (d > n - L)
+    assert (c[~support] == 0).all() and (c[support] > 0).all()
+
+
+def test_shape_pure_tone_scaled_by_multiplier(oracle_mod):
+    """A tone at bin k0 is an eigenvector of the circulant W: with SD_j =
+    w_hat_k0 for every j (eq. SD), m = max_inner here and the IMF is
+    (1 - w_hat_k0)^m times the tone, w_hat from numpy's FFT of h."""
+    n, k0, L = 512, 6, 25
+    g = SHAPES["sine"]
+    s = np.cos(2 * np.pi * k0 * np.arange(n) / n + 0.4)
+    h = oracle_mod.shape_filter(L, g)
+    lam = np.abs(np.fft.fft(h, n)[k0]) ** 2 / h.sum() ** 2
+    assert 1e-3 < lam < 0.9
+    for tier in ("direct", "iterative"):
+        r = getattr(oracle_mod, tier)(s, force_L=[L], max_imfs=1, max_inner=120, shape=g)
+        assert r["m"][0] == 120 and r["L"][0] == L
+        assert np.abs(r["imfs"][0] - (1 - lam) ** 120 * s).max() < 1e-13
+
+
+@pytest.mark.parametrize("name", ["sine", "ramp", "rough"])
+@pytest.mark.parametrize("seed,n,delta", [(0, 128, 1e-3), (3, 729, 1e-2), (6, 512, 3e-2)])
+def test_shape_direct_equals_iterative(oracle_mod, name, seed, n, delta):
+    s = signals.component_signal(98, seed, n).astype(np.float64)
+    kw = dict(max_imfs=5, max_inner=80, delta=delta, shape=SHAPES[name], trace=True)
+    a, b = oracle_mod.iterative(s, **kw), oracle_mod.direct(s, **kw)
+    assert a["n_imfs"] == b["n_imfs"] and a["status"] == b["status"]
+    assert np.array_equal(a["m"], b["m"]) and np.array_equal(a["L"], b["L"])
+    for i in range(a["n_imfs"]):
+        assert rel(a["imfs"][i], b["imfs"][i]) < 1e-11
+        mm = a["m"][i]
+        assert np.allclose(a["sd_trace"][i][:mm], b["sd_trace"][i][:mm], rtol=1e-10, atol=0)
+    assert rel(a["remainder"], b["remainder"]) < 1e-11
+
+
+def test_shape_windows_change_the_decomposition(oracle_mod):
+    """The shape reaches the result: a non-constant shape gives other m and IMFs."""
+    s = signals.component_signal(98, 6, 512).astype(np.float64)
+    a = oracle_mod.direct(s, max_imfs=4, max_inner=80, delta=3e-2)
+    b = oracle_mod.direct(s, max_imfs=4, max_inner=80, delta=3e-2, shape=SHAPES["sine"])
+    assert not np.array_equal(a["m"], b["m"])
+    assert rel(a["imfs"][0], b["imfs"][0]) > 1e-2
+
+
+@pytest.mark.parametrize("g", [[], [-1.0, 1.0], [1.0, np.nan], [1.0, 0.0, 1.0], [0.0], [0.0, 0.0]])
+def test_invalid_shapes_are_rejected(oracle_mod, g):
+    s = signals.component_signal(98, 0, 64).astype(np.float64)
+    with pytest.raises(ValueError):
+        oracle_mod.direct(s, shape=np.asarray(g, dtype=np.float64))
+
+
+def test_shape_with_apriori_is_rejected(oracle_mod):
+    s = signals.component_signal(98, 0, 64).astype(np.float64)
+    with pytest.raises(ValueError):
+        oracle_mod.direct(s, shape=[1.0], apriori=True)
