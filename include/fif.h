@@ -55,7 +55,18 @@ typedef enum {
 } fif_status;
 
 typedef enum {
-  FIF_WIN_TRIANGLE = 0   /* eq. triangular, sampled; w_hat = [sin(pi k L/n) / (L sin(pi k/n))]^2 */
+  FIF_WIN_TRIANGLE = 0,  /* eq. triangular, sampled; w_hat = [sin(pi k L/n) / (L sin(pi k/n))]^2 */
+  FIF_WIN_SHAPE = 1      /* generated by a shape g (Theorem 4's double convolution, eq. W_m): the
+                            filter h_i = g((i + 1/2)/L), i < L, g the piecewise-linear
+                            interpolant of fif_plan_desc.window_shape on [0, 1] (one sample = a
+                            constant); the window is the autocorrelation h * h divided by its
+                            sum, half-support L like the triangle's, and
+                            w_hat_k = |DFT(h)_k|^2 / (sum h)^2 in [0, 1].  A constant shape is
+                            the triangle.  Tabulated for every L when the plan first meets a
+                            length n (Lmax * P * 16 bytes of device memory, Lmax = (n+1)/2,
+                            P = n/2+1).  Lengths that take the multi-pass path, FIF_APRIORI_N0,
+                            FIF_FORCE_MULTIPASS and fif_decompose_noalloc return
+                            FIF_EUNSUPPORTED with it. */
 } fif_window;
 
 typedef enum {
@@ -98,7 +109,7 @@ typedef enum {
                             second bin within 1e-5 (relative) of the peak. */
 
 typedef struct {
-  fif_window window;        /* FIF_WIN_TRIANGLE */
+  fif_window window;        /* FIF_WIN_TRIANGLE or FIF_WIN_SHAPE */
   double nu;                /* eq. Unif_Mask_length tuning parameter (1.6) */
   int32_t mask_scale;       /* leading factor of the mask rule: 1 (half-support L = floor(nu n/k))
                                or 2 (the paper's l = 2 floor(nu N/k)) */
@@ -113,6 +124,12 @@ typedef struct {
                                eq. IMF_cont_stop_threshold): with m chosen as usual, every bin
                                with (1 - w_hat_k)^m >= 1 - gamma passes whole into the IMF
                                (w_hat_k taken as 0) and leaves the remainder */
+  const double* window_shape;  /* FIF_WIN_SHAPE: HOST array of the shape's samples g_0..g_{len-1}
+                                  at x = j/(len-1) (copied by fif_plan_create): finite, >= 0,
+                                  and the interpolant > 0 inside (0, 1) (every interior sample
+                                  > 0; len 1: g_0 > 0; len 2: g_0 + g_1 > 0), else FIF_EINVAL.
+                                  Ignored for FIF_WIN_TRIANGLE. */
+  int32_t window_shape_len;    /* 1 .. 65536 */
 } fif_plan_desc;
 
 /* Optional per-IMF diagnostics, one record per outer step: record K < n_imfs

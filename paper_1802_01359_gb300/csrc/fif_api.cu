@@ -23,6 +23,7 @@ struct LengthTables {
   float2* tw_lo = nullptr;
   float2* wtab = nullptr;
   double* sin64 = nullptr;
+  double* om64 = nullptr;  // shape window only
 };
 
 struct BatchLayout {
@@ -91,6 +92,9 @@ struct fif_plan_s {
   std::map<int64_t, LargeBuffers> large_single_bufs;  // per length, fif_decompose
   // fused schedules chosen by fif_plan_tune / fif_plan_load_tuning: n -> E
   std::map<int64_t, int> fused_E;
+  // FIF_WIN_SHAPE: the shape's samples (host copy, and on the device)
+  std::vector<double> shape;
+  double* d_shape = nullptr;
   // branches of the batch graph: one per length class
   static constexpr int kBranches = 8;
   cudaStream_t aux[kBranches] = {nullptr};
@@ -252,20 +256,31 @@ fif_status get_tables(fif_plan_t p, int64_t n, LengthTables** out) {
   if (e == cudaSuccess) e = cudaMalloc(&t.tw_lo, sizeof(float2) * (size_t)s.n);
   if (e == cudaSuccess) e = cudaMalloc(&t.sin64, sizeof(double) * (size_t)(s.n / 2 + 1));
   if (e == cudaSuccess) e = cudaMalloc(&t.wtab, sizeof(float2) * (size_t)s.Lmax * (size_t)s.P);
-  if (e == cudaSuccess)
-    e = build_tables(s.n, s.P, s.Lmax, t.tw, t.tw_lo, t.wtab, t.sin64, p->stream);
+  if (e == cudaSuccess && p->d_shape)
+    e = cudaMalloc(&t.om64, sizeof(double) * (size_t)s.Lmax * (size_t)s.P);
+  t.sched.tw = t.tw;
+  t.sched.tw_lo = t.tw_lo;
+  t.sched.wtab = t.wtab;
+  t.sched.sin64 = t.sin64;
+  t.sched.om64 = t.om64;
+  if (e == cudaSuccess) {
+    if (p->d_shape) {
+      e = build_twiddles(s.n, t.tw, t.tw_lo, t.sin64, p->stream);
+      if (e == cudaSuccess)
+        e = build_shape_window(t.sched, p->d_shape, (int)p->shape.size(), t.wtab, t.om64, p->stream);
+    } else {
+      e = build_tables(s.n, s.P, s.Lmax, t.tw, t.tw_lo, t.wtab, t.sin64, p->stream);
+    }
+  }
   if (e != cudaSuccess) {
     cudaFree(t.tw);
     cudaFree(t.tw_lo);
     cudaFree(t.sin64);
     cudaFree(t.wtab);
+    cudaFree(t.om64);
     cudaGetLastError();
     return cuda_status(e);
   }
-  t.sched.tw = t.tw;
-  t.sched.tw_lo = t.tw_lo;
-  t.sched.wtab = t.wtab;
-  t.sched.sin64 = t.sin64;
   auto res = p->tables.emplace(n, t);
   *out = &res.first->second;
   return FIF_OK;
@@ -279,9 +294,26 @@ void free_layout(BatchLayout& l) {
   l = BatchLayout();
 }
 
+// A shape is usable when its samples are finite and >= 0 and its linear
+// interpolant is > 0 inside (0, 1), so that every filter tap h_i > 0.
+bool shape_valid(const double* g, int32_t len) {
+  if (!g || len < 1 || len > 65536) return false;
+  for (int32_t j = 0; j < len; j++)
+    if (!isfinite(g[j]) || g[j] < 0.0) return false;
+  if (len == 1) return g[0] > 0.0;
+  if (len == 2) return g[0] + g[1] > 0.0;
+  for (int32_t j = 1; j < len - 1; j++)
+    if (!(g[j] > 0.0)) return false;
+  return true;
+}
+
 fif_status validate_desc(const fif_plan_desc* d) {
   if (!d) return FIF_EINVAL;
-  if (d->window != FIF_WIN_TRIANGLE) return FIF_EINVAL;
+  if (d->window != FIF_WIN_TRIANGLE && d->window != FIF_WIN_SHAPE) return FIF_EINVAL;
+  if (d->window == FIF_WIN_SHAPE) {
+    if (!shape_valid(d->window_shape, d->window_shape_len)) return FIF_EINVAL;
+    if (d->flags & (FIF_APRIORI_N0 | FIF_FORCE_MULTIPASS)) return FIF_EUNSUPPORTED;
+  }
   if (d->precision != FIF_PREC_FP32) return FIF_EUNSUPPORTED;
   if (!(d->delta > 0.0) || !isfinite(d->delta)) return FIF_EINVAL;
   if (d->max_inner < 1 || d->max_inner > (1 << 20)) return FIF_EINVAL;
@@ -428,6 +460,7 @@ fif_status get_large(fif_plan_t p, int64_t n, LargeTables** out) {
     *out = &it->second;
     return FIF_OK;
   }
+  if (p->d_shape) return FIF_EUNSUPPORTED;  // the multi-pass path has the triangle only
   LargeTables lt;
   if (!make_large_sched(n, p->smem_optin, lt.G)) return FIF_EUNSUPPORTED;
   LgSched& G = lt.G;
@@ -736,6 +769,13 @@ fif_status fif_plan_create(fif_plan_t* out, const fif_plan_desc* desc, void* cud
   fif_plan_s* p = new (std::nothrow) fif_plan_s();
   if (!p) return FIF_ENOMEM;
   p->desc = *desc;
+  if (desc->window == FIF_WIN_SHAPE) {
+    p->shape.assign(desc->window_shape, desc->window_shape + desc->window_shape_len);
+    p->desc.window_shape = p->shape.data();
+  } else {
+    p->desc.window_shape = nullptr;
+    p->desc.window_shape_len = 0;
+  }
   p->mp.nu = desc->nu;
   p->mp.delta = desc->delta;
   p->mp.delta2 = (float)(desc->delta * desc->delta);
@@ -759,6 +799,12 @@ fif_status fif_plan_create(fif_plan_t* out, const fif_plan_desc* desc, void* cud
   if (e == cudaSuccess) e = cudaMalloc(&p->scr.work, sizeof(float2) * (size_t)(n + 2));
   if (e == cudaSuccess) e = cudaMalloc(&p->scr.rem, sizeof(float) * (size_t)n);
   if (e == cudaSuccess) e = cudaMalloc(&p->scr.state, sizeof(int) * 16);
+  if (e == cudaSuccess && !p->shape.empty()) {
+    e = cudaMalloc(&p->d_shape, sizeof(double) * p->shape.size());
+    if (e == cudaSuccess)
+      e = cudaMemcpy(p->d_shape, p->shape.data(), sizeof(double) * p->shape.size(),
+                     cudaMemcpyHostToDevice);
+  }
   if (e != cudaSuccess) {
     fif_plan_destroy(p);
     cudaGetLastError();
@@ -787,7 +833,9 @@ fif_status fif_plan_destroy(fif_plan_t p) {
     cudaFree(kv.second.tw_lo);
     cudaFree(kv.second.wtab);
     cudaFree(kv.second.sin64);
+    cudaFree(kv.second.om64);
   }
+  cudaFree(p->d_shape);
   free_layout(p->layout);
   for (auto& kv : p->large)
     for (void* a : kv.second.allocs) cudaFree(a);
@@ -819,7 +867,10 @@ fif_status fif_plan_prepare(fif_plan_t p, const int64_t* lengths, int64_t count)
   for (int64_t i = 0; i < count; i++) {
     if (lengths[i] > p->desc.max_n || !is_smooth(lengths[i])) return FIF_EUNSUPPORTED;
     fif_status st;
-    if (fits_fused(p, lengths[i])) {
+    FftSched probe;
+    if (fits_fused(p, lengths[i]) ||
+        (p->d_shape && make_sched(lengths[i], probe, p->smem_optin) &&
+         staged_fits(probe, p->smem_optin))) {
       LengthTables* t = nullptr;
       st = get_tables(p, lengths[i], &t);
     } else {

@@ -574,6 +574,21 @@ __device__ __forceinline__ double what64(const FftSched& S, int L, int k) {
   return w > 1.0 ? 1.0 : (w < 0.0 ? 0.0 : w);
 }
 
+// w_hat_k, 1 - w_hat_k and log2(1 - w_hat_k) in binary64: the closed form for
+// the triangle, the plan's binary64 row of 1 - w_hat_k for a shape window.
+struct W64 {
+  double w, om, hl;
+};
+
+__device__ __forceinline__ W64 win64(const FftSched& S, int L, int k) {
+  if (S.om64) {
+    const double om = S.om64[(size_t)(L - 1) * (size_t)S.P + k];
+    return W64{1.0 - om, om, log2(om)};
+  }
+  const double w = what64(S, L, k);
+  return W64{w, 1.0 - w, log1p(-w) * 1.4426950408889634};
+}
+
 // --------------------------------------------------------- m selection
 
 struct MSelState {
@@ -594,14 +609,13 @@ __device__ __forceinline__ float spectrum_scale(int n, float smax) {
 // weight under- or overflows: weight_k = c_k |r_k|^2 (1 - w_k)^{2(j-1)}.
 static __device__ double exact_sd(const float2* spec, const FftSched& S, int L, int j, RedScratch* red) {
   const int tid = threadIdx.x, nt = blockDim.x;
-  const double inv_ln2 = 1.4426950408889634;
   double M = -INFINITY, dummy = -INFINITY;
   for (int k = tid; k < S.P; k += nt) {
     const float2 z = spec[k];
     const double q = (double)parseval_weight(S, k) * ((double)z.x * z.x + (double)z.y * z.y);
     if (q > 0.0) {
       double lw = log2(q);
-      if (j > 1) lw += 2.0 * (j - 1) * log1p(-what64(S, L, k)) * inv_ln2;
+      if (j > 1) lw += 2.0 * (j - 1) * win64(S, L, k).hl;
       M = fmax(M, lw);
     }
   }
@@ -612,12 +626,12 @@ static __device__ double exact_sd(const float2* spec, const FftSched& S, int L, 
       const float2 z = spec[k];
       const double q = (double)parseval_weight(S, k) * ((double)z.x * z.x + (double)z.y * z.y);
       if (q > 0.0) {
-        const double w = what64(S, L, k);
+        const W64 v = win64(S, L, k);
         double lw = log2(q);
-        if (j > 1) lw += 2.0 * (j - 1) * log1p(-w) * inv_ln2;
+        if (j > 1) lw += 2.0 * (j - 1) * v.hl;
         const double e = exp2(lw - M);
         den += e;
-        num += e * w * w;
+        num += e * v.w * v.w;
       }
     }
   }
@@ -975,8 +989,9 @@ __device__ __forceinline__ void multiplier(int m, float hl, float& g, float& omg
 // whole (w_hat_k taken as 0) when (1 - w_hat_k)^m >= 1 - gamma.  Decided in
 // FP32 on m log2(1 - w_hat_k) against log2(1 - gamma) outside the rounding
 // band of both sides (table value good to 4u, the product u/2, the rounded
-// log2(1 - gamma) u/2: band 8u (|x| + |c|)), else in binary64 from the sine
-// table, as the binary64 definition decides.
+// log2(1 - gamma) u/2: band 8u (|x| + |c|)), else in binary64 (the sine
+// table, or the shape window's binary64 row), as the binary64 definition
+// decides.
 __device__ __forceinline__ bool passes_whole(int m, float hl, const FftSched& S, int L, int k,
                                              const MethodParams& mp) {
   const float x = (float)m * hl, c = mp.log2_keep;
@@ -984,7 +999,7 @@ __device__ __forceinline__ bool passes_whole(int m, float hl, const FftSched& S,
   const float band = 8.f * 5.9604645e-8f * (fabsf(x) + fabsf(c)) + 1e-30f;
   if (x > c + band) return true;
   if (x < c - band) return false;
-  return pow(1.0 - what64(S, L, k), (double)m) >= 1.0 - mp.gamma;
+  return pow(win64(S, L, k).om, (double)m) >= 1.0 - mp.gamma;
 }
 
 __device__ __forceinline__ void multiplier_th(int m, float hl, const FftSched& S, int L, int k,

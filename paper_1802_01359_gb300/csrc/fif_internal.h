@@ -36,6 +36,8 @@ struct FftSched {
   const float2* tw_lo;         // [n]  binary64 value minus tw, rounded (float-float twiddles)
   const float2* wtab;          // [Lmax * P]  row L-1: {log2(1 - w_hat_k), w_hat_k}
   const double* sin64;         // [n/2 + 1]  sin(pi t/n) in binary64
+  const double* om64;          // shape window only: [Lmax * P] row L-1: 1 - w_hat_k in binary64;
+                               // nullptr for the triangle (closed form from sin64)
 };
 
 // Method parameters as the kernels see them.
@@ -169,5 +171,9 @@ cudaError_t launch_staged(const FftSched& s, const FftSched* d_sched, const Meth
 cudaError_t build_tables(int n, int P, int Lmax, float2* tw, float2* tw_lo, float2* wtab,
                          double* sin64, cudaStream_t st);
 cudaError_t build_twiddles(int n, float2* tw, float2* tw_lo, double* sin64, cudaStream_t st);
+// Window rows of a shape-generated window for every L = 1..s.Lmax into wtab
+// and om64 (s.tw / s.tw_lo must be built); g: device copy of the shape.
+cudaError_t build_shape_window(const FftSched& s, const double* g, int glen, float2* wtab,
+                               double* om64, cudaStream_t st);
 
 }  // namespace fif

@@ -277,6 +277,8 @@ extern "C" fif_status fif_decompose_noalloc(const fif_plan_desc* d, const float*
                                             int32_t* n_imfs, int32_t* sig_status,
                                             fif_imf_diag* diag, void* cuda_stream) {
   if (!d || !signal || !imfs || !n_imfs || !sig_status) return FIF_EINVAL;
+  // a shape window needs a table per (n, L) that only a plan holds
+  if (d->window == FIF_WIN_SHAPE) return FIF_EUNSUPPORTED;
   if (d->window != FIF_WIN_TRIANGLE || !(d->delta > 0.0) || !isfinite(d->delta) ||
       d->max_inner < 1 || d->max_inner > (1 << 20) || d->max_imfs < 0 || d->max_imfs > kMaxImfs ||
       (d->flags & ~(FIF_FORCE_L | FIF_APRIORI_N0 | FIF_PEAK_MASK)) ||

@@ -37,6 +37,8 @@ FORCE_L = 1
 FORCE_MULTIPASS = 2
 APRIORI_N0 = 4
 PEAK_MASK = 8
+WIN_TRIANGLE = 0
+WIN_SHAPE = 1
 
 # every symbol include/fif.h declares
 EXPORTS = ("fif_plan_create", "fif_plan_destroy", "fif_plan_set_stream", "fif_plan_prepare",
@@ -56,7 +58,9 @@ class PlanDesc(ctypes.Structure):
     _fields_ = [("window", ctypes.c_int), ("nu", ctypes.c_double), ("mask_scale", ctypes.c_int32),
                 ("delta", ctypes.c_double), ("max_inner", ctypes.c_int32),
                 ("max_imfs", ctypes.c_int32), ("precision", ctypes.c_int),
-                ("max_n", ctypes.c_int64), ("flags", ctypes.c_int32), ("gamma", ctypes.c_double)]
+                ("max_n", ctypes.c_int64), ("flags", ctypes.c_int32), ("gamma", ctypes.c_double),
+                ("window_shape", ctypes.POINTER(ctypes.c_double)),
+                ("window_shape_len", ctypes.c_int32)]
 
 
 class ImfDiag(ctypes.Structure):
@@ -183,7 +187,9 @@ class Plan:
     def __init__(self, *, nu: float = 1.6, mask_scale: int = 1, delta: float = 1e-3,
                  max_inner: int = 200, max_imfs: int = 10, max_n: int = 16384,
                  force_L: bool = False, multipass: bool = False, apriori_n0: bool = False,
-                 gamma: float = 0.0, peak_mask: bool = False, stream=None):
+                 gamma: float = 0.0, peak_mask: bool = False, window_shape=None, stream=None):
+        """window_shape: None for the triangle, else the samples of the generating
+        shape g on [0, 1] (FIF_WIN_SHAPE; copied by the plan)."""
         import torch
         lib = load_library()
         self.max_imfs = max_imfs
@@ -193,6 +199,12 @@ class Plan:
                              (FORCE_L if force_L else 0) | (FORCE_MULTIPASS if multipass else 0)
                              | (APRIORI_N0 if apriori_n0 else 0) | (PEAK_MASK if peak_mask else 0),
                              float(gamma))
+        shape = None
+        if window_shape is not None:
+            shape = np.ascontiguousarray(np.asarray(window_shape, dtype=np.float64))
+            self.desc.window = WIN_SHAPE
+            self.desc.window_shape = shape.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+            self.desc.window_shape_len = shape.size
         if stream is None:
             stream = torch.cuda.current_stream()
         self._stream = stream
@@ -200,6 +212,8 @@ class Plan:
         _check(lib.fif_plan_create(ctypes.byref(h), ctypes.byref(self.desc),
                                    ctypes.c_void_p(stream.cuda_stream)), "fif_plan_create")
         self._h = h
+        self.desc.window_shape = None  # the plan holds its own copy
+        del shape
 
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value:

@@ -3,6 +3,7 @@ import ctypes
 import os
 import re
 
+import numpy as np
 import pytest
 
 from paper_1802_01359_gb300 import build, fif
@@ -71,6 +72,42 @@ def test_null_arguments(lib):
                                    None) == fif.FIF_EINVAL
     assert lib.fif_decompose_batch_host(None, None, None, 1, None, None, None, None, None, None,
                                         None) == fif.FIF_EINVAL
+
+
+def _shape_desc(g, **kw):
+    d = _desc(window=fif.WIN_SHAPE, **kw)
+    arr = None
+    if g is not None:
+        arr = np.ascontiguousarray(np.asarray(g, dtype=np.float64))
+        d.window_shape = arr.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        d.window_shape_len = arr.size
+    return d, arr
+
+
+@pytest.mark.parametrize("g", [None, [], [-1.0, 1.0], [1.0, float("nan")], [1.0, 0.0, 1.0], [0.0],
+                               [0.0, 0.0], [float("inf")]])
+def test_shape_window_validation(lib, g):
+    """FIF_WIN_SHAPE needs finite samples >= 0 with an interpolant > 0 inside (0, 1)."""
+    d, keep = _shape_desc(g)
+    h = ctypes.c_void_p()
+    assert lib.fif_plan_create(ctypes.byref(h), ctypes.byref(d), None) == fif.FIF_EINVAL
+    assert not h.value
+
+
+@pytest.mark.parametrize("flags", [fif.APRIORI_N0, fif.FORCE_MULTIPASS])
+def test_shape_window_unsupported_combinations(lib, flags):
+    d, keep = _shape_desc([0.0, 1.0, 0.0], flags=flags)
+    h = ctypes.c_void_p()
+    assert lib.fif_plan_create(ctypes.byref(h), ctypes.byref(d), None) == fif.FIF_EUNSUPPORTED
+
+
+def test_shape_window_not_on_the_noalloc_path(lib):
+    """The allocation-free entry point has no per-(n, L) table: refused before any CUDA call."""
+    d, keep = _shape_desc([1.0])
+    dummy = ctypes.c_void_p(16)
+    rc = lib.fif_decompose_noalloc(ctypes.byref(d), dummy, 64, dummy, dummy, dummy, dummy, dummy,
+                                   None, None)
+    assert rc == fif.FIF_EUNSUPPORTED
 
 
 def test_split_bf16_precision_not_implemented(lib):
