@@ -60,7 +60,13 @@ WORKLOADS = {
                                "gamma=0.05; delta=1e-3, max_inner=200, max_imfs=10)"),
     "batch16384_pk": dict(desc="the batch16384 signals, mask length from the spectral peak "
                                "(end of Sec. 2; delta=1e-3, max_inner=200, max_imfs=10)"),
+    "batch16384_sh": dict(desc="the batch16384 signals, window generated by the shape "
+                               "g(x) = sin(pi x) (33 samples; Theorem 4's h * h); delta=1e-3, "
+                               "max_inner=200, max_imfs=10"),
 }
+
+# generating shape of the batch16384_sh workload
+SINE_SHAPE = np.sin(np.pi * np.linspace(0.0, 1.0, 33))
 
 
 def _gen_chunk(args):
@@ -95,7 +101,8 @@ def make_workload(name, rank=0):
     """(data, offsets, params) of a named workload."""
     from paper_1802_01359_gb300 import signals
     params = dict(PARAMS)
-    if name in ("batch16384", "batch16384_n0", "batch16384_th", "batch16384_pk"):
+    if name in ("batch16384", "batch16384_n0", "batch16384_th", "batch16384_pk",
+                "batch16384_sh"):
         data, offs = generate(signals.W_BATCH_16384, np.full(BATCH, N), first=rank * BATCH)
         if name == "batch16384_n0":
             params.update(delta=2.0, max_inner=1 << 16, apriori_n0=True)
@@ -103,6 +110,8 @@ def make_workload(name, rank=0):
             params.update(gamma=0.05)
         if name == "batch16384_pk":
             params.update(peak_mask=True)
+        if name == "batch16384_sh":
+            params.update(window_shape=SINE_SHAPE)
     elif name == "single4096":
         s = signals.single_4096()
         data, offs = s, np.array([0, s.size], dtype=np.int64)
@@ -238,6 +247,8 @@ def oracle_sample(data, offs, idx, threads, params=None):
     prm = dict(params or PARAMS)
     if prm.pop("apriori_n0", False):
         prm["apriori"] = True
+    if "window_shape" in prm:
+        prm["shape"] = prm.pop("window_shape")
 
     def one(i):
         return oracle.direct(data[offs[i]:offs[i + 1]].astype(np.float64), **prm)
@@ -373,6 +384,14 @@ def main():
         stream.synchronize()
         tune_s = time.perf_counter() - t0
 
+    chosen = []  # fused schedule of the first few lengths
+    for n in sorted(set(int(v) for v in lens))[:4]:
+        try:
+            E, T, _ = plan.schedule(n)
+            chosen.append(f"n={n}: E={E}, {T} threads")
+        except fif.FifError:
+            pass
+
     def step():
         plan.decompose_batch(x, offs, out=out)
 
@@ -422,8 +441,9 @@ def main():
                    "path": "fused batch (one CTA per signal, shared-memory resident)" if fused_only
                    else "batch: fused for short signals, multi-pass for long ones, one CUDA graph",
                    "l2": f"flushed between steps ({L2_FLUSH_BYTES >> 20} MiB write)",
-                   "schedule": "fixed rule" if tune_s is None
-                   else f"autotuned per length class (fif_plan_tune, {tune_s:.2f} s before timing)",
+                   "schedule": ("fixed rule" if tune_s is None
+                                else f"autotuned per length class (fif_plan_tune, {tune_s:.2f} s "
+                                     "before timing)") + ("; " + "; ".join(chosen) if chosen else ""),
                    "mean_imfs": float(nim.mean())},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
