@@ -244,7 +244,7 @@ __device__ __forceinline__ float2 tw_value(const TwSrc& ts, int t) {
     const int qd = (t >= quarter) + (t >= 2 * quarter) + (t >= 3 * quarter);
     const int u = t - qd * quarter;
     const bool sw = ts.fold == 3 && u > (n >> 3);
-    const float2 v = ts.q[sw ? quarter - u : u];
+    const float2 v = ts.q[tw_slot(sw ? quarter - u : u)];
     const float c = sw ? v.y : v.x, s = sw ? v.x : v.y;
     // exp(-i (qd pi/2 + phi)) with cos phi = c, sin phi = s
     const float a = (qd & 1) ? s : c, b = (qd & 1) ? c : s;
@@ -253,10 +253,10 @@ __device__ __forceinline__ float2 tw_value(const TwSrc& ts, int t) {
   if (ts.fold == 1) {
     const int half = n >> 1;
     const bool h = t >= half;
-    const float2 v = ts.q[h ? t - half : t];
+    const float2 v = ts.q[tw_slot(h ? t - half : t)];
     return h ? make_float2(-v.x, v.y) : make_float2(v.x, -v.y);
   }
-  const float2 v = ts.q[t];
+  const float2 v = ts.q[tw_slot(t)];
   return make_float2(v.x, -v.y);
 }
 
@@ -1128,10 +1128,11 @@ static __device__ EpiOut epilogue_extrema_even(const float2* work, float* rem, f
         out_row[2 * t] = a;
         out_row[2 * t + 1] = b;
       }
-      ra = rem[2 * t] - a;
-      rb = rem[2 * t + 1] - b;
-      rem[2 * t] = ra;
-      rem[2 * t + 1] = rb;
+      // one 8-byte access per lane: conflict-free, where two scalar ones are 2-way
+      const float2 rr = *reinterpret_cast<const float2*>(rem + 2 * t);
+      ra = rr.x - a;
+      rb = rr.y - b;
+      *reinterpret_cast<float2*>(rem + 2 * t) = make_float2(ra, rb);
       imax = fmaxf(imax, fmaxf(fabsf(a), fabsf(b)));
       rmax = fmaxf(rmax, fmaxf(fabsf(ra), fabsf(rb)));
     }

@@ -31,7 +31,7 @@ __device__ void decompose_resident(const FftSched& S, const SigDesc& d, int sig,
   if (smtw) {
     for (int u = tid; u < S.tw_entries; u += nt) {
       const float2 w = __ldg(&S.tw[u]);
-      smtw[u] = make_float2(w.x, -w.y);
+      smtw[tw_slot(u)] = make_float2(w.x, -w.y);
     }
   }
   const TwSrc ts{smtw, S.tw, n, S.tw_fold};

@@ -31,6 +31,7 @@ struct FftSched {
   int tw_fold;                 // symmetry folds of the shared twiddle table: 3 (octant, 8 | n),
                                // 2 (quarter, 4 | n), 1 (half, 2 | n), 0 (none)
   int tw_entries;              // entries of the shared twiddle table: n / 2^tw_fold + 1
+                               // (stored in tw_slots() slots, see tw_slot)
   int tw_shared;               // 1 if the fused kernel keeps the table in shared memory
   const float2* tw;            // [n]  exp(-2 pi i t/n), rounded from binary64
   const float2* tw_lo;         // [n]  binary64 value minus tw, rounded (float-float twiddles)
@@ -83,8 +84,21 @@ struct Outputs {
 // not read back).
 __host__ __device__ inline size_t rem_bytes(const FftSched& s) { return ((size_t)s.n * sizeof(float) + 15) & ~(size_t)15; }
 __host__ __device__ inline size_t work_points(const FftSched& s) { return (size_t)(s.odd ? s.n : s.Nc + 1); }
+// Slot of entry u of a shared twiddle table: u with its low four bits XOR-ed
+// by a fold of its higher bits.  The passes of a transform read entries a
+// power of two apart (k times n / (Ns R), folded); without the swizzle those
+// land in one bank (up to 32-way conflicts).  A bijection inside each block of
+// 16 entries, so consecutive entries still hit distinct banks.
+__host__ __device__ inline int tw_slot(int u) {
+  const int x = u >> 4;
+  return u ^ ((x ^ (x >> 4) ^ (x >> 8) ^ (x >> 12)) & 15);
+}
+// Slots a table of s.tw_entries entries occupies (whole blocks of 16).
+__host__ __device__ inline size_t tw_slots(const FftSched& s) {
+  return ((size_t)s.tw_entries + 15) & ~(size_t)15;
+}
 __host__ __device__ inline size_t tw_table_bytes(const FftSched& s) {
-  return s.tw_shared ? (((size_t)s.tw_entries * sizeof(float2) + 15) & ~(size_t)15) : 0;
+  return s.tw_shared ? tw_slots(s) * sizeof(float2) : 0;
 }
 inline size_t fused_smem_bytes(const FftSched& s) {
   return 1024 + rem_bytes(s) + (work_points(s) + (size_t)s.P) * sizeof(float2) + tw_table_bytes(s);

@@ -190,7 +190,7 @@ __global__ void __launch_bounds__(512, sizeof(Cx) == 8 ? 2 : 1) lg_level(const L
     q = reinterpret_cast<float2*>(smem + (size_t)TJ * R * sizeof(Cx));
     for (int u = tid; u < SR.tw_entries; u += nt) {
       const float2 w = __ldg(&SR.tw[u]);
-      q[u] = make_float2(w.x, -w.y);
+      q[tw_slot(u)] = make_float2(w.x, -w.y);
     }
   }
   __syncthreads();
@@ -996,7 +996,7 @@ size_t large_level_smem(const LgSched& G, int level, bool ff) {
   const FftSched& SR = level == 1 ? G.S1 : G.S2;
   const int TJ = ff ? (level == 1 ? G.TJF1 : G.TJF2) : (level == 1 ? G.TJ1 : G.TJ2);
   size_t b = (size_t)TJ * R * (ff ? 16 : 8);
-  if (!ff) b += (size_t)SR.tw_entries * sizeof(float2);
+  if (!ff) b += tw_slots(SR) * sizeof(float2);
   return b;
 }
 

@@ -174,7 +174,7 @@ __global__ void __launch_bounds__(512, 1) na_inverse(FftSched S, NaScratch scr, 
   for (int k = threadIdx.x; k < S.P; k += blockDim.x) work[k] = scr.work[k];
   for (int u = threadIdx.x; u < S.tw_entries; u += blockDim.x) {
     const float2 w = __ldg(&S.tw[u]);
-    smtw[u] = make_float2(w.x, -w.y);
+    smtw[tw_slot(u)] = make_float2(w.x, -w.y);
   }
   __syncthreads();
   const TwSrc ts{smtw, S.tw, S.n, S.tw_fold};
@@ -222,7 +222,7 @@ static cudaError_t na_launch(const FftSched& s, const MethodParams& mp, const fl
   cudaFuncSetAttribute(na_inverse<E>, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn_max);
   const int threads = sched_threads(s);
   const size_t work_bytes = ((work_points(s) + 1) & ~(size_t)1) * sizeof(float2) +
-                            (size_t)s.tw_entries * sizeof(float2);
+                            tw_slots(s) * sizeof(float2);
   const size_t ff_bytes = (size_t)s.Nc * sizeof(ffc);
   const int pblocks = (s.P + 255) / 256;
   na_forward<E><<<1, threads, ff_bytes, st>>>(s, signal, scr, out);

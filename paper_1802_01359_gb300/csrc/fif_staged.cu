@@ -115,7 +115,7 @@ __global__ void __launch_bounds__(512, 1) staged_inverse(FftSched S, StagedScrat
   for (int k = threadIdx.x; k < S.P; k += blockDim.x) work[k] = scr.work[k];
   for (int u = threadIdx.x; u < S.tw_entries; u += blockDim.x) {
     const float2 w = __ldg(&S.tw[u]);
-    smtw[u] = make_float2(w.x, -w.y);
+    smtw[tw_slot(u)] = make_float2(w.x, -w.y);
   }
   __syncthreads();
   const TwSrc ts{smtw, S.tw, S.n, S.tw_fold};
@@ -162,7 +162,7 @@ static cudaError_t launch_staged_e(const FftSched& s, const MethodParams& mp, co
   cudaFuncSetAttribute(staged_inverse<E>, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn_max);
   const int threads = sched_threads(s);
   const size_t work_bytes = ((work_points(s) + 1) & ~(size_t)1) * sizeof(float2) +
-                            (size_t)s.tw_entries * sizeof(float2);
+                            tw_slots(s) * sizeof(float2);
   const size_t ff_bytes = (size_t)s.Nc * sizeof(ffc);
   staged_forward<E><<<1, threads, ff_bytes, st>>>(s, signal, scr, out, mp);
   cudaError_t e = cudaGetLastError();
