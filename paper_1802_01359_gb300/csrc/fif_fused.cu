@@ -6,27 +6,40 @@
 
 namespace fif {
 
+// Per-signal loop state kept in shared memory rather than in registers: the
+// kernel runs at 64 registers a thread, and values carried across the
+// transforms and the m search would otherwise be spilled to local memory.
+// Thread 0 writes it between barriers; every thread reads it after one.
+struct LoopState {
+  int K;         // IMFs extracted so far
+  int flags;     // FIF_FLAG_* of the extracted IMFs
+  int ek, ezc;   // extrema and zero crossings of the current remainder
+  int etie;      // extrema tie of the current remainder
+  float ermax;   // ||r||_inf of the current remainder
+  float tau;     // tie band of the extrema count
+  float sc;      // power-of-two scale of the spectrum for the m screen
+};
+
 struct FusedShared {
   FftSched S;
   RedScratch red;
+  SigDesc d;
+  LoopState ls;
   int sig;
   int ot[3];  // outer test result broadcast: reason, L, flags
 };
-static_assert(sizeof(FusedShared) + 16 <= 1024, "fused_smem_bytes reserves 1 KiB for the header");
+static_assert(sizeof(FusedShared) + 16 <= kFusedHeader, "the fused kernel's shared header");
 
 // One signal, Algorithm 2's outer loop with the inner loop replaced by the
 // spectral multiplier (Theorem 5, eq. One step_algo).
 template <int E>
-__device__ void decompose_resident(const FftSched& S, const SigDesc& d, int sig,
-                                   const MethodParams& mp, const float* __restrict__ signals,
-                                   const Outputs& out, float2* spec, float2* work, float* rem,
-                                   ffc* zf, float2* smtw, RedScratch* red, int* ot) {
+__device__ void decompose_resident(FusedShared* sh, const MethodParams& mp,
+                                   const float* __restrict__ signals, const Outputs& out,
+                                   float2* spec, float2* work, float* rem, ffc* zf, float2* smtw) {
+  const FftSched& S = sh->S;
+  LoopState& ls = sh->ls;
+  RedScratch* red = &sh->red;
   const int n = S.n, tid = threadIdx.x, nt = blockDim.x;
-  const float* x = signals + d.in_off;
-  float* orow = out.imfs + d.out_off;
-  int32_t* m_out = out.m + (size_t)sig * mp.max_imfs;
-  int32_t* L_io = out.mask_len + (size_t)sig * mp.max_imfs;
-  fif_imf_diag* dg = out.diag ? out.diag + (size_t)sig * (mp.max_imfs + 1) : nullptr;
 
   if (smtw) {
     for (int u = tid; u < S.tw_entries; u += nt) {
@@ -35,76 +48,94 @@ __device__ void decompose_resident(const FftSched& S, const SigDesc& d, int sig,
     }
   }
   const TwSrc ts{smtw, S.tw, n, S.tw_fold};
-  const float smax = forward_real<E>(x, rem, zf, spec, S, red);
-  if (smax < 0.f) {  // NaN or Inf in the input
-    for (int i = tid; i < n; i += nt) orow[i] = x[i];
-    if (tid == 0) {
-      out.n_imfs[sig] = 0;
-      out.sig_status[sig] = FIF_STOP_NONFINITE;
-      if (dg) dg[0] = fif_imf_diag{0, 0, 0, 0.f};
+  {
+    const float* x = signals + sh->d.in_off;
+    const float smax = forward_real<E>(x, rem, zf, spec, S, red);
+    if (smax < 0.f) {  // NaN or Inf in the input
+      float* orow = out.imfs + sh->d.out_off;
+      for (int i = tid; i < n; i += nt) orow[i] = x[i];
+      if (tid == 0) {
+        const int sig = sh->d.idx;
+        out.n_imfs[sig] = 0;
+        out.sig_status[sig] = FIF_STOP_NONFINITE;
+        if (out.diag) out.diag[(size_t)sig * (mp.max_imfs + 1)] = fif_imf_diag{0, 0, 0, 0.f};
+      }
+      return;
     }
-    return;
-  }
-  const float tau = tie_tau(smax);
-  const float sc = spectrum_scale(n, smax);
-  ExtremaInfo e = count_extrema(rem, n, tau, red);
-  e.tie = 0;  // the input itself is exact on both sides
-  int K = 0, flags = 0, reason = 0;
-  for (;;) {
-    // the outer test (binary64 division) on one thread, broadcast
-    int L = 0, iflags = e.tie ? FIF_FLAG_EXTREMA_TIE : 0;
-    SpecPeak pk{0, 0};
-    if (mp.peak_mask) pk = spectral_peak(spec, S, red);
-    if (pk.tie) iflags |= FIF_FLAG_EXTREMA_TIE;
+    const float tau = tie_tau(smax);
+    const ExtremaInfo e = count_extrema(rem, n, tau, red);
     if (tid == 0) {
-      ot[0] = outer_test(e.k, K, n, mp, L_io, L, iflags, pk.k);
-      ot[1] = L;
-      ot[2] = iflags;
+      ls = LoopState{0, 0, e.k, e.zc, 0, e.rmax, tau, spectrum_scale(n, smax)};
+      // (the input itself is exact on both sides: no extrema tie at step 0)
     }
     __syncthreads();
-    reason = ot[0];
-    L = ot[1];
-    iflags = ot[2];
-    if (dg && tid == 0) {
-      dg[K].k_extrema = e.k;
-      dg[K].zero_crossings = e.zc;
-    }
-    if (reason) {
-      flags |= iflags & FIF_FLAG_EXTREMA_TIE;
-      if (dg && tid == 0) {
-        dg[K].flags = iflags & FIF_FLAG_EXTREMA_TIE;
-        dg[K].inf_norm = e.rmax;
+  }
+  int reason = 0;
+  for (;;) {
+    // the outer test (binary64 division) on one thread, broadcast
+    SpecPeak pk{0, 0};
+    if (mp.peak_mask) pk = spectral_peak(spec, S, red);
+    if (tid == 0) {
+      const int sig = sh->d.idx;
+      int L = 0, iflags = ls.etie ? FIF_FLAG_EXTREMA_TIE : 0;
+      if (pk.tie) iflags |= FIF_FLAG_EXTREMA_TIE;
+      sh->ot[0] = outer_test(ls.ek, ls.K, n, mp, out.mask_len + (size_t)sig * mp.max_imfs, L,
+                             iflags, pk.k);
+      sh->ot[1] = L;
+      sh->ot[2] = iflags;
+      if (out.diag) {
+        fif_imf_diag* dg = out.diag + (size_t)sig * (mp.max_imfs + 1) + ls.K;
+        dg->k_extrema = ls.ek;
+        dg->zero_crossings = ls.ezc;
+        if (sh->ot[0]) {
+          dg->flags = iflags & FIF_FLAG_EXTREMA_TIE;
+          dg->inf_norm = ls.ermax;
+        }
       }
-      break;
+      if (sh->ot[0]) ls.flags |= iflags & FIF_FLAG_EXTREMA_TIE;
     }
-    const int m = select_m(spec, S, L, mp, sc, iflags, red);
+    __syncthreads();
+    reason = sh->ot[0];
+    if (reason) break;
+    const int L = sh->ot[1];
+    int iflags = sh->ot[2];
+    const int m = select_m(spec, S, L, mp, ls.sc, iflags, red);
     apply_multiplier(spec, work, S, L, m, mp);
     inverse_real<E>(work, S, ts);
-    float imax;
+    float* orow = out.imfs + sh->d.out_off + (size_t)ls.K * n;
+    float imax, ermax;
+    int ek, ezc, etie;
     if (!S.odd) {
-      const EpiOut eo = epilogue_extrema_even(work, rem, orow + (size_t)K * n, S, tau, red);
+      const EpiOut eo = epilogue_extrema_even(work, rem, orow, S, ls.tau, red);
       imax = eo.imax;
-      e = ExtremaInfo{eo.k, eo.zc, eo.tie, eo.rmax};
+      ek = eo.k, ezc = eo.zc, etie = eo.tie, ermax = eo.rmax;
     } else {
-      imax = store_imf_update_rem(work, rem, orow + (size_t)K * n, S, red);
-      e = count_extrema(rem, n, tau, red);
+      imax = store_imf_update_rem(work, rem, orow, S, red);
+      const ExtremaInfo e = count_extrema(rem, n, ls.tau, red);
+      ek = e.k, ezc = e.zc, etie = e.tie, ermax = e.rmax;
     }
     if (tid == 0) {
-      m_out[K] = m;
-      if (!mp.force_L) L_io[K] = L;
-      if (dg) {
-        dg[K].flags = iflags;
-        dg[K].inf_norm = imax;
+      const int sig = sh->d.idx, K = ls.K;
+      out.m[(size_t)sig * mp.max_imfs + K] = m;
+      if (!mp.force_L) out.mask_len[(size_t)sig * mp.max_imfs + K] = L;
+      if (out.diag) {
+        fif_imf_diag* dg = out.diag + (size_t)sig * (mp.max_imfs + 1) + K;
+        dg->flags = iflags;
+        dg->inf_norm = imax;
       }
+      ls.flags |= iflags;
+      ls.K = K + 1;
+      ls.ek = ek, ls.ezc = ezc, ls.etie = etie, ls.ermax = ermax;
     }
-    flags |= iflags;
-    K++;
+    __syncthreads();
   }
-  float* rrow = orow + (size_t)K * n;
+  const int K = ls.K;
+  float* rrow = out.imfs + sh->d.out_off + (size_t)K * n;
   for (int i = tid; i < n; i += nt) rrow[i] = rem[i];
   if (tid == 0) {
+    const int sig = sh->d.idx;
     out.n_imfs[sig] = K;
-    out.sig_status[sig] = reason | flags;
+    out.sig_status[sig] = reason | ls.flags;
   }
 }
 
@@ -116,14 +147,16 @@ __global__ void __launch_bounds__(E <= kWideMaxE ? 1024 : 512, 1) fused_kernel(c
                                                     int* counter) {
   extern __shared__ __align__(16) unsigned char smem[];
   FusedShared* sh = reinterpret_cast<FusedShared*>(smem);
-  unsigned char* dyn = smem + 1024;
+  unsigned char* dyn = smem + kFusedHeader;
   for (;;) {
     if (threadIdx.x == 0) sh->sig = atomicAdd(counter, 1);
     __syncthreads();
     const int sig = sh->sig;
     if (sig >= nsig) break;
-    const SigDesc d = sigs[sig];
-    if (threadIdx.x == 0) sh->S = scheds[d.sched];
+    if (threadIdx.x == 0) {
+      sh->d = sigs[sig];
+      sh->S = scheds[sh->d.sched];
+    }
     __syncthreads();
     const FftSched& S = sh->S;
     float* rem = reinterpret_cast<float*>(dyn);
@@ -131,7 +164,7 @@ __global__ void __launch_bounds__(E <= kWideMaxE ? 1024 : 512, 1) fused_kernel(c
     float2* spec = work + work_points(S);
     ffc* zf = reinterpret_cast<ffc*>(dyn);
     float2* smtw = S.tw_shared ? spec + S.P : nullptr;
-    decompose_resident<E>(S, d, d.idx, mp, signals, out, spec, work, rem, zf, smtw, &sh->red, sh->ot);
+    decompose_resident<E>(sh, mp, signals, out, spec, work, rem, zf, smtw);
     __syncthreads();
   }
 }

@@ -83,6 +83,9 @@ struct Outputs {
 // first two regions (and, for odd n, the start of the third, which it does
 // not read back).
 __host__ __device__ inline size_t rem_bytes(const FftSched& s) { return ((size_t)s.n * sizeof(float) + 15) & ~(size_t)15; }
+// Bytes of the fused kernel's shared header (schedule, reduction scratch,
+// loop state) ahead of its arrays.
+constexpr size_t kFusedHeader = 1280;
 __host__ __device__ inline size_t work_points(const FftSched& s) { return (size_t)(s.odd ? s.n : s.Nc + 1); }
 // Slot of entry u of a shared twiddle table: u with its low four bits XOR-ed
 // by a fold of its higher bits.  The passes of a transform read entries a
@@ -101,7 +104,8 @@ __host__ __device__ inline size_t tw_table_bytes(const FftSched& s) {
   return s.tw_shared ? tw_slots(s) * sizeof(float2) : 0;
 }
 inline size_t fused_smem_bytes(const FftSched& s) {
-  return 1024 + rem_bytes(s) + (work_points(s) + (size_t)s.P) * sizeof(float2) + tw_table_bytes(s);
+  return kFusedHeader + rem_bytes(s) + (work_points(s) + (size_t)s.P) * sizeof(float2) +
+         tw_table_bytes(s);
 }
 
 inline int sched_threads(const FftSched& s) {
