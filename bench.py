@@ -451,7 +451,8 @@ def main():
                      "kernel": "fused_kernel (one launch per step)" if fused_only
                      else "whole step (all kernels of the graph)",
                      "alg_bytes_per_launch": alg_bytes},
-        "gpu_launches": args.steps,
+        # kernels of one graph replay (fif_plan_batch_launches) times the timed steps
+        "gpu_launches": plan.batch_launches() * args.steps,
         "clocks": clk.summary(),
     }
 

@@ -246,6 +246,14 @@ fif_status fif_plan_get_schedule(fif_plan_t plan, int64_t n, int32_t* E, int32_t
 fif_status fif_plan_save_tuning(fif_plan_t plan, const char* path);
 fif_status fif_plan_load_tuning(fif_plan_t plan, const char* path);
 
+/* Kernel launches one fif_decompose_batch (or fif_decompose_batch_host) call
+ * enqueues for the batch layout the plan last prepared: one fused kernel per
+ * length class of the fused path, and the multi-pass kernels of every longer
+ * class (their number depends on max_imfs, max_inner, the class size and the
+ * peak mode).  0 before the first batch call.  Host-side only (no CUDA call).
+ * Errors: FIF_EINVAL (NULL argument). */
+fif_status fif_plan_batch_launches(fif_plan_t plan, int64_t* launches);
+
 /* ---- allocation-free single-signal entry point ----------------------------
  * The paper has no counterpart to this; it exists for callers of this
  * library that cannot allocate device memory at the moment they decompose:

@@ -1122,6 +1122,16 @@ fif_status fif_plan_tune(fif_plan_t p, const float* signals, const int64_t* offs
                              sig_status, nullptr);
 }
 
+fif_status fif_plan_batch_launches(fif_plan_t p, int64_t* launches) {
+  if (!p || !launches) return FIF_EINVAL;
+  *launches = 0;
+  if (!p->layout_valid) return FIF_OK;
+  int64_t c = (int64_t)p->layout.classes.size();  // one fused kernel a class
+  for (const auto& lc : p->layout.lcls) c += large_launches(lc.count, p->mp);
+  *launches = c;
+  return FIF_OK;
+}
+
 fif_status fif_plan_get_schedule(fif_plan_t p, int64_t n, int32_t* E, int32_t* threads,
                                  int32_t* tuned) {
   if (!p || !E || !threads || !tuned) return FIF_EINVAL;

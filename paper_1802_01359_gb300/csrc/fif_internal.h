@@ -168,6 +168,8 @@ cudaError_t large_run(const LgSched& G, const LgSig* d_sigs, int nsig, const Met
 size_t large_level_smem(const LgSched& G, int level, bool ff);
 cudaError_t large_set_attrs(const LgSched& G);
 int large_sel_rounds(int max_inner);
+// Kernel launches large_run enqueues for nsig signals of one class.
+int large_launches(int nsig, const MethodParams& mp);
 
 // Kernel launchers (fif_fused.cu, fif_staged.cu, fif_tables.cu).
 cudaError_t launch_fused(int E, const SigDesc* d_sigs, int nsig, const FftSched* d_scheds,

@@ -828,6 +828,9 @@ __global__ void __launch_bounds__(512, 1) lg_select_cta(const LgSig* __restrict_
 // r_hat, and the inverse real-transform split of IMF_hat (same formulas as
 // inverse_real) into work2, in one pass: the thread of k (even n) owns the
 // bins k and Nc - k (Nyquist for k = 0), which the split combines.
+// TH: the thresholded IMF (gamma > 0).  A separate instance, so that the
+// plain one keeps the register count (and occupancy) of a streaming kernel.
+template <bool TH>
 __global__ void lg_multiply_split(const LgSig* __restrict__ sigs, LgSched G, MethodParams mp) {
   const LgSig sg = sigs[blockIdx.y];
   if (sg.st[LG_DONE]) return;
@@ -839,8 +842,13 @@ __global__ void lg_multiply_split(const LgSig* __restrict__ sigs, LgSched G, Met
       const int kc = Nc - k;
       const float2 zk = sg.spec[k], zc = sg.spec[kc];
       float gk, ok, gc, oc;
-      multiplier_th(m, sg.row[k].x, G.S, L, k, mp, gk, ok);
-      multiplier_th(m, sg.row[kc].x, G.S, L, kc, mp, gc, oc);
+      if constexpr (TH) {
+        multiplier_th(m, sg.row[k].x, G.S, L, k, mp, gk, ok);
+        multiplier_th(m, sg.row[kc].x, G.S, L, kc, mp, gc, oc);
+      } else {
+        multiplier(m, sg.row[k].x, gk, ok);
+        multiplier(m, sg.row[kc].x, gc, oc);
+      }
       const float2 xk = make_float2(gk * zk.x, gk * zk.y);
       const float2 xc = make_float2(gc * zc.x, gc * zc.y);
       sg.spec[k] = make_float2(ok * zk.x, ok * zk.y);
@@ -856,7 +864,10 @@ __global__ void lg_multiply_split(const LgSig* __restrict__ sigs, LgSched G, Met
     for (int k = first_signal_point(step); k < G.S.P; k += step) {
       const float2 z = sg.spec[k];
       float g, omg;
-      multiplier_th(m, sg.row[k].x, G.S, L, k, mp, g, omg);
+      if constexpr (TH)
+        multiplier_th(m, sg.row[k].x, G.S, L, k, mp, g, omg);
+      else
+        multiplier(m, sg.row[k].x, g, omg);
       const float2 x = make_float2(g * z.x, g * z.y);
       sg.spec[k] = make_float2(omg * z.x, omg * z.y);
       sg.work2[k] = x;
@@ -881,8 +892,9 @@ __device__ __forceinline__ float new_rem(const float* ro, const float2* w2, int 
 // extrema, zero-crossing and tie terms from the new values of its neighbours
 // (taken from the old buffer and work2, so no CTA waits for another); CTA
 // sums go to the state words by atomics, with max |IMF| and max |r|.
-__global__ void lg_epilogue_ext(const LgSig* __restrict__ sigs, LgSched G, int it,
-                                float* __restrict__ imfs) {
+// (at most 32 registers: eight 256-thread CTAs an SM for this streaming kernel)
+__global__ void __launch_bounds__(256, 8) lg_epilogue_ext(const LgSig* __restrict__ sigs, LgSched G,
+                                                           int it, float* __restrict__ imfs) {
   __shared__ RedScratch red;
   const LgSig sg = sigs[blockIdx.y];
   int* st = sg.st;
@@ -1052,6 +1064,17 @@ cudaError_t large_set_attrs(const LgSched& G) {
   return e;
 }
 
+// The launches of large_run below, counted the same way: pack, two forward
+// levels and the split; the input's extrema; then per outer iteration the
+// peak pair (peak mode), control, window row, the m search (one CTA kernel, or
+// two kernels a round), multiply, two inverse levels and the epilogue.
+int large_launches(int nsig, const MethodParams& mp) {
+  const bool cta_select = nsig >= kSelCtaMinSignals || mp.apriori;
+  const int sel = cta_select ? 1 : 2 * large_sel_rounds(mp.max_inner);
+  const int per_it = (mp.peak_mask ? 2 : 0) + 2 + sel + 1 + 2 + 1;
+  return 4 + 1 + (mp.max_imfs + 1) * per_it;
+}
+
 cudaError_t large_run(const LgSched& G, const LgSig* d_sigs, int nsig, const MethodParams& mp,
                       const float* signals, const Outputs& out, cudaStream_t st) {
   const int pts = G.S.odd ? G.S.n : G.S.Nc;
@@ -1091,7 +1114,10 @@ cudaError_t large_run(const LgSched& G, const LgSig* d_sigs, int nsig, const Met
         lg_sel64<<<dim3(G.sel_blocks, nsig), kSelThreads, 0, st>>>(d_sigs, G, mp, r);
       }
     }
-    lg_multiply_split<<<dim3(bx_split, nsig), 256, 0, st>>>(d_sigs, G, mp);
+    if (mp.threshold)
+      lg_multiply_split<true><<<dim3(bx_split, nsig), 256, 0, st>>>(d_sigs, G, mp);
+    else
+      lg_multiply_split<false><<<dim3(bx_split, nsig), 256, 0, st>>>(d_sigs, G, mp);
     e = cudaGetLastError();
     if (e == cudaSuccess) e = launch_level<float2, true, 1>(G, d_sigs, nsig, st);
     if (e == cudaSuccess) e = launch_level<float2, true, 2>(G, d_sigs, nsig, st);

@@ -44,7 +44,7 @@ WIN_SHAPE = 1
 EXPORTS = ("fif_plan_create", "fif_plan_destroy", "fif_plan_set_stream", "fif_plan_prepare",
            "fif_decompose", "fif_decompose_batch", "fif_decompose_batch_host", "fif_fused_max_n",
            "fif_status_string", "fif_decompose_noalloc", "fif_plan_tune", "fif_plan_get_schedule",
-           "fif_plan_save_tuning", "fif_plan_load_tuning")
+           "fif_plan_save_tuning", "fif_plan_load_tuning", "fif_plan_batch_launches")
 NOALLOC_MAX_N = 16384
 
 
@@ -101,6 +101,7 @@ def load_library(path: str = LIB_PATH):
     lib.fif_status_string.restype = ctypes.c_char_p
     lib.fif_plan_tune.argtypes = [vp, fp, i64p, ctypes.c_int64, fp, i64p, i32p, i32p, i32p, i32p]
     lib.fif_plan_get_schedule.argtypes = [vp, ctypes.c_int64, i32p, i32p, i32p]
+    lib.fif_plan_batch_launches.argtypes = [vp, ctypes.c_void_p]
     lib.fif_plan_save_tuning.argtypes = [vp, ctypes.c_char_p]
     lib.fif_plan_load_tuning.argtypes = [vp, ctypes.c_char_p]
     for name in ("fif_plan_create", "fif_plan_destroy", "fif_plan_set_stream", "fif_plan_prepare",
@@ -326,6 +327,13 @@ class Plan:
                                                     ctypes.byref(T), ctypes.byref(tuned)),
                "fif_plan_get_schedule")
         return E.value, T.value, bool(tuned.value)
+
+    def batch_launches(self) -> int:
+        """Kernel launches one decompose_batch call enqueues for the last prepared layout."""
+        v = ctypes.c_int64()
+        _check(load_library().fif_plan_batch_launches(self._h, ctypes.byref(v)),
+               "fif_plan_batch_launches")
+        return int(v.value)
 
     def save_tuning(self, path: str):
         _check(load_library().fif_plan_save_tuning(self._h, os.fsencode(path)),

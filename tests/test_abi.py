@@ -132,6 +132,11 @@ def test_out_layout():
     assert np.array_equal(fif.out_layout([], 3), np.zeros(0, dtype=np.int64))
 
 
+def test_batch_launches_rejects_null_arguments(lib):
+    v = ctypes.c_int64()
+    assert lib.fif_plan_batch_launches(None, ctypes.byref(v)) == fif.FIF_EINVAL
+
+
 def test_tuning_entry_points_reject_null_arguments(lib):
     i32 = ctypes.c_int32()
     assert lib.fif_plan_tune(None, None, None, 1, None, None, None, None, None, None) == \
