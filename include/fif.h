@@ -207,10 +207,14 @@ fif_status fif_decompose_batch(fif_plan_t plan, const float* signals, const int6
                                fif_imf_diag* diag);
 
 /* Same as fif_decompose_batch, but every data pointer (signals, imfs, m,
- * mask_len, n_imfs, sig_status, diag) is a HOST pointer.  The plan copies the
- * inputs to its device staging buffers, runs the batch and copies the results
- * back; returns after the results are in host memory (blocking).  Pinned host
- * memory makes the copies asynchronous DMA. */
+ * mask_len, n_imfs, sig_status, diag) is a HOST pointer; returns after the
+ * results are in host memory (blocking).  A buffer in page-locked memory that
+ * is mapped into the device's address space (cudaMallocHost, cudaHostAlloc,
+ * or cudaHostRegister with mapping) is read or written in place by the
+ * kernels, so its transfer over the host link overlaps the computation.  Any
+ * other buffer is staged: copied to the plan's device buffers before the
+ * batch, or from them after it.  Rows after n_imfs of an in-place imfs buffer
+ * are left untouched (as on the device path). */
 fif_status fif_decompose_batch_host(fif_plan_t plan, const float* signals, const int64_t* offsets,
                                     int64_t batch, float* imfs, const int64_t* out_offsets,
                                     int32_t* m, int32_t* mask_len, int32_t* n_imfs,

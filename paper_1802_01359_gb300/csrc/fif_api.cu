@@ -993,6 +993,19 @@ fif_status fif_decompose_batch(fif_plan_t p, const float* signals, const int64_t
   return cuda_status(cudaGraphLaunch(l.exec, p->stream));
 }
 
+// Device address of a host buffer that kernels may read and write in place:
+// page-locked memory mapped into the device's address space (cudaMallocHost,
+// cudaHostAlloc, or cudaHostRegister with mapping).  nullptr for anything else.
+static void* device_view(const void* h) {
+  if (!h) return nullptr;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, h) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
+}
+
 fif_status fif_decompose_batch_host(fif_plan_t p, const float* signals, const int64_t* offsets,
                                     int64_t batch, float* imfs, const int64_t* out_offsets,
                                     int32_t* m, int32_t* mask_len, int32_t* n_imfs,
@@ -1009,8 +1022,31 @@ fif_status fif_decompose_batch_host(fif_plan_t p, const float* signals, const in
   const size_t mi_b = sizeof(int32_t) * (size_t)batch * (size_t)p->desc.max_imfs;
   const size_t si_b = sizeof(int32_t) * (size_t)batch;
   const size_t dg_b = diag ? sizeof(fif_imf_diag) * (size_t)batch * (size_t)K1 : 0;
+  // Mapped page-locked buffers are used in place: the kernels read the input
+  // and write the outputs across the host link while they compute.  Other
+  // buffers go through device staging with copies before and after.
+  struct Buf {
+    void* host;
+    void* dev;  // in place, or the staging slot
+    size_t bytes;
+    bool in, out;
+    bool staged;
+  };
+  Buf b[7] = {{(void*)signals, nullptr, in_b, true, false, false},
+              {imfs, nullptr, out_b, false, true, false},
+              {m, nullptr, mi_b, false, true, false},
+              {mask_len, nullptr, mi_b, p->mp.force_L != 0, true, false},
+              {n_imfs, nullptr, si_b, false, true, false},
+              {sig_status, nullptr, si_b, false, true, false},
+              {diag, nullptr, dg_b, false, true, false}};
   auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
-  const size_t need = al(in_b) + al(out_b) + 2 * al(mi_b) + 2 * al(si_b) + al(dg_b);
+  size_t need = 0;
+  for (Buf& x : b) {
+    if (!x.host || !x.bytes) continue;
+    x.dev = device_view(x.host);
+    x.staged = x.dev == nullptr;
+    if (x.staged) need += al(x.bytes);
+  }
   if (need > p->h2d_cap) {
     cudaFree(p->h2d_buf);
     p->h2d_buf = nullptr;
@@ -1022,28 +1058,23 @@ fif_status fif_decompose_batch_host(fif_plan_t p, const float* signals, const in
     }
     p->h2d_cap = need;
   }
-  char* base = (char*)p->h2d_buf;
-  float* d_in = (float*)base;
-  float* d_out = (float*)(base += al(in_b));
-  int32_t* d_m = (int32_t*)(base += al(out_b));
-  int32_t* d_L = (int32_t*)(base += al(mi_b));
-  int32_t* d_nimfs = (int32_t*)(base += al(mi_b));
-  int32_t* d_stat = (int32_t*)(base += al(si_b));
-  fif_imf_diag* d_diag = diag ? (fif_imf_diag*)(base += al(si_b)) : nullptr;
+  char* slot = (char*)p->h2d_buf;
   cudaStream_t s = p->stream;
-  cudaError_t e = cudaMemcpyAsync(d_in, signals, in_b, cudaMemcpyHostToDevice, s);
-  if (e == cudaSuccess && p->mp.force_L && mi_b)
-    e = cudaMemcpyAsync(d_L, mask_len, mi_b, cudaMemcpyHostToDevice, s);
+  cudaError_t e = cudaSuccess;
+  for (Buf& x : b) {
+    if (!x.staged) continue;
+    x.dev = slot;
+    slot += al(x.bytes);
+    if (x.in && e == cudaSuccess) e = cudaMemcpyAsync(x.dev, x.host, x.bytes, cudaMemcpyHostToDevice, s);
+  }
   if (e != cudaSuccess) return cuda_status(e);
-  st = fif_decompose_batch(p, d_in, offsets, batch, d_out, out_offsets, d_m, d_L, d_nimfs, d_stat,
-                           d_diag);
+  st = fif_decompose_batch(p, (const float*)b[0].dev, offsets, batch, (float*)b[1].dev,
+                           out_offsets, (int32_t*)b[2].dev, (int32_t*)b[3].dev,
+                           (int32_t*)b[4].dev, (int32_t*)b[5].dev, (fif_imf_diag*)b[6].dev);
   if (st != FIF_OK) return st;
-  e = cudaMemcpyAsync(imfs, d_out, out_b, cudaMemcpyDeviceToHost, s);
-  if (e == cudaSuccess && mi_b) e = cudaMemcpyAsync(m, d_m, mi_b, cudaMemcpyDeviceToHost, s);
-  if (e == cudaSuccess && mi_b) e = cudaMemcpyAsync(mask_len, d_L, mi_b, cudaMemcpyDeviceToHost, s);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(n_imfs, d_nimfs, si_b, cudaMemcpyDeviceToHost, s);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(sig_status, d_stat, si_b, cudaMemcpyDeviceToHost, s);
-  if (e == cudaSuccess && diag) e = cudaMemcpyAsync(diag, d_diag, dg_b, cudaMemcpyDeviceToHost, s);
+  for (Buf& x : b)
+    if (x.staged && x.out && e == cudaSuccess)
+      e = cudaMemcpyAsync(x.host, x.dev, x.bytes, cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   return cuda_status(e);
 }

@@ -190,6 +190,49 @@ def test_host_entry_point_matches_device_batch(dev):
     assert np.array_equal(hres.status, dres.status.cpu().numpy())
 
 
+@pytest.mark.parametrize("pinned", ["all", "big", "none"])
+def test_host_entry_point_uses_pinned_buffers_in_place(dev, pinned):
+    """Mapped page-locked host buffers are read and written in place by the
+    kernels (fused and multi-pass classes); others are staged.  Every mix gives
+    the device batch's results."""
+    lens = np.array([512, 4096, 729, 1 << 15, 4096])
+    sigs = [signals.component_signal(55, i, int(n)) for i, n in enumerate(lens)]
+    offs = np.concatenate([[0], np.cumsum(lens)]).astype(np.int64)
+    flat = np.concatenate(sigs).astype(np.float32)
+    B, K = lens.size, 6
+    keep = []
+
+    def buf(shape, dtype, pin):
+        t = torch.zeros(shape, dtype=dtype)
+        t = t.pin_memory() if pin else t
+        keep.append(t)
+        return t.numpy()
+
+    big, small = pinned in ("all", "big"), pinned == "all"
+    with fif.Plan(max_n=1 << 15, max_imfs=K) as plan:
+        dres = plan.decompose_batch(torch.from_numpy(flat).to(dev), offs, diag=True)
+        torch.cuda.synchronize()
+        oo = fif.out_layout(lens, K)
+        h_in = buf(flat.shape, torch.float32, big)
+        h_in[:] = flat
+        out = dict(imfs=buf((int(oo[-1] + lens[-1] * (K + 1)),), torch.float32, big),
+                   m=buf((B, K), torch.int32, small), mask_len=buf((B, K), torch.int32, small),
+                   n_imfs=buf((B,), torch.int32, small), status=buf((B,), torch.int32, small),
+                   diag=buf((B, K + 1, 4), torch.int32, small))
+        hres = plan.decompose_batch_host(h_in, offs, diag=True, out=out)
+    d_imfs = dres.imfs.cpu().numpy()
+    d_nim = dres.n_imfs.cpu().numpy()
+    assert np.array_equal(hres.n_imfs, d_nim)
+    assert np.array_equal(hres.status, dres.status.cpu().numpy())
+    for i in range(B):
+        k1, n = int(d_nim[i]) + 1, int(lens[i])
+        a = slice(int(oo[i]), int(oo[i]) + k1 * n)
+        assert np.array_equal(hres.imfs[a], d_imfs[a])
+        assert np.array_equal(hres.m[i, :k1 - 1], dres.m.cpu().numpy()[i, :k1 - 1])
+        assert np.array_equal(hres.mask_len[i, :k1 - 1], dres.mask_len.cpu().numpy()[i, :k1 - 1])
+        assert np.array_equal(hres.diag[i, :k1], dres.diag.cpu().numpy()[i, :k1])
+
+
 def test_full_size_batch_sampled(dev, oracle_mod):
     """1024 x 16384 in the launch configuration the benchmark times; sampled signals
     against the oracle, every signal against the reconstruction identity."""
