@@ -62,11 +62,12 @@ typedef enum {
                             constant); the window is the autocorrelation h * h divided by its
                             sum, half-support L like the triangle's, and
                             w_hat_k = |DFT(h)_k|^2 / (sum h)^2 in [0, 1].  A constant shape is
-                            the triangle.  Tabulated for every L when the plan first meets a
-                            length n (Lmax * P * 16 bytes of device memory, Lmax = (n+1)/2,
-                            P = n/2+1).  Lengths that take the multi-pass path, FIF_APRIORI_N0,
-                            FIF_FORCE_MULTIPASS and fif_decompose_noalloc return
-                            FIF_EUNSUPPORTED with it. */
+                            the triangle.  Fused and staged lengths: tabulated for every L
+                            when the plan first meets a length n (Lmax * P * 16 bytes of
+                            device memory, Lmax = (n+1)/2, P = n/2+1).  Multi-pass lengths:
+                            each IMF's row is computed for its L (a float-float transform of
+                            h per IMF, P * 8 more bytes per signal).  FIF_APRIORI_N0 and
+                            fif_decompose_noalloc return FIF_EUNSUPPORTED with it. */
 } fif_window;
 
 typedef enum {

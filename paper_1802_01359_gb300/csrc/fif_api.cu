@@ -69,6 +69,7 @@ struct LargeBuffers {
   float2* row = nullptr;
   int* st = nullptr;
   unsigned char* part = nullptr;
+  double* om64 = nullptr;  // shape window rows
   LgSig* d_sigs = nullptr;
 };
 
@@ -270,6 +271,7 @@ fif_status get_tables(fif_plan_t p, int64_t n, LengthTables** out) {
   t.sched.wtab = t.wtab;
   t.sched.sin64 = t.sin64;
   t.sched.om64 = t.om64;
+  t.sched.om64_stride = s.P;
   if (e == cudaSuccess) {
     if (p->d_shape) {
       e = build_twiddles(s.n, t.tw, t.tw_lo, t.sin64, p->stream);
@@ -319,7 +321,7 @@ fif_status validate_desc(const fif_plan_desc* d) {
   if (d->window != FIF_WIN_TRIANGLE && d->window != FIF_WIN_SHAPE) return FIF_EINVAL;
   if (d->window == FIF_WIN_SHAPE) {
     if (!shape_valid(d->window_shape, d->window_shape_len)) return FIF_EINVAL;
-    if (d->flags & (FIF_APRIORI_N0 | FIF_FORCE_MULTIPASS)) return FIF_EUNSUPPORTED;
+    if (d->flags & FIF_APRIORI_N0) return FIF_EUNSUPPORTED;
   }
   if (d->precision != FIF_PREC_FP32) return FIF_EUNSUPPORTED;
   if (!(d->delta > 0.0) || !isfinite(d->delta)) return FIF_EINVAL;
@@ -467,7 +469,6 @@ fif_status get_large(fif_plan_t p, int64_t n, LargeTables** out) {
     *out = &it->second;
     return FIF_OK;
   }
-  if (p->d_shape) return FIF_EUNSUPPORTED;  // the multi-pass path has the triangle only
   LargeTables lt;
   if (!make_large_sched(n, p->smem_optin, lt.G)) return FIF_EUNSUPPORTED;
   LgSched& G = lt.G;
@@ -507,6 +508,10 @@ fif_status get_large(fif_plan_t p, int64_t n, LargeTables** out) {
   G.S.tw = tw;
   G.S.tw_lo = twl;
   G.S.sin64 = s64;
+  G.S.om64 = nullptr;  // shape window: each kernel points it at its signal's row
+  G.S.om64_stride = 0;
+  G.shape = p->d_shape;
+  G.shape_len = (int)p->shape.size();
   G.S1.tw = tw1;
   G.S1.tw_lo = tw1l;
   G.S2.tw = tw2;
@@ -562,6 +567,7 @@ fif_status large_buffers(fif_plan_t p, const LgSched& G, int nsig, LargeBuffers*
   b.row = (float2*)alloc(8 * P * S);
   b.st = (int*)alloc(sizeof(int) * kLgStateWords * S);
   b.part = (unsigned char*)alloc((size_t)G.sel_blocks * kSelCand * kSelPartBytes * S);
+  if (G.shape) b.om64 = (double*)alloc(sizeof(double) * P * S);
   b.d_sigs = (LgSig*)alloc(sizeof(LgSig) * S);
   if (e != cudaSuccess) {
     free_large_buffers(b);
@@ -599,6 +605,7 @@ fif_status upload_large_class(fif_plan_t p, const LgSched& G, LargeBuffers* b,
     g.row = b->row + P * q;
     g.st = b->st + (size_t)kLgStateWords * q;
     g.part = b->part + (size_t)G.sel_blocks * kSelCand * kSelPartBytes * q;
+    g.om64 = b->om64 ? b->om64 + P * q : nullptr;
   }
   cudaError_t e = cudaMemcpyAsync(b->d_sigs, h.data(), sizeof(LgSig) * cnt,
                                   cudaMemcpyHostToDevice, p->stream);
@@ -1158,7 +1165,7 @@ fif_status fif_plan_batch_launches(fif_plan_t p, int64_t* launches) {
   *launches = 0;
   if (!p->layout_valid) return FIF_OK;
   int64_t c = (int64_t)p->layout.classes.size();  // one fused kernel a class
-  for (const auto& lc : p->layout.lcls) c += large_launches(lc.count, p->mp);
+  for (const auto& lc : p->layout.lcls) c += large_launches(lc.count, p->mp, p->d_shape != nullptr);
   *launches = c;
   return FIF_OK;
 }

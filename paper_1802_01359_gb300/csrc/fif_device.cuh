@@ -582,11 +582,62 @@ struct W64 {
 
 __device__ __forceinline__ W64 win64(const FftSched& S, int L, int k) {
   if (S.om64) {
-    const double om = S.om64[(size_t)(L - 1) * (size_t)S.P + k];
+    const double om = S.om64[(size_t)(L - 1) * (size_t)S.om64_stride + k];
     return W64{1.0 - om, om, log2(om)};
   }
   const double w = what64(S, L, k);
   return W64{w, 1.0 - w, log1p(-w) * 1.4426950408889634};
+}
+
+// ---------------------------------------------- shape-generated windows
+// The window generated by a shape g (Theorem 4's double convolution, eq.
+// W_m): filter h_i = g((i + 1/2)/L), i < L, g the piecewise-linear interpolant
+// of glen equispaced samples on [0, 1]; w_hat_k = |H_k|^2 / H_0^2.
+
+// Bins with 1 - w_hat below this are taken from shape_om_direct.
+constexpr double kShapeDirectBelow = 1.0 / 4096.0;
+
+__device__ __forceinline__ double shape_tap(const double* __restrict__ g, int glen, int L, int i) {
+  if (glen == 1) return g[0];
+  const double t = ((double)i + 0.5) / (double)L * (double)(glen - 1);
+  int j = (int)floor(t);
+  if (j > glen - 2) j = glen - 2;
+  const double f = t - (double)j;
+  return (1.0 - f) * g[j] + f * g[j + 1];
+}
+
+__device__ __forceinline__ ff ff_from_double(double v) {
+  const float hi = (float)v;
+  return ff{hi, (float)(v - (double)hi)};
+}
+
+__device__ __forceinline__ double ff_to_double(ff a) { return (double)a.hi + (double)a.lo; }
+
+// 1 - w_hat_k in binary64 without cancellation next to DC, for one bin k >= 1,
+// by the 32 lanes of a warp together (every lane gets the result).  With the
+// phase centred on the centroid c of h (inv = 1 / sum h):
+//   H_0^2 - |H_k|^2 = (H_0 - C)(H_0 + C) - S^2,
+//   H_0 - C = 2 sum_i h_i sin^2(pi k (i - c)/n),  S = sum_i h_i sin(2 pi k (i - c)/n),
+// where S is third order in k (i - c)/n, so nothing cancels.
+__device__ __forceinline__ double shape_om_direct(const double* __restrict__ g, int glen, int L,
+                                                  int n, int k, double c, double inv) {
+  const int lane = threadIdx.x & 31;
+  const double kc = fmod((double)k * c, (double)n);  // common phase: its rounding cancels in |H_k|
+  double A = 0.0, Sk = 0.0;
+  for (int i = lane; i < L; i += 32) {
+    const double h = shape_tap(g, glen, L, i) * inv;
+    double u = ((double)(((long long)k * (long long)i) % n) - kc) / (double)n;
+    u -= rint(u);  // k (i - c)/n reduced to [-1/2, 1/2]: sin^2 and sin(2 pi u) keep their values
+    double sn, cs;
+    sincospi(u, &sn, &cs);
+    A += h * sn * sn;
+    Sk += 2.0 * h * sn * cs;
+  }
+  A = warp_reduce(A, OpAdd());
+  Sk = warp_reduce(Sk, OpAdd());
+  // (H_0 - C)(H_0 + C) - S^2 with H_0 = 1, H_0 - C = 2A, H_0 + C = 2 - 2A
+  const double om = 4.0 * A * (1.0 - A) - Sk * Sk;
+  return om < 0.0 ? 0.0 : (om > 1.0 ? 1.0 : om);
 }
 
 // --------------------------------------------------------- m selection

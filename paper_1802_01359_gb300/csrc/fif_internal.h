@@ -37,8 +37,10 @@ struct FftSched {
   const float2* tw_lo;         // [n]  binary64 value minus tw, rounded (float-float twiddles)
   const float2* wtab;          // [Lmax * P]  row L-1: {log2(1 - w_hat_k), w_hat_k}
   const double* sin64;         // [n/2 + 1]  sin(pi t/n) in binary64
-  const double* om64;          // shape window only: [Lmax * P] row L-1: 1 - w_hat_k in binary64;
-                               // nullptr for the triangle (closed form from sin64)
+  const double* om64;          // shape window only: 1 - w_hat_k in binary64 at
+                               // om64[(L-1) * om64_stride + k]; nullptr for the triangle
+                               // (closed form from sin64)
+  int om64_stride;             // P (plan table, a row per L) or 0 (one row, the current L)
 };
 
 // Method parameters as the kernels see them.
@@ -131,6 +133,8 @@ struct LgSched {
   const float2* sinff;    // {hi, lo} of sin(pi t/n), t = 0..n/2
   const float2* rcpff;    // {hi, lo} of 1/sin(pi k/n), k = 1..n/2 (entry 0 unused)
   int sel_blocks;         // CTAs per signal in the grid-wide m search
+  const double* shape;    // shape window: the shape's samples (device); nullptr: triangle
+  int shape_len;
 };
 
 // The grid-wide m search evaluates SD_j at up to kSelCand values of j per
@@ -159,6 +163,7 @@ struct LgSig {
   float2* row;
   int* st;                // kLgStateWords state words, zeroed before each run
   unsigned char* part;    // sel_blocks * kSelCand * kSelPartBytes
+  double* om64;           // shape window: 1 - w_hat_k of the current L in binary64 [P]
 };
 
 cudaError_t large_build_tables(const LgSched& G, float2* thi, float2* thi_lo, float2* tlo,
@@ -169,7 +174,7 @@ size_t large_level_smem(const LgSched& G, int level, bool ff);
 cudaError_t large_set_attrs(const LgSched& G);
 int large_sel_rounds(int max_inner);
 // Kernel launches large_run enqueues for nsig signals of one class.
-int large_launches(int nsig, const MethodParams& mp);
+int large_launches(int nsig, const MethodParams& mp, bool shape);
 
 // Kernel launchers (fif_fused.cu, fif_staged.cu, fif_tables.cu).
 cudaError_t launch_fused(int E, const SigDesc* d_sigs, int nsig, const FftSched* d_scheds,

@@ -39,6 +39,8 @@ enum {
   LG_LO, LG_HI, LG_STAT, LG_AMB, LG_CNT,  // m search: bracket, statuses, arrivals
   LG_PTIE, LG_PAD,                        // spectral peak: tie flag
   LG_PK, LG_PK_HI,                        // spectral peak key (8-byte aligned word pair)
+  LG_KDC, LG_SPAD,                        // shape window: last bin next to DC to redo
+  LG_P0, LG_P0_HI,                        // shape window: H_0^2 (binary64, 8-byte aligned)
   LG_NWORDS
 };
 static_assert(LG_PK % 2 == 0, "64-bit atomics on the peak key");
@@ -144,7 +146,7 @@ template <class Cx, bool INV, int E, int LV>
 __global__ void __launch_bounds__(512, sizeof(Cx) == 8 ? 2 : 1) lg_level(const LgSig* __restrict__ sigs, LgSched G) {
   extern __shared__ __align__(16) unsigned char smem[];
   const LgSig sg = sigs[blockIdx.y];
-  if (INV && sg.st[LG_DONE]) return;
+  if (sg.st[LG_DONE]) return;  // (zero during the input's forward transform)
   constexpr bool FF = sizeof(Cx) == 16;
   const FftSched& SR = LV == 1 ? G.S1 : G.S2;
   const int R = LV == 1 ? G.R1 : G.R2;
@@ -440,6 +442,7 @@ __global__ void lg_row(const LgSig* __restrict__ sigs, LgSched G, int it, float*
     }
     return;
   }
+  if (G.shape) return;  // the shape kernels below build the row
   const int L = sg.st[LG_L];
   for (int k = first_signal_point(step); k < G.S.P; k += step) {
     float hl, wf;
@@ -463,6 +466,121 @@ __global__ void lg_row(const LgSig* __restrict__ sigs, LgSched G, int it, float*
       }
     }
     sg.row[k] = make_float2(hl, wf);
+  }
+}
+
+// ------------------------------------------------- shape-generated window
+// For a shape window each outer iteration builds the row of its own L: the
+// filter h (h_i = g((i + 1/2)/L), i < L) goes through the forward float-float
+// levels of the input transform (za/zb are free after it), lg_split_shape
+// leaves |H_k|^2 in the signal's binary64 row, lg_shape_row turns it into
+// w_hat_k = |H_k|^2 / H_0^2 (and the FP32 row), and lg_shape_dc redoes the
+// bins next to DC, where 1 - w_hat_k < 2^-12, with shape_om_direct.
+
+__global__ void lg_pack_shape(const LgSig* __restrict__ sigs, LgSched G) {
+  const LgSig sg = sigs[blockIdx.y];
+  if (sg.st[LG_DONE]) return;
+  const int L = sg.st[LG_L], Nc = G.S.Nc;
+  ffc* za = reinterpret_cast<ffc*>(sg.za);
+  int step;
+  for (int t = first_signal_point(step); t < Nc; t += step) {
+    if (!G.S.odd) {
+      const double a = 2 * t < L ? shape_tap(G.shape, G.shape_len, L, 2 * t) : 0.0;
+      const double b = 2 * t + 1 < L ? shape_tap(G.shape, G.shape_len, L, 2 * t + 1) : 0.0;
+      za[t] = ffc{ff_from_double(a), ff_from_double(b)};
+    } else {
+      const double a = t < L ? shape_tap(G.shape, G.shape_len, L, t) : 0.0;
+      za[t] = ffc{ff_from_double(a), ff{0.f, 0.f}};
+    }
+  }
+}
+
+__device__ __forceinline__ double ffc_power(const ffc& x) {
+  const double re = ff_to_double(x.re), im = ff_to_double(x.im);
+  return re * re + im * im;
+}
+
+// |H_k|^2 into om64 (the split of lg_split_fwd, kept in float-float); H_0^2
+// into the state, and the DC-bin marker reset.
+__global__ void lg_split_shape(const LgSig* __restrict__ sigs, LgSched G) {
+  const LgSig sg = sigs[blockIdx.y];
+  if (sg.st[LG_DONE]) return;
+  const ffc* za = reinterpret_cast<const ffc*>(sg.za);
+  const int Nc = G.S.Nc;
+  int step;
+  if (!G.S.odd) {
+    for (int k = first_signal_point(step); k <= Nc / 2; k += step) {
+      const ffc zk = za[k];
+      const ffc zc = cconj(za[k == 0 ? 0 : Nc - k]);
+      const ffc e = chalf(cadd(zk, zc));
+      const ffc o = rot_i<false>(chalf(csub(zk, zc)));
+      const ffc wo = cmul(load_tw<ffc, false>(G.S, k), o);
+      const double pk = ffc_power(cadd(e, wo));
+      sg.om64[k] = pk;
+      sg.om64[Nc - k] = ffc_power(csub(e, wo));
+      if (k == 0) {
+        *reinterpret_cast<double*>(&sg.st[LG_P0]) = pk;
+        sg.st[LG_KDC] = 0;
+      }
+    }
+  } else {
+    for (int k = first_signal_point(step); k < G.S.P; k += step) {
+      const double pk = ffc_power(za[k]);
+      sg.om64[k] = pk;
+      if (k == 0) {
+        *reinterpret_cast<double*>(&sg.st[LG_P0]) = pk;
+        sg.st[LG_KDC] = 0;
+      }
+    }
+  }
+}
+
+__global__ void lg_shape_row(const LgSig* __restrict__ sigs, LgSched G) {
+  const LgSig sg = sigs[blockIdx.y];
+  if (sg.st[LG_DONE]) return;
+  const double p0 = *reinterpret_cast<const double*>(&sg.st[LG_P0]);
+  int kdc = 0, step;
+  for (int k = first_signal_point(step); k < G.S.P; k += step) {
+    if (k == 0) {
+      sg.row[0] = make_float2(-INFINITY, 1.f);
+      sg.om64[0] = 0.0;
+      continue;
+    }
+    double w = sg.om64[k] / p0;
+    w = w > 1.0 ? 1.0 : w;
+    const double om = 1.0 - w;
+    sg.row[k] = make_float2((float)(log1p(-w) * 1.4426950408889634), (float)w);
+    sg.om64[k] = om;
+    if (om < kShapeDirectBelow) kdc = k;
+  }
+  kdc = warp_reduce(kdc, OpMax());
+  if ((threadIdx.x & 31) == 0 && kdc > 0) atomicMax(&sg.st[LG_KDC], kdc);
+}
+
+// Bins 1..kdc again, one warp per bin (kShapeDcBlocks CTAs a signal).
+constexpr int kShapeDcBlocks = 16;
+__global__ void __launch_bounds__(256) lg_shape_dc(const LgSig* __restrict__ sigs, LgSched G) {
+  __shared__ RedScratch red;
+  const LgSig sg = sigs[blockIdx.y];
+  if (sg.st[LG_DONE]) return;
+  const int kdc = sg.st[LG_KDC];
+  if (kdc == 0) return;
+  const int L = sg.st[LG_L], n = G.S.n;
+  double s0 = 0.0, s1 = 0.0;
+  for (int i = threadIdx.x; i < L; i += blockDim.x) {
+    const double h = shape_tap(G.shape, G.shape_len, L, i);
+    s0 += h;
+    s1 += h * (double)i;
+  }
+  block_reduce2(s0, s1, OpAdd(), 0.0, &red);
+  const double inv = 1.0 / s0, c = s1 / s0;
+  const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int k = 1 + blockIdx.x * nw + (threadIdx.x >> 5); k <= kdc; k += gridDim.x * nw) {
+    const double om = shape_om_direct(G.shape, G.shape_len, L, n, k, c, inv);
+    if (lane == 0) {
+      sg.row[k] = make_float2((float)log2(om), (float)(1.0 - om));
+      sg.om64[k] = om;
+    }
   }
 }
 
@@ -735,8 +853,8 @@ __global__ void __launch_bounds__(kSelThreads) lg_sel64(const LgSig* __restrict_
   const int amb = st[LG_AMB];
   if (amb == 0) return;
   const int jmax = mp.max_inner, lo = st[LG_LO], hi = st[LG_HI], L = st[LG_L];
-  const FftSched& S = G.S;
-  const double inv_ln2 = 1.4426950408889634;
+  FftSched S = G.S;
+  S.om64 = sg.om64;  // shape window: this signal's binary64 row (stride 0)
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int stride = gridDim.x * blockDim.x;
   for (int i = 0; i < kSelCand; i++) {
@@ -747,9 +865,10 @@ __global__ void __launch_bounds__(kSelThreads) lg_sel64(const LgSig* __restrict_
       const float2 z = sg.spec[k];
       const double q = (double)parseval_weight(S, k) * ((double)z.x * z.x + (double)z.y * z.y);
       if (!(q > 0.0)) continue;
-      const double w = what64(S, L, k);
+      const W64 v = win64(S, L, k);
+      const double w = v.w;
       double lw = log2(q);
-      if (j > 1) lw += 2.0 * (j - 1) * log1p(-w) * inv_ln2;
+      if (j > 1) lw += 2.0 * (j - 1) * v.hl;
       if (lw == -INFINITY) continue;
       if (lw > o.M) {
         const double s = exp2(o.M - lw);
@@ -817,7 +936,9 @@ __global__ void __launch_bounds__(512, 1) lg_select_cta(const LgSig* __restrict_
   const int L = st[LG_L];
   int iflags = st[LG_IFLAGS];
   const float sc = spectrum_scale(G.S.n, __int_as_float(st[LG_SMAX]));
-  const int m = select_m_on_row(sg.spec, G.S, sg.row, L, mp, sc, iflags, &red);
+  FftSched S = G.S;
+  S.om64 = sg.om64;  // shape window: this signal's binary64 row (stride 0)
+  const int m = select_m_on_row(sg.spec, S, sg.row, L, mp, sc, iflags, &red);
   if (threadIdx.x == 0) {
     st[LG_M] = m;
     st[LG_IFLAGS] = iflags;
@@ -836,6 +957,8 @@ __global__ void lg_multiply_split(const LgSig* __restrict__ sigs, LgSched G, Met
   if (sg.st[LG_DONE]) return;
   const int m = sg.st[LG_M], L = sg.st[LG_L];
   const int Nc = G.S.Nc, n = G.S.n;
+  FftSched ST = G.S;  // the threshold's binary64 decisions: this signal's row (shape window)
+  ST.om64 = sg.om64;
   int step;
   if (!G.S.odd) {
     for (int k = first_signal_point(step); k <= Nc / 2; k += step) {
@@ -843,8 +966,8 @@ __global__ void lg_multiply_split(const LgSig* __restrict__ sigs, LgSched G, Met
       const float2 zk = sg.spec[k], zc = sg.spec[kc];
       float gk, ok, gc, oc;
       if constexpr (TH) {
-        multiplier_th(m, sg.row[k].x, G.S, L, k, mp, gk, ok);
-        multiplier_th(m, sg.row[kc].x, G.S, L, kc, mp, gc, oc);
+        multiplier_th(m, sg.row[k].x, ST, L, k, mp, gk, ok);
+        multiplier_th(m, sg.row[kc].x, ST, L, kc, mp, gc, oc);
       } else {
         multiplier(m, sg.row[k].x, gk, ok);
         multiplier(m, sg.row[kc].x, gc, oc);
@@ -865,7 +988,7 @@ __global__ void lg_multiply_split(const LgSig* __restrict__ sigs, LgSched G, Met
       const float2 z = sg.spec[k];
       float g, omg;
       if constexpr (TH)
-        multiplier_th(m, sg.row[k].x, G.S, L, k, mp, g, omg);
+        multiplier_th(m, sg.row[k].x, ST, L, k, mp, g, omg);
       else
         multiplier(m, sg.row[k].x, g, omg);
       const float2 x = make_float2(g * z.x, g * z.y);
@@ -1066,12 +1189,13 @@ cudaError_t large_set_attrs(const LgSched& G) {
 
 // The launches of large_run below, counted the same way: pack, two forward
 // levels and the split; the input's extrema; then per outer iteration the
-// peak pair (peak mode), control, window row, the m search (one CTA kernel, or
+// peak pair (peak mode), control, window row, the shape window's six (pack,
+// two forward levels, split, row, DC bins), the m search (one CTA kernel, or
 // two kernels a round), multiply, two inverse levels and the epilogue.
-int large_launches(int nsig, const MethodParams& mp) {
+int large_launches(int nsig, const MethodParams& mp, bool shape) {
   const bool cta_select = nsig >= kSelCtaMinSignals || mp.apriori;
   const int sel = cta_select ? 1 : 2 * large_sel_rounds(mp.max_inner);
-  const int per_it = (mp.peak_mask ? 2 : 0) + 2 + sel + 1 + 2 + 1;
+  const int per_it = (mp.peak_mask ? 2 : 0) + 2 + sel + 1 + 2 + 1 + (shape ? 6 : 0);
   return 4 + 1 + (mp.max_imfs + 1) * per_it;
 }
 
@@ -1106,6 +1230,16 @@ cudaError_t large_run(const LgSched& G, const LgSig* d_sigs, int nsig, const Met
     }
     lg_ctl<<<nsig, 1, 0, st>>>(d_sigs, G, mp, it, signals, out);
     lg_row<<<dim3(bx_bins, nsig), 256, 0, st>>>(d_sigs, G, it, out.imfs);
+    if (G.shape) {
+      lg_pack_shape<<<dim3(bx_pts, nsig), 256, 0, st>>>(d_sigs, G);
+      e = cudaGetLastError();
+      if (e == cudaSuccess) e = launch_level<ffc, false, 1>(G, d_sigs, nsig, st);
+      if (e == cudaSuccess) e = launch_level<ffc, false, 2>(G, d_sigs, nsig, st);
+      if (e != cudaSuccess) break;
+      lg_split_shape<<<dim3(bx_split, nsig), 256, 0, st>>>(d_sigs, G);
+      lg_shape_row<<<dim3(bx_bins, nsig), 256, 0, st>>>(d_sigs, G);
+      lg_shape_dc<<<dim3(kShapeDcBlocks, nsig), 256, 0, st>>>(d_sigs, G);
+    }
     if (cta_select) {
       lg_select_cta<<<nsig, 512, 0, st>>>(d_sigs, G, mp);
     } else {

@@ -20,25 +20,6 @@
 
 namespace fif {
 
-// Bins with 1 - w_hat below this are redone by the centred direct sum.
-constexpr double kShapeDirectBelow = 1.0 / 4096.0;
-
-__device__ __forceinline__ double shape_tap(const double* __restrict__ g, int glen, int L, int i) {
-  if (glen == 1) return g[0];
-  const double t = ((double)i + 0.5) / (double)L * (double)(glen - 1);
-  int j = (int)floor(t);
-  if (j > glen - 2) j = glen - 2;
-  const double f = t - (double)j;
-  return (1.0 - f) * g[j] + f * g[j + 1];
-}
-
-__device__ __forceinline__ ff ff_from_double(double v) {
-  const float hi = (float)v;
-  return ff{hi, (float)(v - (double)hi)};
-}
-
-__device__ __forceinline__ double ff_to_double(ff a) { return (double)a.hi + (double)a.lo; }
-
 __device__ __forceinline__ void put_row(float2* wtab, double* om64, size_t idx, double w, double om,
                                         double hl) {
   om64[idx] = om;
@@ -122,25 +103,8 @@ __global__ void __launch_bounds__(512, 1) shape_window_kernel(FftSched S, const 
   // bins 1..kdc again, one warp per bin: the centred sums in binary64
   const int lane = tid & 31, warp = tid >> 5, nwarps = nt >> 5;
   for (int k = 1 + warp; k <= kdc; k += nwarps) {
-    const double kc = fmod((double)k * c, (double)n);  // common phase: its rounding cancels in |H_k|
-    double A = 0.0, Sk = 0.0;
-    for (int i = lane; i < L; i += 32) {
-      const double h = shape_tap(g, glen, L, i) * inv;
-      double u = ((double)(((long long)k * (long long)i) % n) - kc) / (double)n;
-      u -= rint(u);  // k (i - c)/n reduced to [-1/2, 1/2]: sin^2 and sin(2 pi u) keep their values
-      double sn, cs;
-      sincospi(u, &sn, &cs);
-      A += h * sn * sn;
-      Sk += 2.0 * h * sn * cs;
-    }
-    A = warp_reduce(A, OpAdd());
-    Sk = warp_reduce(Sk, OpAdd());
-    if (lane == 0) {
-      // (H_0 - C)(H_0 + C) - S^2 with H_0 = 1, H_0 - C = 2A, H_0 + C = 2 - 2A
-      double om = 4.0 * A * (1.0 - A) - Sk * Sk;
-      om = om < 0.0 ? 0.0 : (om > 1.0 ? 1.0 : om);
-      put_row(wtab, om64, row + k, 1.0 - om, om, log2(om));
-    }
+    const double om = shape_om_direct(g, glen, L, n, k, c, inv);
+    if (lane == 0) put_row(wtab, om64, row + k, 1.0 - om, om, log2(om));
   }
 }
 

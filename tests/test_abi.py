@@ -94,7 +94,7 @@ def test_shape_window_validation(lib, g):
     assert not h.value
 
 
-@pytest.mark.parametrize("flags", [fif.APRIORI_N0, fif.FORCE_MULTIPASS])
+@pytest.mark.parametrize("flags", [fif.APRIORI_N0])
 def test_shape_window_unsupported_combinations(lib, flags):
     d, keep = _shape_desc([0.0, 1.0, 0.0], flags=flags)
     h = ctypes.c_void_p()

@@ -1,6 +1,6 @@
 """GPU parity of shape-generated windows (FIF_WIN_SHAPE: the window is h * h,
 h sampled from a shape g; Theorem 4's double convolution, eq. W_m) on the
-fused batch path and the staged single-signal path."""
+fused batch path, the staged single-signal path and the multi-pass path."""
 import numpy as np
 import pytest
 
@@ -113,11 +113,39 @@ def test_shape_pure_tone_eigenvalue(dev, oracle_mod):
     assert parity.rel_l2(_np(d.imfs)[0].astype(np.float64), want) < 1e-5
 
 
-def test_shape_long_length_is_unsupported(dev):
-    """Lengths that take the multi-pass path have the triangle only."""
-    n = 1 << 16
-    x = torch.zeros(n, device=dev)
-    with fif.Plan(max_n=n, max_imfs=2, window_shape=[1.0]) as plan:
-        with pytest.raises(fif.FifError) as e:
-            plan.decompose(x)
-        assert e.value.code == fif.FIF_EUNSUPPORTED
+def test_shape_multipass_forced_matches_oracle(dev, oracle_mod):
+    """The multi-pass path builds each IMF's row from a float-float transform of h."""
+    g = SHAPES["sine"]
+    lens = [256, 729, 1024, 2048, 4096]
+    sigs = [signals.component_signal(92, i, n) for i, n in enumerate(lens)]
+    x, offs = _pack(sigs, dev)
+    with fif.Plan(max_n=4096, max_imfs=5, window_shape=g, multipass=True) as plan:
+        res = plan.decompose_batch(x, offs, diag=True)
+        torch.cuda.synchronize()
+    for i, s in enumerate(sigs):
+        parity.compare(res.signal(i), oracle_mod.direct(s.astype(np.float64), max_imfs=5, shape=g))
+
+
+@pytest.mark.parametrize("count", [1, 9])  # grid-wide m search; one CTA per signal
+def test_shape_long_signals_match_oracle(dev, oracle_mod, count):
+    g = SHAPES["ramp"]
+    n = 1 << 15
+    sigs = [signals.component_signal(93, i, n) for i in range(count)]
+    x, offs = _pack(sigs, dev)
+    with fif.Plan(max_n=n, max_imfs=4, window_shape=g) as plan:
+        res = plan.decompose_batch(x, offs, diag=True)
+        torch.cuda.synchronize()
+    for i in range(min(count, 2)):
+        ref = oracle_mod.direct(sigs[i].astype(np.float64), max_imfs=4, shape=g)
+        parity.compare(res.signal(i), ref)
+
+
+def test_shape_long_single_with_threshold(dev, oracle_mod):
+    """The threshold's binary64 decisions read the signal's own binary64 row."""
+    g = SHAPES["rough"]
+    n = 1 << 15
+    s = signals.component_signal(94, 0, n, sigma=0.0)
+    kw = dict(max_imfs=4, gamma=0.05)
+    with fif.Plan(max_n=n, window_shape=g, **kw) as plan:
+        d = plan.decompose(torch.from_numpy(s).to(dev), diag=True)
+    parity.compare(d, oracle_mod.direct(s.astype(np.float64), shape=g, **kw))
