@@ -11,8 +11,9 @@
  *
  * Two tiers, same outer loop (Algorithm 2, Section 3):
  *   tier A  fifo_iterative(): the discrete IF of Algorithm 2 literally --
- *           repeated periodic convolution with the sampled triangle window
- *           (eq. s_m+1, eq. MatrixForm, eq. W_m), stopping rule eq. SD.
+ *           repeated periodic convolution with the sampled window (the
+ *           triangle, or the taps of a shape-generated window; eq. s_m+1,
+ *           eq. MatrixForm, eq. W_m), stopping rule eq. SD.
  *   tier B  fifo_direct(): the FIF direct method of Section 4
  *           (eq. One step_algo): DFT, multiply the spectrum by (1-w_hat)^m,
  *           inverse DFT, with m chosen by evaluating eq. SD for
