@@ -63,6 +63,9 @@ WORKLOADS = {
     "batch16384_sh": dict(desc="the batch16384 signals, window generated by the shape "
                                "g(x) = sin(pi x) (33 samples; Theorem 4's h * h); delta=1e-3, "
                                "max_inner=200, max_imfs=10"),
+    "uneven_sh": dict(desc="the uneven signals with the window generated by g(x) = sin(pi x) "
+                           "(a float-float transform of h per IMF on the multi-pass path); "
+                           "delta=1e-3, max_imfs=10"),
 }
 
 # generating shape of the batch16384_sh workload
@@ -115,9 +118,11 @@ def make_workload(name, rank=0):
     elif name == "single4096":
         s = signals.single_4096()
         data, offs = s, np.array([0, s.size], dtype=np.int64)
-    elif name == "uneven":
+    elif name in ("uneven", "uneven_sh"):
         lens = signals.uneven_lengths(4096)
         data, offs = generate(signals.W_UNEVEN, lens)
+        if name == "uneven_sh":
+            params.update(window_shape=SINE_SHAPE)
     elif name == "long":
         s = signals.long_signal()
         data, offs = s, np.array([0, s.size], dtype=np.int64)
