@@ -29,6 +29,17 @@ def main():
     r = oracle.direct(s, mask_scale=2)
     out["direct_mask_scale_2"] = {"n_imfs": r["n_imfs"], "status": r["status"], "m": r["m"].tolist(),
                                   "L": r["L"].tolist(), "kext": r["kext"].tolist()}
+    # the method's options, direct tier: a-priori N0 (Theorem 5, absolute delta), thresholded
+    # IMF (eq. I_gamma), Fourier-peak mask length (end of Sec. 2), shape window (Theorem 4)
+    modes = {"apriori_delta2": dict(apriori=True, delta=2.0, max_inner=1 << 16),
+             "threshold_gamma0.05": dict(gamma=0.05),
+             "peak_mask": dict(peak_mask=True),
+             "shape_sine33": dict(shape=np.sin(np.pi * np.linspace(0.0, 1.0, 33)))}
+    for name, kw in modes.items():
+        r = oracle.direct(s, **kw)
+        out["direct_" + name] = {"n_imfs": r["n_imfs"], "status": r["status"], "m": r["m"].tolist(),
+                                 "L": r["L"].tolist(), "kext": r["kext"].tolist(),
+                                 "imf_l2": [float(np.linalg.norm(x)) for x in r["imfs"]]}
     with open(os.path.join(HERE, "single_4096_oracle.json"), "w") as f:
         json.dump(out, f, indent=1)
 

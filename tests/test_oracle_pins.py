@@ -306,7 +306,8 @@ def test_config_single_4096_saturates_max_inner(oracle_mod):
 
 def test_golden_single_4096_regression(oracle_mod):
     """Regression fixture written by tests/golden/make_golden.py (oracle only): both tiers
-    still produce the stored integers on the n=4096 three-component signal."""
+    still produce the stored integers on the n=4096 three-component signal, and so do the
+    direct tier's options (a-priori N0, threshold, peak mask, shape window)."""
     import json
     import os
     with open(os.path.join(os.path.dirname(__file__), "golden", "single_4096_oracle.json")) as f:
@@ -317,6 +318,15 @@ def test_golden_single_4096_regression(oracle_mod):
     assert b["kext"].tolist() == g["direct"]["kext"] and b["status"] == g["direct"]["status"]
     assert g["iterative"]["m"] == g["direct"]["m"] and g["iterative"]["L"] == g["direct"]["L"]
     assert np.allclose([np.linalg.norm(x) for x in b["imfs"]], g["direct"]["imf_l2"], rtol=1e-12)
+    modes = {"apriori_delta2": dict(apriori=True, delta=2.0, max_inner=1 << 16),
+             "threshold_gamma0.05": dict(gamma=0.05),
+             "peak_mask": dict(peak_mask=True),
+             "shape_sine33": dict(shape=np.sin(np.pi * np.linspace(0.0, 1.0, 33)))}
+    for name, kw in modes.items():
+        r, ref = oracle_mod.direct(s, **kw), g["direct_" + name]
+        assert r["m"].tolist() == ref["m"] and r["L"].tolist() == ref["L"], name
+        assert r["kext"].tolist() == ref["kext"] and r["status"] == ref["status"], name
+        assert np.allclose([np.linalg.norm(x) for x in r["imfs"]], ref["imf_l2"], rtol=1e-12), name
 
 
 def _algorithm2_high_precision(s, *, max_imfs, max_inner, delta, nu=1.6, dps=60):
