@@ -41,10 +41,12 @@ enum {
   LG_PK, LG_PK_HI,                        // spectral peak key (8-byte aligned word pair)
   LG_KDC, LG_SPAD,                        // shape window: last bin next to DC to redo
   LG_P0, LG_P0_HI,                        // shape window: H_0^2 (binary64, 8-byte aligned)
+  LG_ROWOK,                               // 1: this iteration's L is the last one's, its row stands
   LG_NWORDS
 };
 static_assert(LG_PK % 2 == 0, "64-bit atomics on the peak key");
 static_assert(LG_NWORDS <= kLgStateWords, "state words");
+static_assert(LG_P0 % 2 == 0, "binary64 H_0^2 in two aligned words");
 
 // The caller's arrays of one signal.
 struct LgIO {
@@ -146,7 +148,9 @@ template <class Cx, bool INV, int E, int LV>
 __global__ void __launch_bounds__(512, sizeof(Cx) == 8 ? 2 : 1) lg_level(const LgSig* __restrict__ sigs, LgSched G) {
   extern __shared__ __align__(16) unsigned char smem[];
   const LgSig sg = sigs[blockIdx.y];
-  if (sg.st[LG_DONE]) return;  // (zero during the input's forward transform)
+  // (both zero during the input's forward transform; later the forward levels
+  // transform a shape window's h, which an unchanged L does not need again)
+  if (sg.st[LG_DONE] || (!INV && sg.st[LG_ROWOK])) return;
   constexpr bool FF = sizeof(Cx) == 16;
   const FftSched& SR = LV == 1 ? G.S1 : G.S2;
   const int R = LV == 1 ? G.R1 : G.R2;
@@ -403,6 +407,7 @@ __global__ void lg_ctl(const LgSig* __restrict__ sigs, LgSched G, MethodParams m
     return;
   }
   st[LG_FLAGS] = flags;
+  st[LG_ROWOK] = it > 0 && L == st[LG_L];  // the row of the last iteration's L is still in place
   st[LG_L] = L;
   st[LG_IFLAGS] = iflags;
   st[LG_IMAX] = 0;
@@ -442,7 +447,7 @@ __global__ void lg_row(const LgSig* __restrict__ sigs, LgSched G, int it, float*
     }
     return;
   }
-  if (G.shape) return;  // the shape kernels below build the row
+  if (G.shape || sg.st[LG_ROWOK]) return;  // shape rows: the kernels below; same L: kept
   const int L = sg.st[LG_L];
   for (int k = first_signal_point(step); k < G.S.P; k += step) {
     float hl, wf;
@@ -479,7 +484,7 @@ __global__ void lg_row(const LgSig* __restrict__ sigs, LgSched G, int it, float*
 
 __global__ void lg_pack_shape(const LgSig* __restrict__ sigs, LgSched G) {
   const LgSig sg = sigs[blockIdx.y];
-  if (sg.st[LG_DONE]) return;
+  if (sg.st[LG_DONE] || sg.st[LG_ROWOK]) return;
   const int L = sg.st[LG_L], Nc = G.S.Nc;
   ffc* za = reinterpret_cast<ffc*>(sg.za);
   int step;
@@ -504,7 +509,7 @@ __device__ __forceinline__ double ffc_power(const ffc& x) {
 // into the state, and the DC-bin marker reset.
 __global__ void lg_split_shape(const LgSig* __restrict__ sigs, LgSched G) {
   const LgSig sg = sigs[blockIdx.y];
-  if (sg.st[LG_DONE]) return;
+  if (sg.st[LG_DONE] || sg.st[LG_ROWOK]) return;
   const ffc* za = reinterpret_cast<const ffc*>(sg.za);
   const int Nc = G.S.Nc;
   int step;
@@ -537,7 +542,7 @@ __global__ void lg_split_shape(const LgSig* __restrict__ sigs, LgSched G) {
 
 __global__ void lg_shape_row(const LgSig* __restrict__ sigs, LgSched G) {
   const LgSig sg = sigs[blockIdx.y];
-  if (sg.st[LG_DONE]) return;
+  if (sg.st[LG_DONE] || sg.st[LG_ROWOK]) return;
   const double p0 = *reinterpret_cast<const double*>(&sg.st[LG_P0]);
   int kdc = 0, step;
   for (int k = first_signal_point(step); k < G.S.P; k += step) {
@@ -562,7 +567,7 @@ constexpr int kShapeDcBlocks = 16;
 __global__ void __launch_bounds__(256) lg_shape_dc(const LgSig* __restrict__ sigs, LgSched G) {
   __shared__ RedScratch red;
   const LgSig sg = sigs[blockIdx.y];
-  if (sg.st[LG_DONE]) return;
+  if (sg.st[LG_DONE] || sg.st[LG_ROWOK]) return;
   const int kdc = sg.st[LG_KDC];
   if (kdc == 0) return;
   const int L = sg.st[LG_L], n = G.S.n;
