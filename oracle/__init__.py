@@ -73,7 +73,8 @@ class _Outputs(ctypes.Structure):
                 ("L", ctypes.POINTER(ctypes.c_int)), ("kext", ctypes.POINTER(ctypes.c_int)),
                 ("n_imfs", ctypes.POINTER(ctypes.c_int)), ("status", ctypes.POINTER(ctypes.c_int)),
                 ("sd_m", ctypes.POINTER(ctypes.c_double)), ("sd_prev", ctypes.POINTER(ctypes.c_double)),
-                ("sd_trace", ctypes.POINTER(ctypes.c_double))]
+                ("sd_trace", ctypes.POINTER(ctypes.c_double)),
+                ("imf_flags", ctypes.POINTER(ctypes.c_int))]
 
 
 def _load():
@@ -243,8 +244,10 @@ def _run(fn_name, s, *, nu=1.6, mask_scale=1, delta=1e-3, max_inner=200, max_imf
     sd_m = np.zeros(max(max_imfs, 1))
     sd_prev = np.zeros(max(max_imfs, 1))
     sd_trace = np.full((max(max_imfs, 1), max_inner), np.nan) if trace else None
+    imf_flags = np.zeros(max_imfs + 1, dtype=np.int32)
     o = _Outputs(_dptr(imfs), _iptr(m), _iptr(L), _iptr(kext), _iptr(n_imfs), _iptr(status),
-                 _dptr(sd_m), _dptr(sd_prev), _dptr(sd_trace) if trace else None)
+                 _dptr(sd_m), _dptr(sd_prev), _dptr(sd_trace) if trace else None,
+                 _iptr(imf_flags))
     rc = getattr(lib, fn_name)(_dptr(s), n, ctypes.byref(p), ctypes.byref(o))
     if rc != 0:
         raise ValueError(f"{fn_name}: invalid arguments (rc={rc})")
@@ -253,7 +256,7 @@ def _run(fn_name, s, *, nu=1.6, mask_scale=1, delta=1e-3, max_inner=200, max_imf
         "imfs": imfs[:K].copy(), "remainder": imfs[K].copy(), "n_imfs": K,
         "m": m[:K].copy(), "L": L[:K].copy(), "kext": kext[:K + 1].copy(),
         "status": int(status[0]), "stop": int(status[0]) & 0xFF, "sd_m": sd_m[:K].copy(),
-        "sd_prev": sd_prev[:K].copy(),
+        "sd_prev": sd_prev[:K].copy(), "imf_flags": imf_flags[:K + 1].copy(),
     }
     if trace:
         out["sd_trace"] = sd_trace[:K].copy()
@@ -263,7 +266,8 @@ def _run(fn_name, s, *, nu=1.6, mask_scale=1, delta=1e-3, max_inner=200, max_imf
 def iterative(s, **kw):
     """Tier A: Algorithm 2 (time-domain iteration).  Returns a dict with
     imfs [K, n], remainder [n], m [K], L [K], kext [K+1], status, stop,
-    sd_m, sd_prev and optionally sd_trace [K, max_inner]."""
+    sd_m, sd_prev, imf_flags [K+1] (the flags raised at each outer step; entry K
+    is the final stop test) and optionally sd_trace [K, max_inner]."""
     return _run("fifo_iterative", s, **kw)
 
 

@@ -450,8 +450,13 @@ int fifo_iterative(const double* s, long n, const fifo_params* p, const fifo_out
       peak = fifo_spectral_peak(Xre, Xim, n, &ptie);
       free(Xre), free(Xim);
     }
-    reason = outer_test(r, n, K, p, o->kext, &L, &flags, peak, ptie);
-    if (reason) break;
+    int iflags = 0; /* flags raised at this outer step (recorded per step) */
+    reason = outer_test(r, n, K, p, o->kext, &L, &iflags, peak, ptie);
+    if (reason) {
+      flags |= iflags;
+      if (o->imf_flags) o->imf_flags[K] = iflags;
+      break;
+    }
     if (window_taps(n, L, p, c)) { /* the shape was checked: out of memory */
       free(r), free(u), free(v), free(c);
       return -2;
@@ -472,7 +477,7 @@ int fifo_iterative(const double* s, long n, const fifo_params* p, const fifo_out
       for (long i = 0; i < n; i++) Xim[i] = 0.0;
       fifo_fft(Xre, Xim, n, -1);
       fifo_window_spectrum(n, L, wk);
-      n0 = apriori_m(Xre, Xim, wk, n, p, &flags);
+      n0 = apriori_m(Xre, Xim, wk, n, p, &iflags);
       free(Xre), free(Xim), free(wk);
     }
     int j;
@@ -503,10 +508,12 @@ int fifo_iterative(const double* s, long n, const fifo_params* p, const fifo_out
     }
     int m = j > p->max_inner ? p->max_inner : j;
     if (!p->apriori) {
-      if (j > p->max_inner) flags |= FIFO_FLAG_MAX_INNER_HIT;
+      if (j > p->max_inner) iflags |= FIFO_FLAG_MAX_INNER_HIT;
       if (near_tie(sd, p->delta) || (m > 1 && near_tie(sd_prev, p->delta)))
-        flags |= FIFO_FLAG_NEAR_DELTA_TIE;
+        iflags |= FIFO_FLAG_NEAR_DELTA_TIE;
     }
+    flags |= iflags;
+    if (o->imf_flags) o->imf_flags[K] = iflags;
     o->m[K] = m;
     o->L[K] = L;
     o->sd_m[K] = sd;
@@ -560,8 +567,13 @@ int fifo_direct(const double* s, long n, const fifo_params* p, const fifo_output
     int L = 0;
     int ptie = 0;
     const long peak = p->peak_mask ? fifo_spectral_peak(Rre, Rim, n, &ptie) : 0;
-    reason = outer_test(r, n, K, p, o->kext, &L, &flags, peak, ptie);
-    if (reason) break;
+    int iflags = 0; /* flags raised at this outer step (recorded per step) */
+    reason = outer_test(r, n, K, p, o->kext, &L, &iflags, peak, ptie);
+    if (reason) {
+      flags |= iflags;
+      if (o->imf_flags) o->imf_flags[K] = iflags;
+      break;
+    }
     if (window_spectrum(n, L, p, w)) { /* the shape was checked: out of memory */
       free(r), free(Rre), free(Rim), free(Ire), free(Iim), free(w), free(E);
       return -2;
@@ -569,7 +581,7 @@ int fifo_direct(const double* s, long n, const fifo_params* p, const fifo_output
     for (long k = 0; k < n; k++) E[k] = Rre[k] * Rre[k] + Rim[k] * Rim[k];
     double sd = INFINITY, sd_prev = INFINITY;
     int j;
-    const int n0 = p->apriori ? apriori_m(Rre, Rim, w, n, p, &flags) : 0;
+    const int n0 = p->apriori ? apriori_m(Rre, Rim, w, n, p, &iflags) : 0;
     for (j = p->apriori ? p->max_inner + 1 : 1; j <= p->max_inner; j++) {
       double num = 0.0, den = 0.0;
       for (long k = 0; k < n; k++) {
@@ -589,10 +601,12 @@ int fifo_direct(const double* s, long n, const fifo_params* p, const fifo_output
     if (p->apriori) {
       m = n0;
     } else {
-      if (j > p->max_inner) flags |= FIFO_FLAG_MAX_INNER_HIT;
+      if (j > p->max_inner) iflags |= FIFO_FLAG_MAX_INNER_HIT;
       if (near_tie(sd, p->delta) || (m > 1 && near_tie(sd_prev, p->delta)))
-        flags |= FIFO_FLAG_NEAR_DELTA_TIE;
+        iflags |= FIFO_FLAG_NEAR_DELTA_TIE;
     }
+    flags |= iflags;
+    if (o->imf_flags) o->imf_flags[K] = iflags;
     for (long k = 0; k < n; k++) {
       double g = pow(1.0 - w[k], (double)m);
       double keep = -expm1((double)m * log1p(-w[k]));

@@ -83,6 +83,8 @@ typedef struct {
   double* sd_m;
   double* sd_prev;
   double* sd_trace;
+  int* imf_flags;     /* NULL, or [max_imfs + 1]: the FIFO_FLAG_* raised at each outer step
+                         (entry K: the step that extracted IMF K, or the final stop test) */
 } fifo_outputs;
 
 int fifo_iterative(const double* s, long n, const fifo_params* p, const fifo_outputs* o);

@@ -739,3 +739,24 @@ def test_shape_with_apriori_is_rejected(oracle_mod):
     s = signals.component_signal(98, 0, 64).astype(np.float64)
     with pytest.raises(ValueError):
         oracle_mod.direct(s, shape=[1.0], apriori=True)
+
+
+def test_per_step_flags_are_the_status_flags_by_step(oracle_mod):
+    """The oracle's per-step flag records OR to its status flags, and a near tie of SD_m
+    with delta is recorded at the IMF where it occurs (eq. SD, the 1e-6 delta band)."""
+    from paper_1802_01359_gb300 import signals
+    for kw in ({}, {"peak_mask": True}, {"max_inner": 30, "delta": 3e-2}):
+        s = signals.component_signal(90, 0, 1024).astype(np.float64)
+        for fn in (oracle_mod.direct, oracle_mod.iterative):
+            r = fn(s, **kw)
+            acc = 0
+            for f in r["imf_flags"]:
+                acc |= int(f)
+            assert acc == r["status"] & ~0xFF, (kw, r["imf_flags"], hex(r["status"]))
+    s = signals.component_signal(52, 3, 1024).astype(np.float64)
+    base = oracle_mod.direct(s, delta=3e-2, max_inner=100, max_imfs=3)
+    k = 1
+    delta = float(base["sd_m"][k]) * (1 + 1e-7)     # SD_m of IMF 1 within the tie band
+    r = oracle_mod.direct(s, delta=delta, max_inner=100, max_imfs=3)
+    assert r["m"][k] == base["m"][k]
+    assert r["imf_flags"][k] & oracle_mod.FLAG_NEAR_DELTA_TIE
