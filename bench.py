@@ -1,21 +1,22 @@
 """Benchmark: decomposed samples/s of FFT-based Iterative Filtering on GB300.
 
-Workload: 1024 independent float32 signals of n = 16384 samples, each 2-5
-chirped, amplitude-modulated components plus N(0, 0.01^2) noise (seeded,
-synthetic), triangle window, nu = 1.6, delta = 1e-3, max_inner = 200,
-max_imfs = 10.  One step = the full decomposition of the batch (every IMF and
-the remainder) through fif_decompose_batch.
+Default workload (the large uniform batch): 65536 independent float32 signals
+of n = 4096 samples, each 2-5 chirped, amplitude-modulated components plus
+N(0, 0.01^2) noise (seeded, synthetic), triangle window, nu = 1.6,
+delta = 1e-3, max_inner = 200, max_imfs = 12.  One step = the full
+decomposition of the batch (every IMF and the remainder) through
+fif_decompose_batch.  Other workloads: --workload (see WORKLOADS).
 
-Prints ONE JSON line (rank 0).  value = whole-job samples/s of the fused batch
-path with inputs resident in HBM; e2e = the same through
-fif_decompose_batch_host with pinned host buffers (copies inside the timed
-region); plain = the staged one-launch-per-step path on a subset of signals;
-roofline = the fused kernel's algorithmic HBM bytes per launch / its measured
-duration against the measured copy bandwidth; cpu_baseline = the FP64 oracle
-(direct method) on a bounded sample, timed on the host cores, whose outputs
-also give the parity summary of the sampled signals.
+Prints ONE JSON line (rank 0).  value = whole-job samples/s of the batch path
+with inputs resident in HBM; e2e = the same through fif_decompose_batch_host
+with pinned host buffers (the host-link transfers inside the timed region);
+plain = the staged one-launch-per-step path on a subset of signals; roofline =
+the fused kernel's algorithmic HBM bytes per launch / its measured duration
+against the measured copy bandwidth; cpu_baseline = the FP64 oracle (direct
+method) on a bounded sample, timed on the host cores, whose outputs also give
+the parity summary of the sampled signals.
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference] [--workload NAME]
 """
 from __future__ import annotations
 
@@ -36,23 +37,24 @@ sys.path.insert(0, ROOT)
 
 METRIC = "decomposed samples/s (batched FIF vs plain) at stated IMF error; HBM roofline %"
 UNIT = "samples/s"
-BATCH, N = 1024, 16384
 PARAMS = dict(nu=1.6, mask_scale=1, delta=1e-3, max_inner=200, max_imfs=10)
-WORKLOAD = (f"batch of {BATCH} float32 signals, n={N}, 2-5 chirped AM components + N(0,0.01^2) "
-            "noise; triangle window, nu=1.6, delta=1e-3, max_inner=200, max_imfs=10")
+DEFAULT_WORKLOAD = "batch4096"
 
 # Other synthetic workloads (not the default line): name -> description, generator args
 WORKLOADS = {
-    "batch16384": dict(desc=WORKLOAD),
+    "batch4096": dict(desc="65536 float32 signals, n=4096, 2-5 chirped AM components + "
+                           "N(0,0.01^2) noise; triangle window, nu=1.6, delta=1e-3, max_inner=200, "
+                           "max_imfs=12"),
+    "batch4096_d1e-4": dict(desc="65536 float32 signals, n=4096, as batch4096 with delta=1e-4"),
+    "batch16384": dict(desc="1024 float32 signals, n=16384, 2-5 chirped AM components + "
+                            "N(0,0.01^2) noise; triangle window, nu=1.6, delta=1e-3, "
+                            "max_inner=200, max_imfs=10"),
     "single4096": dict(desc="one n=4096 three-component test signal (noise from default_rng(0)); "
                             "delta=1e-3, max_inner=200, max_imfs=10"),
     "uneven": dict(desc="4096 float32 signals, n log-uniform in [256, 2^20] rounded to 2^a 3^b, "
                         "2-5 chirped AM components + noise; delta=1e-3, max_imfs=10"),
     "long": dict(desc="one float32 signal, n=2^24, 6 components f0=10^{0..6}, noise 1e-3; "
                       "delta=1e-3, max_imfs=10"),
-    "batch4096": dict(desc="65536 float32 signals, n=4096, 2-5 chirped AM components + noise; "
-                           "delta=1e-3, max_imfs=12"),
-    "batch4096_d1e-4": dict(desc="65536 float32 signals, n=4096, as batch4096 with delta=1e-4"),
     "batch16384_n0": dict(desc="the batch16384 signals with m from the a-priori bound of "
                                "Theorem 5 (eq. N0_discrete; absolute delta=2.0, "
                                "max_inner=65536, max_imfs=10)"),
@@ -100,13 +102,27 @@ def generate(wid, lens, first=0):
     return data, offs
 
 
+# uniform batches: workload -> (seed stream, signals per rank, n); rank r decomposes signals
+# r*count .. r*count+count-1 of the stream (weak scaling, disjoint batches)
+UNIFORM = {"batch4096": ("W_BATCH_4096", 65536, 4096), "batch4096_d1e-4": ("W_BATCH_4096", 65536, 4096),
+           "batch16384": ("W_BATCH_16384", 1024, 16384), "batch16384_n0": ("W_BATCH_16384", 1024, 16384),
+           "batch16384_th": ("W_BATCH_16384", 1024, 16384), "batch16384_pk": ("W_BATCH_16384", 1024, 16384),
+           "batch16384_sh": ("W_BATCH_16384", 1024, 16384)}
+
+
+def first_signal(name, rank):
+    """Index of rank's first signal in the workload's seed stream."""
+    return rank * UNIFORM[name][1] if name in UNIFORM else 0
+
+
 def make_workload(name, rank=0):
     """(data, offsets, params) of a named workload."""
     from paper_1802_01359_gb300 import signals
     params = dict(PARAMS)
     if name in ("batch16384", "batch16384_n0", "batch16384_th", "batch16384_pk",
                 "batch16384_sh"):
-        data, offs = generate(signals.W_BATCH_16384, np.full(BATCH, N), first=rank * BATCH)
+        data, offs = generate(signals.W_BATCH_16384, np.full(1024, 16384),
+                              first=first_signal(name, rank))
         if name == "batch16384_n0":
             params.update(delta=2.0, max_inner=1 << 16, apriori_n0=True)
         if name == "batch16384_th":
@@ -127,7 +143,8 @@ def make_workload(name, rank=0):
         s = signals.long_signal()
         data, offs = s, np.array([0, s.size], dtype=np.int64)
     elif name in ("batch4096", "batch4096_d1e-4"):
-        data, offs = generate(signals.W_BATCH_4096, np.full(65536, 4096))
+        data, offs = generate(signals.W_BATCH_4096, np.full(65536, 4096),
+                              first=first_signal(name, rank))
         params["max_imfs"] = 12
         if name == "batch4096_d1e-4":
             params["delta"] = 1e-4
@@ -264,61 +281,106 @@ def oracle_sample(data, offs, idx, threads, params=None):
     return res, time.perf_counter() - t0
 
 
-def parity_summary(res_gpu, refs, idx):
-    int_mismatch, errs, flagged = 0, [], 0
+def _step_divergence(g, r):
+    """First outer step where the GPU result g (with diag records) and the oracle result r
+    part, as (step, what, excused): excused when the side-specific tie flag of THAT step
+    (the GPU's diag[k].flags or the oracle's imf_flags[k]) allows it.  An extrema count
+    that differs (flagged) but leaves the stop test and L unchanged does not part them.
+    None if the decisions agree everywhere (stop tests, L, m, IMF count, stop reason)."""
+    EXT, NDT = 1 << 9, 1 << 8
+    K_g, K_r = g.n_imfs, r["n_imfs"]
+    m = g.m.cpu().numpy() if hasattr(g.m, "cpu") else np.asarray(g.m)
+    L = g.mask_len.cpu().numpy() if hasattr(g.mask_len, "cpu") else np.asarray(g.mask_len)
+    for k in range(min(K_g, K_r) + 1):
+        fl = int(g.diag[k]["flags"]) | int(r["imf_flags"][k])
+        ke_g, ke_r = int(g.diag[k]["k_extrema"]), int(r["kext"][k])
+        if ke_g != ke_r and (not (fl & EXT) or (ke_g < 2) != (ke_r < 2)):
+            return k, "extrema", bool(fl & EXT)
+        if k == K_g or k == K_r:
+            break
+        if L[k] != r["L"][k]:
+            return k, "L", bool(fl & EXT)
+        if m[k] != r["m"][k]:
+            return k, "m", bool(fl & NDT)
+    if K_g != K_r or g.stop != r["stop"]:
+        return min(K_g, K_r), "count", False
+    return None
+
+
+def parity_summary(res_gpu, refs, idx, statuses):
+    """Parity of the sampled signals against the oracle, with the per-step tie rule of the
+    tests: integers exact, a divergence counted as flagged only when a tie flag of that
+    step excuses it; IMF and remainder relative L2 errors of every compared row; and the
+    fraction of all signals of the batch whose status carries each tie flag."""
+    exact, flagged, unflagged, errs, rerrs = 0, 0, 0, [], []
     for r, i in zip(refs, idx):
         g = res_gpu.signal(int(i))
-        K = g.n_imfs
-        m = g.m.cpu().numpy()[:K]
-        L = g.mask_len.cpu().numpy()[:K]
-        same = (K == r["n_imfs"] and np.array_equal(m, r["m"]) and np.array_equal(L, r["L"]))
-        if not same:
-            if g.status & (3 << 8):
-                flagged += 1
-            else:
-                int_mismatch += 1
-            continue
+        div = _step_divergence(g, r)
+        upto = g.n_imfs if div is None else div[0]
         imfs = g.imfs.cpu().numpy().astype(np.float64)
-        for k in range(K):
+        for k in range(upto):
             errs.append(float(np.linalg.norm(imfs[k] - r["imfs"][k]) / np.linalg.norm(r["imfs"][k])))
-    return {"signals": len(idx), "int_mismatch_unflagged": int_mismatch,
-            "diverged_flagged": flagged,
+        if div is None:
+            exact += 1
+            nr = np.linalg.norm(r["remainder"])
+            rerrs.append(float(np.linalg.norm(imfs[g.n_imfs] - r["remainder"]) / nr) if nr > 0
+                         else float(np.linalg.norm(imfs[g.n_imfs])))
+        elif div[2]:
+            flagged += 1
+        else:
+            unflagged += 1
+    st = np.asarray(statuses, dtype=np.int64)
+    frac = lambda b: float(((st & b) != 0).mean()) if st.size else 0.0
+    return {"signals": len(idx), "exact": exact, "diverged_flagged": flagged,
+            "int_mismatch_unflagged": unflagged,
             "max_imf_rel_l2": max(errs) if errs else None,
-            "median_imf_rel_l2": float(np.median(errs)) if errs else None}
+            "median_imf_rel_l2": float(np.median(errs)) if errs else None,
+            "max_remainder_rel_l2": max(rerrs) if rerrs else None,
+            "rule": "per-step flags (GPU diag record or oracle step record)",
+            "tie_fraction_all_signals": {"extrema_tie": frac(1 << 9), "near_delta_tie": frac(1 << 8),
+                                         "fp64_tiebreak": frac(1 << 11)}}
 
 
 def run_reference(args, rank, world):
-    """Reference arm: the FP64 oracle on the host cores, on bounded samples of the workload.
-    The per-step sample is sized from a warm-up step so that the K timed steps take
-    about a minute in total."""
+    """Reference arm: the FP64 oracle on the host cores, on bounded samples of the same
+    workload.  The per-step sample is sized from the warm-up steps so that the K timed
+    steps take about a minute in total."""
     if rank != 0:
         return
-    from paper_1802_01359_gb300 import signals
+    data, offs, params = make_workload(args.workload)
+    lens = np.diff(offs)
     threads = os.cpu_count() or 1
-    pool = 4 * threads
-    data, offs = signals.batch(signals.W_BATCH_16384, pool, N)
+    order = [int(i) for i in np.random.default_rng(777).permutation(lens.size)]
+    first = order[:threads]
     t_warm = None
     for _ in range(args.warmup):
-        _, dt = oracle_sample(data, offs, list(range(threads)), threads)
+        _, dt = oracle_sample(data, offs, first, threads, params)
         t_warm = dt if t_warm is None else min(t_warm, dt)
-    per_step = int(threads * 60.0 / (max(args.steps, 1) * t_warm))
-    per_step = max(1, min(pool, per_step))
-    idx = list(range(per_step))
-    used = min(threads, per_step)
+    rate = float(lens[first].sum()) / t_warm          # samples/s on all cores
+    want = rate * 60.0 / max(args.steps, 1)           # samples per timed step
+    idx, tot = [], 0
+    for i in order:
+        if idx and tot + lens[i] > want:
+            break
+        idx.append(i)
+        tot += int(lens[i])
+    used = min(threads, len(idx))
     t = 0.0
     for _ in range(args.steps):
-        _, dt = oracle_sample(data, offs, idx, used)
+        _, dt = oracle_sample(data, offs, idx, used, params)
         t += dt
-    value = per_step * N * args.steps / t
+    value = tot * args.steps / t
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": {"workload": WORKLOAD, "batch": BATCH, "n": N,
-                                        "step_sample_signals": per_step},
+        "data": "synthetic",
+        "config": {"workload": WORKLOADS[args.workload]["desc"], "name": args.workload,
+                   "signals": int(lens.size), "samples": int(offs[-1]),
+                   "step_sample_signals": len(idx)},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": used, "kind": "oracle",
-                         "sample": f"{per_step} signals of the workload per step, FP64 direct "
-                                   "method (tier B), one signal per thread"},
+                         "sample": f"{len(idx)} random signals of the workload ({tot} samples) "
+                                   "per step, FP64 direct method (tier B), one signal per thread"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -330,7 +392,7 @@ def main():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="fif")
-    ap.add_argument("--workload", default="batch16384", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
     ap.add_argument("--cpu-sample", type=int, default=48)
     ap.add_argument("--plain-signals", type=int, default=64)
     ap.add_argument("--no-e2e", action="store_true")
@@ -526,12 +588,17 @@ def main():
             tot += int(lens[i])
         idx.sort()
         refs, tc = oracle_sample(data, offs, idx, threads, params)
+        # the sampled signals' per-IMF diag records come from one more (untimed) call with
+        # diagnostics on; the timed outputs give the batch's status words
+        dres = plan.decompose_batch(x, offs, diag=True)
+        torch.cuda.synchronize()
         result["cpu_baseline"] = {"value": tot / tc, "unit": UNIT, "cores": min(threads, len(idx)),
                                   "kind": "oracle",
                                   "sample": f"{len(idx)} random signals of the workload "
                                             f"({tot} samples), FP64 direct method (tier B), one "
                                             "signal per thread"}
-        result["parity"] = parity_summary(out, refs, idx)
+        result["parity"] = parity_summary(dres, refs, idx, out.status.cpu().numpy())
+        del dres
 
     plan.close()
     if rank == 0:

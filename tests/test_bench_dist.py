@@ -28,7 +28,8 @@ def _rank(rank, world, port, q):
     my_seconds = [1.25, 2.5][rank]
     t = bench.max_over_ranks(my_seconds, dist, "cpu")
     rate = bench.whole_job_rate(1000, world, t)
-    first = signals.component_signal(signals.W_BATCH_16384, rank * bench.BATCH, 256)
+    wid = getattr(signals, bench.UNIFORM[bench.DEFAULT_WORKLOAD][0])
+    first = signals.component_signal(wid, bench.first_signal(bench.DEFAULT_WORKLOAD, rank), 256)
     q.put((rank, t, rate, first))
     dist.barrier()
     dist.destroy_process_group()
@@ -60,3 +61,5 @@ def test_single_rank_helpers():
     import bench
     assert bench.max_over_ranks(3.0, None, "cpu") == 3.0
     assert bench.whole_job_rate(500, 1, 2.0) == 250.0
+    assert bench.first_signal("batch4096", 3) == 3 * 65536
+    assert bench.first_signal("long", 3) == 0

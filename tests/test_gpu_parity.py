@@ -1,5 +1,7 @@
 """GPU parity: the CUDA path (through the C ABI) against the FP64 oracle."""
+import concurrent.futures as cf
 import math
+import os
 
 import numpy as np
 import pytest
@@ -252,6 +254,12 @@ def test_full_size_batch_sampled(dev, oracle_mod):
         recon = torch.where(mask, imfs.double(), torch.zeros((), dtype=torch.float64, device=dev)).sum(1)
         err = (recon - x.view(B, n).double()).abs().max().item()
         assert err < 1e-5 * x.abs().max().item()
-        for i in (0, 1, 77, 512, 1023):
-            ref = oracle_mod.direct(data[offs[i]:offs[i + 1]].astype(np.float64))
-            parity.compare(res.signal(i), ref)
+        # 32 sampled signals against the oracle (host threads), with the per-step tie rule;
+        # flagged divergences bounded as in the full-size workload tests
+        idx = np.unique(np.linspace(0, B - 1, 32).astype(np.int64))
+        with cf.ThreadPoolExecutor(max_workers=max(2, os.cpu_count() or 2)) as ex:
+            refs = list(ex.map(lambda i: oracle_mod.direct(
+                data[offs[i]:offs[i + 1]].astype(np.float64)), idx))
+        flagged = sum(parity.compare(res.signal(int(i)), r)["diverged_at"] is not None
+                      for i, r in zip(idx, refs))
+        assert flagged <= 0.10 * len(idx), flagged

@@ -1,10 +1,15 @@
-"""The allocation-free entry point fif_decompose_noalloc against fif_decompose.
+"""The allocation-free entry point fif_decompose_noalloc against fif_decompose
+and the FP64 oracle.
 
 fif_decompose_noalloc serves callers that cannot allocate device memory when
-they decompose; it keeps its working arrays in one fixed device array of the
-library instead of a plan.  Two calls in a row (different signals and lengths,
-so the second call finds the first call's data in that array) must each give
-the same integers as fif_decompose and IMFs within the parity tolerance.
+they decompose (latency-critical code that cannot afford cudaMalloc's device
+synchronisation, hosts that give all device memory to their own pool at
+start-up, plug-ins that may only allocate during setup); it keeps its working
+arrays in one fixed device array of the library instead of a plan.  Calls in a
+row (different signals and lengths, so every call finds the previous call's
+data in that array) must each give the integers of fif_decompose and of the
+oracle, and IMFs within the parity tolerance; the lengths cover an even n, an
+odd n (3^8, the odd-length epilogue) and the largest supported n.
 """
 import ctypes
 
@@ -18,14 +23,20 @@ pytestmark = pytest.mark.gpu
 
 torch = pytest.importorskip("torch")
 
+LENGTHS = ((0, 4096), (1, 3072), (2, 6561), (3, fif.NOALLOC_MAX_N))
 
-def test_noalloc_matches_plan_entry_point_two_calls():
+
+@pytest.fixture(scope="module")
+def dev():
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
     from paper_1802_01359_gb300 import build
     build.build()
-    dev = torch.device("cuda:0")
-    for seed, n in ((0, 4096), (1, 3072)):
+    return torch.device("cuda:0")
+
+
+def test_noalloc_matches_plan_entry_point_and_oracle(dev, oracle_mod):
+    for seed, n in LENGTHS:
         s = signals.component_signal(61, seed, n)
         x = torch.from_numpy(s).to(dev)
         with fif.Plan(max_n=n) as plan:
@@ -41,16 +52,37 @@ def test_noalloc_matches_plan_entry_point_two_calls():
         b = ref.imfs.cpu().numpy().astype(np.float64)
         for k in range(K + 1):
             assert parity.rel_l2(a[k], b[k]) < parity.IMF_TOL, (n, k)
+        # and directly against the FP64 oracle (direct method)
+        rep = parity.compare(got, oracle_mod.direct(s.astype(np.float64)))
+        assert rep["diverged_at"] is None, (n, rep)
 
 
-def test_noalloc_rejects_lengths_above_its_maximum():
-    if not torch.cuda.is_available():
-        pytest.skip("no CUDA device")
+def test_noalloc_allocates_no_device_memory(dev):
+    s = signals.component_signal(62, 0, 4096)
+    x = torch.from_numpy(s).to(dev)
+    fif.decompose_noalloc(x)        # first call: address lookup, module load
+    torch.cuda.synchronize()
+    imfs = torch.zeros(11 * 4096, device=dev)
+    ints = torch.zeros(64, dtype=torch.int32, device=dev)
+    desc = fif.PlanDesc(0, 1.6, 1, 1e-3, 200, 10, 0, 4096, 0)
+    lib = fif.load_library()
+    free0, _ = torch.cuda.mem_get_info(dev)
+    for _ in range(3):
+        rc = lib.fif_decompose_noalloc(ctypes.byref(desc), x.data_ptr(), 4096, imfs.data_ptr(),
+                                       ints.data_ptr(), ints.data_ptr() + 64,
+                                       ints.data_ptr() + 128, ints.data_ptr() + 132, None, None)
+        assert rc == fif.FIF_OK
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info(dev)
+    assert free1 == free0
+
+
+def test_noalloc_rejects_lengths_above_its_maximum(dev):
     lib = fif.load_library()
     n = fif.NOALLOC_MAX_N * 2
-    x = torch.zeros(n, device="cuda:0")
-    out = torch.zeros(11 * n, device="cuda:0")
-    ints = torch.zeros(32, dtype=torch.int32, device="cuda:0")
+    x = torch.zeros(n, device=dev)
+    out = torch.zeros(11 * n, device=dev)
+    ints = torch.zeros(32, dtype=torch.int32, device=dev)
     desc = fif.PlanDesc(0, 1.6, 1, 1e-3, 200, 10, 0, n, 0)
     rc = lib.fif_decompose_noalloc(ctypes.byref(desc), x.data_ptr(), n, out.data_ptr(),
                                    ints.data_ptr(), ints.data_ptr() + 64, ints.data_ptr() + 40,
