@@ -83,7 +83,9 @@ typedef enum {
 /* flags, OR-ed into sig_status (any IMF) and into fif_imf_diag.flags (that IMF) */
 #define FIF_FLAG_NEAR_DELTA_TIE  (1 << 8)  /* |SD_m - delta| or |SD_{m-1} - delta| <= 1e-6 delta */
 #define FIF_FLAG_EXTREMA_TIE     (1 << 9)  /* the extrema count could change under a perturbation of
-                                              r of 2^-18 max|s| (see fif_imf_diag) */
+                                              r of 2^-18 max|s|: a first difference within
+                                              2^-17 max|s| of zero whose flip changes the
+                                              count (see fif_imf_diag) */
 #define FIF_FLAG_MAX_INNER_HIT   (1 << 10) /* SD_j >= delta for every j <= max_inner; m = max_inner */
 #define FIF_FLAG_FP64_TIEBREAK   (1 << 11) /* an m decision fell inside the FP32 screen's error band
                                               and was re-evaluated in FP64 */
@@ -269,14 +271,21 @@ fif_status fif_plan_batch_launches(fif_plan_t plan, int64_t* launches);
  * Same method, parameters and outputs as fif_decompose, but no plan: desc is
  * read on every call (desc->max_n is ignored) and every array besides the
  * caller's inputs and outputs lives in one fixed file-scope device array of
- * the library (about 0.8 MB, sized for FIF_NOALLOC_MAX_N), which each GPU that
- * loads the library keeps until the process exits.  The call allocates and
- * frees nothing.
+ * the library (FIF_NOALLOC_SCRATCH_BYTES = 656,640 bytes, sized for
+ * FIF_NOALLOC_MAX_N), which each GPU that loads the library keeps until the
+ * process exits.  The call allocates and frees nothing.  It runs the staged
+ * path's schedule for n, so its integers (m, L, IMF count) equal
+ * fif_decompose's.
  *   - n must be 2^a 3^b with 4 <= n <= FIF_NOALLOC_MAX_N; larger n returns
  *     FIF_EUNSUPPORTED, smaller FIF_EINVAL.
  *   - The first call on each device looks up the device address of the array
- *     (with that device current); make that first call before any stream
- *     capture.
+ *     (with that device current) and keeps it for later calls; make that
+ *     first call before any stream capture.  The address stays valid for the
+ *     life of the device's primary context: after cudaDeviceReset the library
+ *     must not be called again in that process.
+ *   - On entry the call reads and clears a pending (non-sticky) CUDA error of
+ *     the calling thread, so that an earlier, unrelated failure is not
+ *     reported as this call's.
  *   - All calls share the array.  Each call rewrites everything it reads from
  *     it, but calls whose GPU work overlaps (several streams, several host
  *     threads) race on it and must be serialised by the caller.
@@ -284,6 +293,7 @@ fif_status fif_plan_batch_launches(fif_plan_t plan, int64_t* launches);
  * fif_decompose (device memory); cuda_stream is a cudaStream_t or NULL.
  * Errors: FIF_EINVAL, FIF_EUNSUPPORTED, FIF_ECUDA. */
 #define FIF_NOALLOC_MAX_N 16384
+#define FIF_NOALLOC_SCRATCH_BYTES 656640
 fif_status fif_decompose_noalloc(const fif_plan_desc* desc, const float* signal, int64_t n,
                                  float* imfs, int32_t* m, int32_t* mask_len, int32_t* n_imfs,
                                  int32_t* sig_status, fif_imf_diag* diag, void* cuda_stream);

@@ -24,6 +24,7 @@ struct LengthTables {
   float2* wtab = nullptr;
   double* sin64 = nullptr;
   double* om64 = nullptr;  // shape window only
+  int* ltab = nullptr;     // mask length per extrema count (FftSched::ltab)
 };
 
 struct BatchLayout {
@@ -226,6 +227,13 @@ bool make_sched(int64_t n64, FftSched& s, int smem_limit = 0) {
   return make_fft_plan(s.Nc, s);
 }
 
+}  // namespace
+
+// The staged-path schedule of length n (no allocation; host arithmetic only).
+bool fif::staged_schedule(int64_t n, FftSched& s) { return make_sched(n, s, 0); }
+
+namespace {
+
 fif_status cuda_status(cudaError_t e) {
   if (e == cudaSuccess) return FIF_OK;
   if (e == cudaErrorMemoryAllocation) return FIF_ENOMEM;
@@ -266,6 +274,21 @@ fif_status get_tables(fif_plan_t p, int64_t n, LengthTables** out) {
   if (e == cudaSuccess) e = cudaMalloc(&t.wtab, sizeof(float2) * (size_t)s.Lmax * (size_t)s.P);
   if (e == cudaSuccess && p->d_shape)
     e = cudaMalloc(&t.om64, sizeof(double) * (size_t)s.Lmax * (size_t)s.P);
+  // (only when every entry fits an int; forced mask lengths read no rule)
+  const bool want_ltab = !(p->desc.flags & FIF_FORCE_L) && p->desc.nu * (double)s.n < 1e9;
+  if (e == cudaSuccess && want_ltab) e = cudaMalloc(&t.ltab, sizeof(int) * (size_t)(s.n + 1));
+  if (e == cudaSuccess && want_ltab) {
+    // the outer test's mask rule for every extrema count, in the binary64
+    // expression the kernels and the oracle evaluate: mask_scale * floor((nu * n) / k)
+    std::vector<int> h((size_t)s.n + 1, 0);
+    for (int k = 1; k <= s.n; k++) {
+      double v = p->desc.nu * (double)s.n;
+      v = v / (double)k;
+      h[(size_t)k] = p->desc.mask_scale * (int)floor(v);
+    }
+    e = cudaMemcpy(t.ltab, h.data(), sizeof(int) * h.size(), cudaMemcpyHostToDevice);
+  }
+  t.sched.ltab = t.ltab;
   t.sched.tw = t.tw;
   t.sched.tw_lo = t.tw_lo;
   t.sched.wtab = t.wtab;
@@ -287,6 +310,7 @@ fif_status get_tables(fif_plan_t p, int64_t n, LengthTables** out) {
     cudaFree(t.sin64);
     cudaFree(t.wtab);
     cudaFree(t.om64);
+    cudaFree(t.ltab);
     cudaGetLastError();
     return cuda_status(e);
   }
@@ -848,6 +872,7 @@ fif_status fif_plan_destroy(fif_plan_t p) {
     cudaFree(kv.second.wtab);
     cudaFree(kv.second.sin64);
     cudaFree(kv.second.om64);
+    cudaFree(kv.second.ltab);
   }
   cudaFree(p->d_shape);
   free_layout(p->layout);

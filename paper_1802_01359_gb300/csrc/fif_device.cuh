@@ -552,6 +552,49 @@ __device__ void inverse_real(float2* work, const FftSched& S, const TwSrc& ts) {
   fft_inplace<float2, true, E>(work, S, ts);
 }
 
+// The IMF's spectrum, the spectral remainder update and the inverse real FFT
+// in one: on entry work[k] = {g_k, 1 - g_k} (select_m_mult) and spec holds
+// r_hat.  The first step applies IMF_hat_k = g_k r_hat_k (eq. One step_algo)
+// and r_hat_k <- (1 - g_k) r_hat_k (Algorithm 2: s = s - s_m) to the bin pair
+// (k, Nc - k) that the inverse real split combines, so the multiplier needs
+// no pass of its own; then the complex inverse FFT.  Afterwards the time
+// sample t is work[t/2].x or .y (even n) or work[t].x (odd n), times n.
+template <int E>
+__device__ void inverse_real_mult(float2* spec, float2* work, const FftSched& S, const TwSrc& ts) {
+  const int tid = threadIdx.x, nt = blockDim.x;
+  if (!S.odd) {
+    const int Nc = S.Nc;
+    for (int k = tid; k <= Nc / 2; k += nt) {
+      const int kc = Nc - k;
+      const float2 gk = work[k], gc = work[kc];
+      const float2 zk = spec[k], zc = spec[kc];
+      const float2 xk = make_float2(gk.x * zk.x, gk.x * zk.y);
+      const float2 xc = make_float2(gc.x * zc.x, gc.x * zc.y);
+      spec[k] = make_float2(gk.y * zk.x, gk.y * zk.y);
+      if (kc != k) spec[kc] = make_float2(gc.y * zc.x, gc.y * zc.y);
+      // Z_k = F + i W^-k G, Z_{Nc-k} = conj(F - i W^-k G),
+      // F = X_k + conj X_{Nc-k}, G = X_k - conj X_{Nc-k}
+      const float2 f = make_float2(xk.x + xc.x, xk.y - xc.y);
+      const float2 g = make_float2(xk.x - xc.x, xk.y + xc.y);
+      const float2 wg = cmul(cconj(tw_value(ts, k)), g);
+      const float2 iwg = make_float2(-wg.y, wg.x);
+      work[k] = cadd(f, iwg);
+      if (k != 0) work[kc] = cconj(csub(f, iwg));
+    }
+  } else {
+    const int n = S.n;
+    for (int k = tid; k < S.P; k += nt) {
+      const float2 gk = work[k], zk = spec[k];
+      const float2 x = make_float2(gk.x * zk.x, gk.x * zk.y);
+      spec[k] = make_float2(gk.y * zk.x, gk.y * zk.y);
+      work[k] = x;
+      if (k != 0) work[n - k] = cconj(x);
+    }
+  }
+  __syncthreads();
+  fft_inplace<float2, true, E>(work, S, ts);
+}
+
 // ---------------------------------------------------------- window table
 
 __device__ __forceinline__ const float2* wrow(const FftSched& S, int L) {
@@ -638,6 +681,40 @@ __device__ __forceinline__ double shape_om_direct(const double* __restrict__ g, 
   // (H_0 - C)(H_0 + C) - S^2 with H_0 = 1, H_0 - C = 2A, H_0 + C = 2 - 2A
   const double om = 4.0 * A * (1.0 - A) - Sk * Sk;
   return om < 0.0 ? 0.0 : (om > 1.0 ? 1.0 : om);
+}
+
+// g = (1 - w_hat)^m = 2^(m log2(1 - w_hat)) and 1 - g; 1 - g from expm1 when
+// g is close to 1, where 1 - g would cancel.
+__device__ __forceinline__ void multiplier(int m, float hl, float& g, float& omg) {
+  const float e = (float)m * hl;
+  g = exp2f(e);
+  omg = e > -1.f ? -expm1f(e * 0.693147180559945309f) : 1.f - g;
+}
+
+// Thresholded IMF (eq. I_gamma, eq. IMF_cont_stop_threshold): bin k passes
+// whole (w_hat_k taken as 0) when (1 - w_hat_k)^m >= 1 - gamma.  Decided in
+// FP32 on m log2(1 - w_hat_k) against log2(1 - gamma) outside the rounding
+// band of both sides (table value good to 4u, the product u/2, the rounded
+// log2(1 - gamma) u/2: band 8u (|x| + |c|)), else in binary64 (the sine
+// table, or the shape window's binary64 row), as the binary64 definition
+// decides.
+__device__ __forceinline__ bool passes_whole(int m, float hl, const FftSched& S, int L, int k,
+                                             const MethodParams& mp) {
+  const float x = (float)m * hl, c = mp.log2_keep;
+  if (x == -INFINITY) return false;  // w_hat = 1
+  const float band = 8.f * 5.9604645e-8f * (fabsf(x) + fabsf(c)) + 1e-30f;
+  if (x > c + band) return true;
+  if (x < c - band) return false;
+  return pow(win64(S, L, k).om, (double)m) >= 1.0 - mp.gamma;
+}
+
+__device__ __forceinline__ void multiplier_th(int m, float hl, const FftSched& S, int L, int k,
+                                              const MethodParams& mp, float& g, float& omg) {
+  multiplier(m, hl, g, omg);
+  if (mp.threshold && passes_whole(m, hl, S, L, k, mp)) {
+    g = 1.f;
+    omg = 0.f;
+  }
 }
 
 // --------------------------------------------------------- m selection
@@ -802,19 +879,27 @@ static __device__ bool decide_sd(const Online& r, float chain, float levels, con
   return sd < mp.delta;
 }
 
-__device__ __forceinline__ Online shfl_xor_online(const Online& o, int off) {
-  return Online{__shfl_xor_sync(0xffffffffu, o.M, off), __shfl_xor_sync(0xffffffffu, o.num, off),
-                __shfl_xor_sync(0xffffffffu, o.den, off), __shfl_xor_sync(0xffffffffu, o.anum, off),
-                __shfl_xor_sync(0xffffffffu, o.aden, off)};
-}
-
+// Sums of one warp relative to a common reference: the warp's largest M (a
+// max-reduction), each lane's sums rescaled once by 2^(M_lane - M), then
+// plain sums.  Every lane gets the result.
 __device__ __forceinline__ Online warp_merge(Online o) {
+  float M = o.M;
 #pragma unroll
-  for (int off = 16; off > 0; off >>= 1) o = online_merge(o, shfl_xor_online(o, off));
-  return o;
+  for (int off = 16; off > 0; off >>= 1) M = fmaxf(M, __shfl_xor_sync(0xffffffffu, M, off));
+  const float s = o.M == -INFINITY ? 0.f : exp2f(o.M - M);  // <= 1; an empty lane adds 0
+  float num = o.num * s, den = o.den * s, anum = o.anum * s, aden = o.aden * s;
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    num += __shfl_xor_sync(0xffffffffu, num, off);
+    den += __shfl_xor_sync(0xffffffffu, den, off);
+    anum += __shfl_xor_sync(0xffffffffu, anum, off);
+    aden += __shfl_xor_sync(0xffffffffu, aden, off);
+  }
+  return Online{M, num, den, anum, aden};
 }
 
-// Block-wide merge of the per-thread sums; every thread gets the result.
+// Block-wide merge of the per-thread sums (two levels of warp_merge: at most
+// one rescale and five summation levels each); every thread gets the result.
 __device__ __forceinline__ Online online_block_reduce(Online o, RedScratch* red) {
   o = warp_merge(o);
   float* s = reinterpret_cast<float*>(red->d);
@@ -998,6 +1083,67 @@ static __device__ int select_m(const float2* spec, const FftSched& S, int L, con
   return m;
 }
 
+// The multiplier pairs {(1 - w_hat_k)^m, 1 - (1 - w_hat_k)^m} of every bin for
+// this m (thresholded when gamma > 0) into mult[0..P).
+static __device__ void multiplier_pass(float2* mult, const FftSched& S, const float2* row, int L,
+                                       int m, const MethodParams& mp) {
+  const int nt = blockDim.x;
+  for (int k0 = threadIdx.x; k0 < S.P; k0 += kSdBatch * nt) {
+    float hl[kSdBatch];
+#pragma unroll
+    for (int u = 0; u < kSdBatch; u++) {
+      const int k = k0 + u * nt;
+      hl[u] = k < S.P ? __ldg(&row[k].x) : 0.f;
+    }
+#pragma unroll
+    for (int u = 0; u < kSdBatch; u++) {
+      const int k = k0 + u * nt;
+      if (k >= S.P) break;
+      float g, omg;
+      multiplier_th(m, hl[u], S, L, k, mp, g, omg);
+      mult[k] = make_float2(g, omg);
+    }
+  }
+  __syncthreads();
+}
+
+// m of eq. SD (or the a-priori bound) as select_m, then the IMF's multiplier
+// pairs of every bin in mult[0..P) for inverse_real_mult.  (Computing the
+// pairs inside the first screen pass, speculatively for m = max_inner, was
+// measured slower: the longer loop body spills at 64 registers a thread.)
+static __device__ int select_m_mult(const float2* spec, float2* mult, const FftSched& S, int L,
+                                    const MethodParams& mp, float sc, int& flags,
+                                    RedScratch* red) {
+  const float2* row = wrow(S, L);
+  if (mp.apriori) {
+    const int m = apriori_m(spec, S, L, mp, flags, red);
+    multiplier_pass(mult, S, row, L, m, mp);
+    return m;
+  }
+  MSelState st;
+  st.sc = sc;
+  st.flags = 0;
+  int m;
+  const int jmax = mp.max_inner;
+  if (!sd_below(spec, S, row, L, jmax, mp, st, red)) {
+    m = jmax;
+    st.flags |= FIF_FLAG_MAX_INNER_HIT;
+  } else {
+    int lo = 0, hi = jmax;
+    while (hi - lo > 1) {
+      const int mid = lo + (hi - lo) / 2;
+      if (sd_below(spec, S, row, L, mid, mp, st, red))
+        hi = mid;
+      else
+        lo = mid;
+    }
+    m = hi;
+  }
+  multiplier_pass(mult, S, row, L, m, mp);
+  flags |= st.flags;
+  return m;
+}
+
 // select_m on an explicit window row (row[k] = {log2(1 - w_hat_k), w_hat_k} for
 // the current L), for paths that compute the row per IMF instead of keeping
 // the whole table.
@@ -1026,40 +1172,6 @@ static __device__ int select_m_on_row(const float2* spec, const FftSched& S, con
   }
   flags |= st.flags;
   return m;
-}
-
-// g = (1 - w_hat)^m = 2^(m log2(1 - w_hat)) and 1 - g; 1 - g from expm1 when
-// g is close to 1, where 1 - g would cancel.
-__device__ __forceinline__ void multiplier(int m, float hl, float& g, float& omg) {
-  const float e = (float)m * hl;
-  g = exp2f(e);
-  omg = e > -1.f ? -expm1f(e * 0.693147180559945309f) : 1.f - g;
-}
-
-// Thresholded IMF (eq. I_gamma, eq. IMF_cont_stop_threshold): bin k passes
-// whole (w_hat_k taken as 0) when (1 - w_hat_k)^m >= 1 - gamma.  Decided in
-// FP32 on m log2(1 - w_hat_k) against log2(1 - gamma) outside the rounding
-// band of both sides (table value good to 4u, the product u/2, the rounded
-// log2(1 - gamma) u/2: band 8u (|x| + |c|)), else in binary64 (the sine
-// table, or the shape window's binary64 row), as the binary64 definition
-// decides.
-__device__ __forceinline__ bool passes_whole(int m, float hl, const FftSched& S, int L, int k,
-                                             const MethodParams& mp) {
-  const float x = (float)m * hl, c = mp.log2_keep;
-  if (x == -INFINITY) return false;  // w_hat = 1
-  const float band = 8.f * 5.9604645e-8f * (fabsf(x) + fabsf(c)) + 1e-30f;
-  if (x > c + band) return true;
-  if (x < c - band) return false;
-  return pow(win64(S, L, k).om, (double)m) >= 1.0 - mp.gamma;
-}
-
-__device__ __forceinline__ void multiplier_th(int m, float hl, const FftSched& S, int L, int k,
-                                              const MethodParams& mp, float& g, float& omg) {
-  multiplier(m, hl, g, omg);
-  if (mp.threshold && passes_whole(m, hl, S, L, k, mp)) {
-    g = 1.f;
-    omg = 0.f;
-  }
 }
 
 // IMF spectrum work = (1 - w_hat)^m r_hat (eq. One step_algo) and the
@@ -1189,8 +1301,20 @@ static __device__ EpiOut epilogue_extrema_even(const float2* work, float* rem, f
     }
     const float p_rb = __shfl_up_sync(0xffffffffu, rb, 1);
     const float n_ra = __shfl_down_sync(0xffffffffu, ra, 1);
-    const float n_rb = __shfl_down_sync(0xffffffffu, rb, 1);
-    if (act && lane != 0 && lane != 31 && t != Nc - 1) pair_terms(p_rb, ra, rb, n_ra, n_rb, tau, ext, zc, tie);
+    // the pair's extrema and crossings (as pair_terms); its tie test only in the
+    // rare warps where one of its two differences lies within tau of zero
+    const bool in = act && lane != 0 && lane != 31 && t != Nc - 1;
+    const float dm1 = ra - p_rb, d0 = rb - ra, d1 = n_ra - rb;
+    if (in) {
+      ext += (dm1 > 0.f && d0 < 0.f) || (dm1 < 0.f && d0 > 0.f);
+      ext += (d0 > 0.f && d1 < 0.f) || (d0 < 0.f && d1 > 0.f);
+      zc += (ra > 0.f && rb < 0.f) || (ra < 0.f && rb > 0.f);
+      zc += (rb > 0.f && n_ra < 0.f) || (rb < 0.f && n_ra > 0.f);
+    }
+    if (__any_sync(0xffffffffu, in && (fabsf(d0) <= tau || fabsf(d1) <= tau))) {
+      const float n_rb = __shfl_down_sync(0xffffffffu, rb, 1);
+      if (in) tie |= diff_tie(dm1, d0, d1, tau) || diff_tie(d0, d1, n_rb - n_ra, tau);
+    }
   }
   __syncthreads();
   const int nblk = (Nc + 31) >> 5;
@@ -1343,7 +1467,7 @@ static __device__ SpecPeak spectral_peak(const float2* spec, const FftSched& S, 
 // count k still decides the stop.
 __device__ __forceinline__ int outer_test(int k, int K, int n, const MethodParams& mp,
                                           const int32_t* forced_L, int& L, int& flags,
-                                          int peak = 0) {
+                                          int peak = 0, const int* ltab = nullptr) {
   if (mp.force_L) {
     if (K == mp.max_imfs) return FIF_STOP_MAX_IMFS;
     L = forced_L[K];
@@ -1353,9 +1477,13 @@ __device__ __forceinline__ int outer_test(int k, int K, int n, const MethodParam
   }
   if (k < 2) return FIF_STOP_EXTREMA;
   const int kk = mp.peak_mask ? 2 * (peak > 0 ? peak : 1) : k;
-  double t = mp.nu * (double)n;
-  t = t / (double)kk;
-  L = mp.mask_scale * (int)floor(t);
+  if (ltab) {
+    L = ltab[kk];  // the same binary64 rule, tabulated per length on the host
+  } else {
+    double t = mp.nu * (double)n;
+    t = t / (double)kk;
+    L = mp.mask_scale * (int)floor(t);
+  }
   if (L < 2) {
     L = 2;
     flags |= FIF_FLAG_L_CLAMPED;

@@ -80,7 +80,7 @@ __device__ void decompose_resident(FusedShared* sh, const MethodParams& mp,
       int L = 0, iflags = ls.etie ? FIF_FLAG_EXTREMA_TIE : 0;
       if (pk.tie) iflags |= FIF_FLAG_EXTREMA_TIE;
       sh->ot[0] = outer_test(ls.ek, ls.K, n, mp, out.mask_len + (size_t)sig * mp.max_imfs, L,
-                             iflags, pk.k);
+                             iflags, pk.k, S.ltab);
       sh->ot[1] = L;
       sh->ot[2] = iflags;
       if (out.diag) {
@@ -99,9 +99,10 @@ __device__ void decompose_resident(FusedShared* sh, const MethodParams& mp,
     if (reason) break;
     const int L = sh->ot[1];
     int iflags = sh->ot[2];
-    const int m = select_m(spec, S, L, mp, ls.sc, iflags, red);
-    apply_multiplier(spec, work, S, L, m, mp);
-    inverse_real<E>(work, S, ts);
+    // m, the multiplier pairs of every bin in work, then IMF_hat and the spectral
+    // remainder update applied inside the inverse real transform's split step
+    const int m = select_m_mult(spec, work, S, L, mp, ls.sc, iflags, red);
+    inverse_real_mult<E>(spec, work, S, ts);
     float* orow = out.imfs + sh->d.out_off + (size_t)ls.K * n;
     float imax, ermax;
     int ek, ezc, etie;

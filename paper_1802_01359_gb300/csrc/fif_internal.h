@@ -41,6 +41,9 @@ struct FftSched {
                                // om64[(L-1) * om64_stride + k]; nullptr for the triangle
                                // (closed form from sin64)
   int om64_stride;             // P (plan table, a row per L) or 0 (one row, the current L)
+  const int* ltab;             // [n + 1] or nullptr: ltab[k] = mask_scale * floor((nu * n) / k)
+                               // for k >= 1 (binary64, the mask rule of the outer test), built
+                               // on the host for the plan's nu and mask_scale
 };
 
 // Method parameters as the kernels see them.
@@ -175,6 +178,12 @@ cudaError_t large_set_attrs(const LgSched& G);
 int large_sel_rounds(int max_inner);
 // Kernel launches large_run enqueues for nsig signals of one class.
 int large_launches(int nsig, const MethodParams& mp, bool shape);
+
+// The schedule the staged path uses for length n (at most 512 threads, the
+// folded twiddle table in shared memory): FFT radix passes, E, T, P, Lmax.
+// Host arithmetic only, no allocation.  false if n is not 2^a 3^b in
+// [4, 2^24] or no schedule exists.
+bool staged_schedule(int64_t n, FftSched& s);
 
 // Kernel launchers (fif_fused.cu, fif_staged.cu, fif_tables.cu).
 cudaError_t launch_fused(int E, const SigDesc* d_sigs, int nsig, const FftSched* d_scheds,

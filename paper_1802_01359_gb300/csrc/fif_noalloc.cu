@@ -271,6 +271,7 @@ static bool na_smooth(int64_t n) {
   while (n % 3 == 0) n /= 3;
   return n == 1;
 }
+static_assert(kScratchBytes == FIF_NOALLOC_SCRATCH_BYTES, "the documented size of the scratch array");
 
 extern "C" fif_status fif_decompose_noalloc(const fif_plan_desc* d, const float* signal, int64_t n,
                                             float* imfs, int32_t* m, int32_t* mask_len,
@@ -292,45 +293,10 @@ extern "C" fif_status fif_decompose_noalloc(const fif_plan_desc* d, const float*
   if (n < 4) return FIF_EINVAL;
   if (n > kNoAllocMaxN || !na_smooth(n)) return FIF_EUNSUPPORTED;
 
-  // schedule (host arithmetic only, nothing allocated)
+  // schedule: the staged path's own (host arithmetic only, nothing allocated)
   FftSched s;
-  memset(&s, 0, sizeof(s));
-  s.n = (int)n;
-  s.odd = (int)(n & 1);
-  s.Nc = s.odd ? s.n : s.n / 2;
-  s.P = s.odd ? (s.n + 1) / 2 : s.n / 2 + 1;
-  s.Lmax = (s.n + 1) / 2;
-  s.tw_fold = n % 8 == 0 ? 3 : n % 4 == 0 ? 2 : n % 2 == 0 ? 1 : 0;
-  s.tw_entries = s.tw_fold == 0 ? s.n : (s.n >> s.tw_fold) + 1;
+  if (!staged_schedule(n, s)) return FIF_EUNSUPPORTED;
   s.tw_shared = 1;
-  {
-    int p = 0, q = 0, r = s.Nc;
-    while (r % 2 == 0) r /= 2, p++;
-    while (r % 3 == 0) r /= 3, q++;
-    static const int prefs[] = {16, 24, 12, 18, 9, 27, 8, 6, 4, 3, 2};
-    bool ok = false;
-    for (int E : prefs) {
-      if (s.Nc % E || (q > 0 && E % 3) || (p > 0 && E % 2) || s.Nc / E > 512) continue;
-      s.E = E;
-      s.T = s.Nc / E;
-      s.npass = 0;
-      for (int i = 0; i < q; i++) s.radix[s.npass++] = 3;
-      int rem2 = 1 << p;
-      while (rem2 > 1) {
-        int R = 2;
-        for (int c : {16, 8, 4})
-          if (E % c == 0 && rem2 % c == 0) {
-            R = c;
-            break;
-          }
-        s.radix[s.npass++] = R;
-        rem2 /= R;
-      }
-      ok = true;
-      break;
-    }
-    if (!ok) return FIF_EUNSUPPORTED;
-  }
 
   cudaGetLastError();  // a pending error of earlier, unrelated work is not this call's
   void* base = nullptr;
