@@ -71,7 +71,20 @@ typedef enum {
 } fif_window;
 
 typedef enum {
-  FIF_PREC_FP32 = 0      /* FP32 FFTs and multiplier; m chosen with an FP32 screen + FP64 tie-break */
+  FIF_PREC_FP32 = 0,      /* FP32 FFTs and multiplier; m chosen with an FP32 screen + FP64 tie-break */
+  FIF_PREC_SPLIT_BF16 = 1 /* as FIF_PREC_FP32, but the radix-16 passes of the fused path's inverse
+                             FFT (powers of two 32 <= n <= fif_fused_max_n(), which take an
+                             E = 16 schedule) run on the tensor cores: each 16-point DFT as a
+                             real 32 x 32 matrix product (warp-level mma, BF16 operands, FP32
+                             accumulation; no reference in the paper, which uses plain FFTs,
+                             Sec. 4) with both the DFT
+                             matrix and the data split into BF16 hi + lo and three products
+                             (hi*hi + hi*lo + lo*hi), good to a few times 2^-18 relative per pass
+                             instead of FP32's 2^-24.  The forward transform, m selection, window
+                             spectrum and epilogue are those of FIF_PREC_FP32.  Other lengths
+                             (a factor 3, or n < 32), the staged path
+                             (fif_decompose), the multi-pass path (n above fif_fused_max_n) and
+                             fif_decompose_noalloc run FP32.  fif_plan_tune keeps the schedule. */
 } fif_precision;
 
 /* ---- per-signal status word (sig_status): low byte = stop reason ---- */
@@ -119,7 +132,7 @@ typedef struct {
   double delta;             /* stopping threshold of eq. SD, > 0 */
   int32_t max_inner;        /* cap on m (number of inner iterations), 1 .. 1<<20 */
   int32_t max_imfs;         /* cap on the number of IMFs (remainder not counted), 0 .. 64 */
-  fif_precision precision;  /* FIF_PREC_FP32 */
+  fif_precision precision;  /* FIF_PREC_FP32 or FIF_PREC_SPLIT_BF16 */
   int64_t max_n;            /* largest signal length this plan accepts */
   int32_t flags;            /* 0 or FIF_FORCE_L | FIF_FORCE_MULTIPASS | FIF_APRIORI_N0 |
                                FIF_PEAK_MASK */

@@ -25,6 +25,7 @@ struct LengthTables {
   double* sin64 = nullptr;
   double* om64 = nullptr;  // shape window only
   int* ltab = nullptr;     // mask length per extrema count (FftSched::ltab)
+  std::map<std::vector<int>, float2*> ptw;  // per-pass twiddles per fused radix sequence
 };
 
 struct BatchLayout {
@@ -42,6 +43,7 @@ struct BatchLayout {
   // classes: contiguous ranges of the sorted signal list sharing one length
   struct Cls {
     int first, count, smem, threads, grid, E, n;
+    bool tc;  // split-BF16 tensor-core radix-16 passes (E = 16)
   };
   std::vector<Cls> classes;
   SigDesc* d_sigs = nullptr;
@@ -199,6 +201,12 @@ bool make_fft_plan(int Nc, FftSched& s, bool wide = false) {
 // one, else the wide default, else the length's own plan.
 bool fused_plan(const fif_plan_s* p, const FftSched& base, FftSched& out) {
   out = base;
+  // the split-BF16 variant runs its radix-16 passes on the tensor cores: E = 16
+  // wherever the length has such a schedule (else the FP32 schedule below)
+  if (p->desc.precision == FIF_PREC_SPLIT_BF16 &&
+      plan_with_E(base.Nc, 16, fused_max_threads(16), out, true))
+    return true;
+  out = base;
   auto it = p->fused_E.find(base.n);
   if (it != p->fused_E.end() &&
       plan_with_E(base.Nc, it->second, fused_max_threads(it->second), out, true))
@@ -347,7 +355,7 @@ fif_status validate_desc(const fif_plan_desc* d) {
     if (!shape_valid(d->window_shape, d->window_shape_len)) return FIF_EINVAL;
     if (d->flags & FIF_APRIORI_N0) return FIF_EUNSUPPORTED;
   }
-  if (d->precision != FIF_PREC_FP32) return FIF_EUNSUPPORTED;
+  if (d->precision != FIF_PREC_FP32 && d->precision != FIF_PREC_SPLIT_BF16) return FIF_EINVAL;
   if (!(d->delta > 0.0) || !isfinite(d->delta)) return FIF_EINVAL;
   if (d->max_inner < 1 || d->max_inner > (1 << 20)) return FIF_EINVAL;
   if (d->max_imfs < 0 || d->max_imfs > kMaxImfs) return FIF_EINVAL;
@@ -383,9 +391,28 @@ fif_status prepare_layout(fif_plan_t p, const int64_t* offsets, const int64_t* o
     LengthTables* t = nullptr;
     fif_status st = get_tables(p, n, &t);
     if (st != FIF_OK) return st;
-    // the fused kernel's own FFT plan over the length's tables
+    // the fused kernel's own FFT plan over the length's tables, with its per-pass
+    // twiddle table (global memory, read through L1) in place of the folded
+    // shared-memory table
     FftSched fs = t->sched;
     fused_plan(p, t->sched, fs);
+    {
+      std::vector<int> key(fs.radix, fs.radix + fs.npass);
+      auto it = t->ptw.find(key);
+      if (it == t->ptw.end()) {
+        float2* d = nullptr;
+        cudaError_t e = cudaMalloc(&d, sizeof(float2) * (size_t)std::max(fs.Nc - 1, 1));
+        if (e == cudaSuccess) e = build_pass_twiddles(fs, d, p->stream);
+        if (e != cudaSuccess) {
+          cudaFree(d);
+          cudaGetLastError();
+          return cuda_status(e);
+        }
+        it = t->ptw.emplace(key, d).first;
+      }
+      fs.ptw = it->second;
+      fs.tw_shared = 0;
+    }
     if (!sched_idx.count(n)) {
       sched_idx[n] = (int)scheds.size();
       scheds.push_back(fs);
@@ -394,12 +421,15 @@ fif_status prepare_layout(fif_plan_t p, const int64_t* offsets, const int64_t* o
     if (r == 0 || sigs[(size_t)r - 1].n != (int)n) {
       const int smem = (int)fused_smem_bytes(fs);
       const int threads = sched_threads(fs);
-      l.classes.push_back(BatchLayout::Cls{(int)r, 0, smem, threads, 0, fs.E, (int)n});
+      bool tc = false;
+      if (p->desc.precision == FIF_PREC_SPLIT_BF16 && fs.E == 16)
+        for (int q = 0; q < fs.npass; q++) tc |= fs.radix[q] == 16;
+      l.classes.push_back(BatchLayout::Cls{(int)r, 0, smem, threads, 0, fs.E, (int)n, tc});
     }
     l.classes.back().count++;
   }
   for (auto& c : l.classes) {
-    const int occ = fused_blocks_per_sm(c.E, c.smem, c.threads);
+    const int occ = fused_blocks_per_sm(c.E, c.smem, c.threads, c.tc);
     if (occ <= 0) return FIF_EUNSUPPORTED;
     c.grid = std::min(c.count, occ * p->num_sms);
   }
@@ -717,7 +747,7 @@ fif_status enqueue_batch(fif_plan_t p, const float* signals, const Outputs& o) {
     if (jb.cls < nf) {
       const auto& cl = l.classes[jb.cls];
       e = launch_fused(cl.E, l.d_sigs + cl.first, cl.count, l.d_scheds, cl.smem, cl.threads,
-                       cl.grid, p->mp, signals, o, l.d_counters + jb.cls, s);
+                       cl.grid, p->mp, signals, o, l.d_counters + jb.cls, s, cl.tc);
     } else {
       const auto& lc = l.lcls[jb.cls - nf];
       e = cudaMemsetAsync(lc.b->st, 0, sizeof(int) * kLgStateWords * (size_t)lc.count, s);
@@ -873,6 +903,7 @@ fif_status fif_plan_destroy(fif_plan_t p) {
     cudaFree(kv.second.sin64);
     cudaFree(kv.second.om64);
     cudaFree(kv.second.ltab);
+    for (auto& pw : kv.second.ptw) cudaFree(pw.second);
   }
   cudaFree(p->d_shape);
   free_layout(p->layout);
@@ -1121,6 +1152,11 @@ fif_status fif_plan_tune(fif_plan_t p, const float* signals, const int64_t* offs
   if (cudaStreamIsCapturing(p->stream, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone)
     return FIF_EINVAL;
   cudaGetLastError();
+  // the split-BF16 variant's schedule is fixed (E = 16, radix-16 passes on the
+  // tensor cores): nothing to tune, a plain batch call
+  if (p->desc.precision == FIF_PREC_SPLIT_BF16)
+    return fif_decompose_batch(p, signals, offsets, batch, imfs, out_offsets, m, mask_len, n_imfs,
+                               sig_status, nullptr);
   std::vector<int> fused;
   std::map<int64_t, std::vector<FftSched>> cands;
   for (int64_t i = 0; i < batch; i++) {
@@ -1160,7 +1196,7 @@ fif_status fif_plan_tune(fif_plan_t p, const float* signals, const int64_t* offs
         e = cudaEventRecord(e0, p->stream);
         if (e == cudaSuccess)
           e = launch_fused(cl.E, l.d_sigs + cl.first, cl.count, l.d_scheds, cl.smem, cl.threads,
-                           cl.grid, p->mp, signals, o, l.d_counters + c, p->stream);
+                           cl.grid, p->mp, signals, o, l.d_counters + c, p->stream, cl.tc);
         if (e == cudaSuccess) e = cudaEventRecord(e1, p->stream);
         if (e == cudaSuccess) e = cudaEventSynchronize(e1);
         float ms = 0.f;

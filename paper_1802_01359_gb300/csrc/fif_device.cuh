@@ -233,6 +233,7 @@ struct TwSrc {
   const float2* g;   // global table exp(-2 pi i t/n)
   int n;
   int fold;
+  const float2* p;   // or the schedule's per-pass table (FftSched::ptw; inverse direction)
 };
 
 // exp(-2 pi i t/n), 0 <= t < n
@@ -300,6 +301,19 @@ __device__ __forceinline__ void apply_twiddles(float2* v, const TwSrc& ts, int b
   v[15] = cmul(v[15], cmul(w8, w7));
 }
 
+// Multiply v[1..R-1] by the pass's twiddles w^(r k) read from its per-pass
+// table: base = table + (Ns - 1) + k, entry r at base[(r - 1) Ns] (each one
+// rounded from binary64; the table holds the inverse direction).
+template <bool INV, int R>
+__device__ __forceinline__ void apply_pass_twiddles(float2* v, const float2* __restrict__ base,
+                                                    int Ns) {
+  float2 w[R - 1];
+#pragma unroll
+  for (int r = 1; r < R; r++) w[r - 1] = __ldg(base + (r - 1) * Ns);
+#pragma unroll
+  for (int r = 1; r < R; r++) v[r] = cmul(v[r], INV ? w[r - 1] : cconj(w[r - 1]));
+}
+
 template <bool INV, int R>
 __device__ __forceinline__ void apply_twiddles(ffc* v, const FftSched& S, int b) {
 #pragma unroll
@@ -344,7 +358,16 @@ __device__ __forceinline__ void fft_pass(Cx* buf, const FftSched& S,
     for (int t = 0; t < NB; t++) {
       const int j = tid + t * T;
       const int k = j % Ns;
-      if (k != 0) apply_twiddles<INV, R>(&v[t * R], tws, k * twstep);
+      if constexpr (sizeof(Cx) == sizeof(float2)) {
+        if (k != 0) {
+          if (tws.p)
+            apply_pass_twiddles<INV, R>(&v[t * R], tws.p + (Ns - 1) + k, Ns);
+          else
+            apply_twiddles<INV, R>(&v[t * R], tws, k * twstep);
+        }
+      } else {
+        if (k != 0) apply_twiddles<INV, R>(&v[t * R], tws, k * twstep);
+      }
       butterfly<Cx, INV, R>(&v[t * R]);
       const int base = (j - k) * R + k;
 #pragma unroll
@@ -559,8 +582,8 @@ __device__ void inverse_real(float2* work, const FftSched& S, const TwSrc& ts) {
 // (k, Nc - k) that the inverse real split combines, so the multiplier needs
 // no pass of its own; then the complex inverse FFT.  Afterwards the time
 // sample t is work[t/2].x or .y (even n) or work[t].x (odd n), times n.
-template <int E>
-__device__ void inverse_real_mult(float2* spec, float2* work, const FftSched& S, const TwSrc& ts) {
+__device__ __forceinline__ void inverse_real_mult_split(float2* spec, float2* work, const FftSched& S,
+                                                        const TwSrc& ts) {
   const int tid = threadIdx.x, nt = blockDim.x;
   if (!S.odd) {
     const int Nc = S.Nc;
@@ -592,6 +615,11 @@ __device__ void inverse_real_mult(float2* spec, float2* work, const FftSched& S,
     }
   }
   __syncthreads();
+}
+
+template <int E>
+__device__ void inverse_real_mult(float2* spec, float2* work, const FftSched& S, const TwSrc& ts) {
+  inverse_real_mult_split(spec, work, S, ts);
   fft_inplace<float2, true, E>(work, S, ts);
 }
 

@@ -3,6 +3,7 @@
 // memory; CTAs pull signals from a global counter until the batch is done.
 // HBM sees one read of the input and one write per IMF row and remainder.
 #include "fif_device.cuh"
+#include "fif_tc.cuh"
 
 namespace fif {
 
@@ -31,8 +32,9 @@ struct FusedShared {
 static_assert(sizeof(FusedShared) + 16 <= kFusedHeader, "the fused kernel's shared header");
 
 // One signal, Algorithm 2's outer loop with the inner loop replaced by the
-// spectral multiplier (Theorem 5, eq. One step_algo).
-template <int E>
+// spectral multiplier (Theorem 5, eq. One step_algo).  TC: the inverse FFT's
+// radix-16 passes run as split-BF16 tensor-core products (fif_tc.cuh; E = 16).
+template <int E, bool TC>
 __device__ void decompose_resident(FusedShared* sh, const MethodParams& mp,
                                    const float* __restrict__ signals, const Outputs& out,
                                    float2* spec, float2* work, float* rem, ffc* zf, float2* smtw) {
@@ -47,7 +49,7 @@ __device__ void decompose_resident(FusedShared* sh, const MethodParams& mp,
       smtw[tw_slot(u)] = make_float2(w.x, -w.y);
     }
   }
-  const TwSrc ts{smtw, S.tw, n, S.tw_fold};
+  const TwSrc ts{smtw, S.tw, n, S.tw_fold, S.ptw};
   {
     const float* x = signals + sh->d.in_off;
     const float smax = forward_real<E>(x, rem, zf, spec, S, red);
@@ -102,7 +104,10 @@ __device__ void decompose_resident(FusedShared* sh, const MethodParams& mp,
     // m, the multiplier pairs of every bin in work, then IMF_hat and the spectral
     // remainder update applied inside the inverse real transform's split step
     const int m = select_m_mult(spec, work, S, L, mp, ls.sc, iflags, red);
-    inverse_real_mult<E>(spec, work, S, ts);
+    if constexpr (TC)
+      inverse_real_mult_tc(spec, work, S, ts);
+    else
+      inverse_real_mult<E>(spec, work, S, ts);
     float* orow = out.imfs + sh->d.out_off + (size_t)ls.K * n;
     float imax, ermax;
     int ek, ezc, etie;
@@ -140,7 +145,7 @@ __device__ void decompose_resident(FusedShared* sh, const MethodParams& mp,
   }
 }
 
-template <int E>
+template <int E, bool TC>
 __global__ void __launch_bounds__(E <= kWideMaxE ? 1024 : 512, 1) fused_kernel(const SigDesc* __restrict__ sigs, int nsig,
                                                     const FftSched* __restrict__ scheds,
                                                     MethodParams mp,
@@ -165,26 +170,27 @@ __global__ void __launch_bounds__(E <= kWideMaxE ? 1024 : 512, 1) fused_kernel(c
     float2* spec = work + work_points(S);
     ffc* zf = reinterpret_cast<ffc*>(dyn);
     float2* smtw = S.tw_shared ? spec + S.P : nullptr;
-    decompose_resident<E>(sh, mp, signals, out, spec, work, rem, zf, smtw);
+    decompose_resident<E, TC>(sh, mp, signals, out, spec, work, rem, zf, smtw);
     __syncthreads();
   }
 }
 
 #define FIF_E_LIST(X) X(2) X(3) X(4) X(6) X(8) X(9) X(12) X(16) X(18) X(24) X(27)
 
-static const void* fused_entry(int E) {
+static const void* fused_entry(int E, bool tc) {
+  if (tc) return E == 16 ? (const void*)fused_kernel<16, true> : nullptr;
   switch (E) {
 #define FIF_CASE(e) \
   case e:           \
-    return (const void*)fused_kernel<e>;
+    return (const void*)fused_kernel<e, false>;
     FIF_E_LIST(FIF_CASE)
 #undef FIF_CASE
   }
   return nullptr;
 }
 
-int fused_blocks_per_sm(int E, int smem_bytes, int threads) {
-  const void* fn = fused_entry(E);
+int fused_blocks_per_sm(int E, int smem_bytes, int threads, bool tc) {
+  const void* fn = fused_entry(E, tc);
   if (!fn) return 0;
   int dev = 0, maxsm = 0;
   cudaGetDevice(&dev);
@@ -200,14 +206,20 @@ int fused_blocks_per_sm(int E, int smem_bytes, int threads) {
 cudaError_t launch_fused(int E, const SigDesc* d_sigs, int nsig, const FftSched* d_scheds,
                          int smem_bytes, int threads, int grid, const MethodParams& mp,
                          const float* signals, const Outputs& out, int* d_counter,
-                         cudaStream_t st) {
+                         cudaStream_t st, bool tc) {
   cudaError_t e = cudaMemsetAsync(d_counter, 0, sizeof(int), st);
   if (e != cudaSuccess) return e;
+  if (tc) {
+    if (E != 16) return cudaErrorInvalidValue;
+    fused_kernel<16, true><<<grid, threads, smem_bytes, st>>>(d_sigs, nsig, d_scheds, mp, signals,
+                                                              out, d_counter);
+    return cudaGetLastError();
+  }
   switch (E) {
-#define FIF_CASE(ee)                                                                     \
-  case ee:                                                                               \
-    fused_kernel<ee><<<grid, threads, smem_bytes, st>>>(d_sigs, nsig, d_scheds, mp, signals, \
-                                                        out, d_counter);                 \
+#define FIF_CASE(ee)                                                                            \
+  case ee:                                                                                      \
+    fused_kernel<ee, false><<<grid, threads, smem_bytes, st>>>(d_sigs, nsig, d_scheds, mp,      \
+                                                               signals, out, d_counter);        \
     break;
     FIF_E_LIST(FIF_CASE)
 #undef FIF_CASE

@@ -41,6 +41,8 @@ struct FftSched {
                                // om64[(L-1) * om64_stride + k]; nullptr for the triangle
                                // (closed form from sin64)
   int om64_stride;             // P (plan table, a row per L) or 0 (one row, the current L)
+  const float2* ptw;           // [Nc - 1] or nullptr: the inverse FFT's per-pass twiddles for
+                               // this schedule (build_pass_twiddles); nullptr: the folded table
   const int* ltab;             // [n + 1] or nullptr: ltab[k] = mask_scale * floor((nu * n) / k)
                                // for k >= 1 (binary64, the mask rule of the outer test), built
                                // on the host for the plan's nu and mask_scale
@@ -186,11 +188,12 @@ int large_launches(int nsig, const MethodParams& mp, bool shape);
 bool staged_schedule(int64_t n, FftSched& s);
 
 // Kernel launchers (fif_fused.cu, fif_staged.cu, fif_tables.cu).
+// tc: the split-BF16 tensor-core variant of the inverse FFT (E = 16 only).
 cudaError_t launch_fused(int E, const SigDesc* d_sigs, int nsig, const FftSched* d_scheds,
                          int smem_bytes, int threads, int grid, const MethodParams& mp,
                          const float* signals, const Outputs& out, int* d_counter,
-                         cudaStream_t st);
-int fused_blocks_per_sm(int E, int smem_bytes, int threads);
+                         cudaStream_t st, bool tc = false);
+int fused_blocks_per_sm(int E, int smem_bytes, int threads, bool tc = false);
 
 struct StagedScratch {
   float2* spec;   // [P]
@@ -202,6 +205,14 @@ cudaError_t launch_staged(const FftSched& s, const FftSched* d_sched, const Meth
                           const float* signal, const Outputs& out, const StagedScratch& scr,
                           cudaStream_t st);
 
+// The radices of a schedule, passed by value to the table kernel.
+struct PassRadix {
+  int r[kMaxPass];
+};
+// Per-pass twiddles of schedule s for its inverse FFT (s.tw must be built):
+// ptw[(Ns - 1) + (r - 1) Ns + k] = exp(+2 pi i r k/(Ns R)) for the pass of
+// radix R after Ns points, Nc - 1 entries in all.
+cudaError_t build_pass_twiddles(const FftSched& s, float2* ptw, cudaStream_t st);
 cudaError_t build_tables(int n, int P, int Lmax, float2* tw, float2* tw_lo, float2* wtab,
                          double* sin64, cudaStream_t st);
 cudaError_t build_twiddles(int n, float2* tw, float2* tw_lo, double* sin64, cudaStream_t st);

@@ -69,3 +69,41 @@ cudaError_t build_twiddles(int n, float2* tw, float2* tw_lo, double* sin64, cuda
 }
 
 }  // namespace fif
+
+namespace fif {
+
+// Per-pass twiddles of an FFT schedule (the inverse direction), gathered from
+// the binary64-rounded table tw[t] = exp(-2 pi i t/n): for the pass with
+// radix R over sub-transforms of Ns points (Ns = product of the earlier
+// radices), entry (Ns - 1) + (r - 1) Ns + k, 1 <= r < R, 0 <= k < Ns, holds
+// exp(+2 pi i r k / (Ns R)) = conj tw[r k n / (Ns R)].  The passes' blocks tile
+// [0, Nc - 1) (sum over passes of Ns (R - 1) = Nc - 1), each r-major so that a
+// warp's consecutive k read consecutive entries.
+__global__ void pass_twiddle_kernel(float2* ptw, const float2* __restrict__ tw, int n, int Nc,
+                                    int npass, PassRadix pr) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= Nc - 1) return;
+  int Ns = 1;
+  for (int p = 0; p < npass; p++) {
+    const int R = pr.r[p];
+    const int base = Ns - 1, span = Ns * (R - 1);
+    if (idx >= base && idx < base + span) {
+      const int o = idx - base, r = o / Ns + 1, k = o % Ns;
+      const long long t = (long long)r * k * (n / (Ns * R));
+      const float2 w = tw[t];
+      ptw[idx] = make_float2(w.x, -w.y);
+      return;
+    }
+    Ns *= R;
+  }
+}
+
+cudaError_t build_pass_twiddles(const FftSched& s, float2* ptw, cudaStream_t st) {
+  PassRadix pr;
+  for (int p = 0; p < kMaxPass; p++) pr.r[p] = p < s.npass ? s.radix[p] : 1;
+  if (s.Nc < 2) return cudaSuccess;
+  pass_twiddle_kernel<<<(s.Nc + 254) / 256, 256, 0, st>>>(ptw, s.tw, s.n, s.Nc, s.npass, pr);
+  return cudaGetLastError();
+}
+
+}  // namespace fif

@@ -39,6 +39,8 @@ APRIORI_N0 = 4
 PEAK_MASK = 8
 WIN_TRIANGLE = 0
 WIN_SHAPE = 1
+PREC_FP32 = 0
+PREC_SPLIT_BF16 = 1
 
 # every symbol include/fif.h declares
 EXPORTS = ("fif_plan_create", "fif_plan_destroy", "fif_plan_set_stream", "fif_plan_prepare",
@@ -188,15 +190,17 @@ class Plan:
     def __init__(self, *, nu: float = 1.6, mask_scale: int = 1, delta: float = 1e-3,
                  max_inner: int = 200, max_imfs: int = 10, max_n: int = 16384,
                  force_L: bool = False, multipass: bool = False, apriori_n0: bool = False,
-                 gamma: float = 0.0, peak_mask: bool = False, window_shape=None, stream=None):
+                 gamma: float = 0.0, peak_mask: bool = False, window_shape=None, stream=None,
+                 precision: int = 0):
         """window_shape: None for the triangle, else the samples of the generating
-        shape g on [0, 1] (FIF_WIN_SHAPE; copied by the plan)."""
+        shape g on [0, 1] (FIF_WIN_SHAPE; copied by the plan).  precision: PREC_FP32 or
+        PREC_SPLIT_BF16 (tensor-core radix-16 passes of the fused inverse FFT)."""
         import torch
         lib = load_library()
         self.max_imfs = max_imfs
         self.max_n = max_n
         self.force_L = force_L
-        self.desc = PlanDesc(0, nu, mask_scale, delta, max_inner, max_imfs, 0, max_n,
+        self.desc = PlanDesc(0, nu, mask_scale, delta, max_inner, max_imfs, int(precision), max_n,
                              (FORCE_L if force_L else 0) | (FORCE_MULTIPASS if multipass else 0)
                              | (APRIORI_N0 if apriori_n0 else 0) | (PEAK_MASK if peak_mask else 0),
                              float(gamma))

@@ -110,10 +110,12 @@ def test_shape_window_not_on_the_noalloc_path(lib):
     assert rc == fif.FIF_EUNSUPPORTED
 
 
-def test_split_bf16_precision_not_implemented(lib):
+def test_unknown_precision_rejected(lib):
+    """FIF_PREC_FP32 (0) and FIF_PREC_SPLIT_BF16 (1) are the precisions; another value is
+    refused before any CUDA call."""
     h = ctypes.c_void_p()
-    assert lib.fif_plan_create(ctypes.byref(h), ctypes.byref(_desc(precision=1)), None) == \
-        fif.FIF_EUNSUPPORTED
+    assert lib.fif_plan_create(ctypes.byref(h), ctypes.byref(_desc(precision=2)), None) == \
+        fif.FIF_EINVAL
 
 
 def test_binding_fails_loudly_without_library(tmp_path):
