@@ -46,6 +46,9 @@ WORKLOADS = {
                            "N(0,0.01^2) noise; triangle window, nu=1.6, delta=1e-3, max_inner=200, "
                            "max_imfs=12"),
     "batch4096_d1e-4": dict(desc="65536 float32 signals, n=4096, as batch4096 with delta=1e-4"),
+    "batch4096_bf16": dict(desc="the batch4096 signals with the split-BF16 tensor-core variant "
+                                "(FIF_PREC_SPLIT_BF16: radix-16 inverse-FFT passes as BF16 hi+lo "
+                                "mma products, FP32 accumulation); delta=1e-3, max_imfs=12"),
     "batch16384": dict(desc="1024 float32 signals, n=16384, 2-5 chirped AM components + "
                             "N(0,0.01^2) noise; triangle window, nu=1.6, delta=1e-3, "
                             "max_inner=200, max_imfs=10"),
@@ -105,6 +108,7 @@ def generate(wid, lens, first=0):
 # uniform batches: workload -> (seed stream, signals per rank, n); rank r decomposes signals
 # r*count .. r*count+count-1 of the stream (weak scaling, disjoint batches)
 UNIFORM = {"batch4096": ("W_BATCH_4096", 65536, 4096), "batch4096_d1e-4": ("W_BATCH_4096", 65536, 4096),
+           "batch4096_bf16": ("W_BATCH_4096", 65536, 4096),
            "batch16384": ("W_BATCH_16384", 1024, 16384), "batch16384_n0": ("W_BATCH_16384", 1024, 16384),
            "batch16384_th": ("W_BATCH_16384", 1024, 16384), "batch16384_pk": ("W_BATCH_16384", 1024, 16384),
            "batch16384_sh": ("W_BATCH_16384", 1024, 16384)}
@@ -142,12 +146,14 @@ def make_workload(name, rank=0):
     elif name == "long":
         s = signals.long_signal()
         data, offs = s, np.array([0, s.size], dtype=np.int64)
-    elif name in ("batch4096", "batch4096_d1e-4"):
+    elif name in ("batch4096", "batch4096_d1e-4", "batch4096_bf16"):
         data, offs = generate(signals.W_BATCH_4096, np.full(65536, 4096),
                               first=first_signal(name, rank))
         params["max_imfs"] = 12
         if name == "batch4096_d1e-4":
             params["delta"] = 1e-4
+        if name == "batch4096_bf16":
+            params["precision"] = 1  # FIF_PREC_SPLIT_BF16
     else:
         raise SystemExit(f"unknown workload {name}")
     return data, offs, params
@@ -267,6 +273,7 @@ def oracle_sample(data, offs, idx, threads, params=None):
     oracle.build()
 
     prm = dict(params or PARAMS)
+    prm.pop("precision", None)  # the oracle is binary64 throughout
     if prm.pop("apriori_n0", False):
         prm["apriori"] = True
     if "window_shape" in prm:
@@ -451,13 +458,20 @@ def main():
         stream.synchronize()
         tune_s = time.perf_counter() - t0
 
-    chosen = []  # fused schedule of the first few lengths
-    for n in sorted(set(int(v) for v in lens))[:4]:
+    chosen = []  # fused schedule of the first few lengths, multi-pass of the largest
+    ulens = sorted(set(int(v) for v in lens))
+    for n in ulens[:4]:
         try:
             E, T, _ = plan.schedule(n)
             chosen.append(f"n={n}: E={E}, {T} threads")
         except fif.FifError:
             pass
+    for n in ulens[-3:]:
+        if n <= fif.fused_max_n():
+            continue
+        ms = plan.multipass_schedule(n)
+        chosen.append(f"n={n}: {ms['R1']}x{ms['R2']}, level 1 E={ms['E1']} TJ={ms['TJ1']}, "
+                      f"level 2 E={ms['E2']} TJ={ms['TJ2']}{' (tuned)' if ms['tuned'] else ''}")
 
     def step():
         plan.decompose_batch(x, offs, out=out)
@@ -501,7 +515,8 @@ def main():
     result = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * t_total / args.steps,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32" if not params.get("precision") else "f32 (radix-16 inverse stages: bf16 hi+lo products, f32 accumulation)",
         "data": "synthetic",
         "config": {"workload": desc, "name": args.workload, "signals": nsig,
                    "samples": int(offs[-1]),

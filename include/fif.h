@@ -239,15 +239,22 @@ fif_status fif_decompose_batch_host(fif_plan_t plan, const float* signals, const
 /* ---- schedule autotuning per length class ---------------------------------
  * The fused kernel's FFT schedule (elements per thread E, hence E-point
  * register butterflies and Nc/E threads per CTA) has one to four valid
- * choices per length; the library picks one by a fixed rule unless the plan
- * has been tuned.
+ * choices per length; the multi-pass path's two FP32 inverse levels (the
+ * transform of Nc = R1 R2 points as R2 sub-FFTs of R1 points, then R1 of R2)
+ * each have a sub-FFT schedule E and a count TJ of sub-FFTs per CTA.  The
+ * library picks them by fixed rules unless the plan has been tuned.
  *
  * fif_plan_tune runs the batch (same arguments and outputs as
  * fif_decompose_batch) once per candidate schedule of every fused length
  * class in it, times each class's launch with CUDA events after a warm-up,
- * and keeps the fastest schedule per length in the plan; later calls use it.
- * Results of the last run are left in the outputs (a valid decomposition).
- * Blocking; not allowed during stream capture (FIF_EINVAL).
+ * and keeps the fastest schedule per length in the plan; then, for every
+ * multi-pass length class, it times whole runs of the class with each
+ * candidate (E in {8, 16, 4, 12, 6, 24}, TJ in {4, 3, 2, 1}, as fits) for the first
+ * inverse level, keeps the fastest, then does the same for the second.
+ * Later calls use the choices.  Results of the last run are left in the
+ * outputs (a valid decomposition).  Under FIF_PREC_SPLIT_BF16 the fused
+ * schedules stay at E = 16 and nothing is tuned.  Blocking; not allowed
+ * during stream capture (FIF_EINVAL).
  * Errors: as fif_decompose_batch. */
 fif_status fif_plan_tune(fif_plan_t plan, const float* signals, const int64_t* offsets,
                          int64_t batch, float* imfs, const int64_t* out_offsets, int32_t* m,
@@ -259,9 +266,21 @@ fif_status fif_plan_tune(fif_plan_t plan, const float* signals, const int64_t* o
 fif_status fif_plan_get_schedule(fif_plan_t plan, int64_t n, int32_t* E, int32_t* threads,
                                  int32_t* tuned);
 
+/* The multi-pass schedule the plan uses for length n: Nc = *R1 * *R2 (n/2
+ * complex points for even n, n for odd n), the first FP32 inverse level's
+ * sub-FFT elements per thread *E1 and sub-FFTs per CTA *TJ1, the second's *E2
+ * and *TJ2; *tuned = 1 if set by tuning or loading.  Builds the length's
+ * multi-pass tables if needed (not during stream capture).
+ * FIF_EUNSUPPORTED if n takes the fused path (and the plan does not force
+ * the multi-pass path) or is not a valid length.  Errors: FIF_EINVAL (NULL). */
+fif_status fif_plan_get_multipass_schedule(fif_plan_t plan, int64_t n, int32_t* R1, int32_t* R2,
+                                           int32_t* E1, int32_t* TJ1, int32_t* E2, int32_t* TJ2,
+                                           int32_t* tuned);
+
 /* Save the plan's tuned schedules to a text file (HOST path; one line
- * "n E" per tuned length), or load them from one (lines for lengths or E the
- * device cannot use are skipped).  Errors: FIF_EINVAL (NULL or unreadable /
+ * "n E" per tuned fused length, "n E1 TJ1 E2 TJ2" per tuned multi-pass
+ * length), or load them from one (lines for lengths or schedules the device
+ * cannot use are skipped).  Errors: FIF_EINVAL (NULL or unreadable /
  * unwritable path, malformed line). */
 fif_status fif_plan_save_tuning(fif_plan_t plan, const char* path);
 fif_status fif_plan_load_tuning(fif_plan_t plan, const char* path);

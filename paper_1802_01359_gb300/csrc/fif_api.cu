@@ -5,6 +5,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <array>
 #include <map>
 #include <vector>
 
@@ -25,6 +26,7 @@ struct LengthTables {
   double* sin64 = nullptr;
   double* om64 = nullptr;  // shape window only
   int* ltab = nullptr;     // mask length per extrema count (FftSched::ltab)
+  float2* gtab = nullptr;  // multipliers of m = max_inner per (L, k) (fused path; built lazily)
   std::map<std::vector<int>, float2*> ptw;  // per-pass twiddles per fused radix sequence
 };
 
@@ -96,6 +98,9 @@ struct fif_plan_s {
   std::map<int64_t, LargeBuffers> large_single_bufs;  // per length, fif_decompose
   // fused schedules chosen by fif_plan_tune / fif_plan_load_tuning: n -> E
   std::map<int64_t, int> fused_E;
+  // multi-pass schedules chosen by fif_plan_tune / fif_plan_load_tuning:
+  // n -> {E1, TJ1, E2, TJ2} of the two FP32 inverse levels
+  std::map<int64_t, std::array<int, 4>> large_sched;
   // FIF_WIN_SHAPE: the shape's samples (host copy, and on the device)
   std::vector<double> shape;
   double* d_shape = nullptr;
@@ -372,22 +377,28 @@ fif_status validate_desc(const fif_plan_desc* d) {
 
 // Sort signals by length (longest first), one class per distinct length, and
 // upload the descriptors.  Reused while the same layout is passed again.
+// merge: classes with the same E and precision share one persistent launch (a
+// single work counter over all their signals, longest first; each signal
+// brings its own schedule), sized for the largest member; a length joins a
+// launch only while its shared memory is at least half the launch's, so a
+// short signal's CTA does not hold the shared memory (and SM slots) of a much
+// longer one.  The tuner times every length on its own (merge = false).
 fif_status prepare_layout(fif_plan_t p, const int64_t* offsets, const int64_t* out_offsets,
-                          int64_t batch, const std::vector<int>& subset) {
+                          int64_t batch, const std::vector<int>& subset, bool merge = true) {
   BatchLayout& l = p->layout;
   free_layout(l);
   p->layout_valid = false;
-  std::vector<int> order(subset);
-  std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
-    return offsets[a + 1] - offsets[a] > offsets[b + 1] - offsets[b];
-  });
-  const int64_t nfused = (int64_t)order.size();
-  std::vector<SigDesc> sigs((size_t)nfused);
+  // per distinct length: its fused schedule (with its per-pass twiddle table)
+  struct LenInfo {
+    FftSched fs;
+    int smem, threads, sched, group;
+    bool tc;
+  };
+  std::map<int64_t, LenInfo> info;
   std::vector<FftSched> scheds;
-  std::map<int64_t, int> sched_idx;
-  for (int64_t r = 0; r < nfused; r++) {
-    const int i = order[(size_t)r];
+  for (int i : subset) {
     const int64_t n = offsets[i + 1] - offsets[i];
+    if (info.count(n)) continue;
     LengthTables* t = nullptr;
     fif_status st = get_tables(p, n, &t);
     if (st != FIF_OK) return st;
@@ -413,18 +424,75 @@ fif_status prepare_layout(fif_plan_t p, const int64_t* offsets, const int64_t* o
       fs.ptw = it->second;
       fs.tw_shared = 0;
     }
-    if (!sched_idx.count(n)) {
-      sched_idx[n] = (int)scheds.size();
-      scheds.push_back(fs);
+    if (!t->gtab) {
+      // the multipliers of m = max_inner per (L, k), read by the inverse split
+      // step directly whenever the search ends at max_inner
+      cudaError_t e = cudaMalloc(&t->gtab, sizeof(float2) * (size_t)fs.Lmax * (size_t)fs.P);
+      if (e == cudaSuccess)
+        e = build_mult_table(fs.n, fs.P, fs.Lmax, p->desc.max_inner, p->desc.gamma, t->om64,
+                             t->gtab, p->stream);
+      if (e != cudaSuccess) {
+        cudaFree(t->gtab);
+        t->gtab = nullptr;
+        cudaGetLastError();
+        return cuda_status(e);
+      }
     }
-    sigs[(size_t)r] = SigDesc{offsets[i], out_offsets[i], sched_idx[n], (int)n, i, 0};
-    if (r == 0 || sigs[(size_t)r - 1].n != (int)n) {
-      const int smem = (int)fused_smem_bytes(fs);
-      const int threads = sched_threads(fs);
-      bool tc = false;
-      if (p->desc.precision == FIF_PREC_SPLIT_BF16 && fs.E == 16)
-        for (int q = 0; q < fs.npass; q++) tc |= fs.radix[q] == 16;
-      l.classes.push_back(BatchLayout::Cls{(int)r, 0, smem, threads, 0, fs.E, (int)n, tc});
+    fs.gtab = t->gtab;
+    LenInfo li;
+    li.fs = fs;
+    li.smem = (int)fused_smem_bytes(fs);
+    li.threads = sched_threads(fs);
+    li.sched = (int)scheds.size();
+    li.tc = false;
+    if (p->desc.precision == FIF_PREC_SPLIT_BF16 && fs.E == 16)
+      for (int q = 0; q < fs.npass; q++) li.tc |= fs.radix[q] == 16;
+    li.group = 0;
+    scheds.push_back(fs);
+    info[n] = li;
+  }
+  // launch groups: lengths longest first; without merging one group per length,
+  // else a length joins the first group of its E and precision whose largest
+  // shared memory is at most twice its own
+  struct Group {
+    int E, smem, threads;
+    bool tc;
+  };
+  std::vector<Group> groups;
+  for (auto it = info.rbegin(); it != info.rend(); ++it) {
+    LenInfo& li = it->second;
+    int gsel = -1;
+    if (merge)
+      for (size_t g = 0; g < groups.size(); g++)
+        if (groups[g].E == li.fs.E && groups[g].tc == li.tc && 2 * li.smem >= groups[g].smem) {
+          gsel = (int)g;
+          break;
+        }
+    if (gsel < 0) {
+      gsel = (int)groups.size();
+      groups.push_back(Group{li.fs.E, li.smem, li.threads, li.tc});
+    }
+    groups[gsel].smem = std::max(groups[gsel].smem, li.smem);
+    groups[gsel].threads = std::max(groups[gsel].threads, li.threads);
+    li.group = gsel;
+  }
+  // signals in group order, longest first inside a group
+  std::vector<int> order(subset);
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+    const int64_t na = offsets[a + 1] - offsets[a], nb = offsets[b + 1] - offsets[b];
+    const int ga = info[na].group, gb = info[nb].group;
+    return ga != gb ? ga < gb : na > nb;
+  });
+  const int64_t nfused = (int64_t)order.size();
+  std::vector<SigDesc> sigs((size_t)nfused);
+  for (int64_t r = 0; r < nfused; r++) {
+    const int i = order[(size_t)r];
+    const int64_t n = offsets[i + 1] - offsets[i];
+    const LenInfo& li = info[n];
+    sigs[(size_t)r] = SigDesc{offsets[i], out_offsets[i], li.sched, (int)n, i, 0};
+    if (r == 0 || info[(int64_t)sigs[(size_t)r - 1].n].group != li.group) {
+      const Group& g = groups[(size_t)li.group];
+      l.classes.push_back(BatchLayout::Cls{(int)r, 0, g.smem, g.threads, 0, g.E, (int)n, g.tc});
     }
     l.classes.back().count++;
   }
@@ -517,6 +585,29 @@ bool make_large_sched(int64_t n64, int smem_limit, LgSched& G) {
   return true;
 }
 
+// One FP32 inverse level's schedule: sub-FFTs of R points with E elements a
+// thread, tj of them per CTA.  false if it does not fit (threads, shared
+// memory, tile count).
+bool set_level(LgSched& G, int level, int E, int tj, int smem_limit) {
+  const int R = level == 1 ? G.R1 : G.R2, count = level == 1 ? G.R2 : G.R1;
+  FftSched sub = level == 1 ? G.S1 : G.S2;
+  if (!plan_with_E(R, E, 512, sub)) return false;
+  if (tj < 1 || count % tj || tj * sub.T > 512) return false;
+  if ((size_t)tj * R * 8 + tw_slots(sub) * sizeof(float2) + 1024 > (size_t)smem_limit) return false;
+  // the float-float forward level keeps its own sub-FFT count, which must
+  // still fit the schedule's threads
+  const int tjf = level == 1 ? G.TJF1 : G.TJF2;
+  if (tjf * sub.T > 512) return false;
+  if (level == 1) {
+    G.S1 = sub;
+    G.TJ1 = tj;
+  } else {
+    G.S2 = sub;
+    G.TJ2 = tj;
+  }
+  return true;
+}
+
 fif_status get_large(fif_plan_t p, int64_t n, LargeTables** out) {
   auto it = p->large.find(n);
   if (it != p->large.end()) {
@@ -577,6 +668,16 @@ fif_status get_large(fif_plan_t p, int64_t n, LargeTables** out) {
   G.sinff = sff;
   G.rcpff = rff;
   if (e == cudaSuccess) e = large_build_tables(G, thi, thil, tlo, tlol, sff, rff, p->stream);
+  {
+    // a tuned (or loaded) schedule of the inverse levels replaces the rule's
+    auto tv = p->large_sched.find(n);
+    if (tv != p->large_sched.end()) {
+      LgSched t = G;
+      if (set_level(t, 1, tv->second[0], tv->second[1], p->smem_optin) &&
+          set_level(t, 2, tv->second[2], tv->second[3], p->smem_optin))
+        G = t;
+    }
+  }
   if (e == cudaSuccess) e = large_set_attrs(G);
   if (e != cudaSuccess) {
     for (void* a : lt.allocs) cudaFree(a);
@@ -903,6 +1004,7 @@ fif_status fif_plan_destroy(fif_plan_t p) {
     cudaFree(kv.second.sin64);
     cudaFree(kv.second.om64);
     cudaFree(kv.second.ltab);
+    cudaFree(kv.second.gtab);
     for (auto& pw : kv.second.ptw) cudaFree(pw.second);
   }
   cudaFree(p->d_shape);
@@ -1184,7 +1286,7 @@ fif_status fif_plan_tune(fif_plan_t p, const float* signals, const int64_t* offs
       p->fused_E[kv.first] = kv.second[std::min(r, kv.second.size() - 1)].E;
     }
     drop_layout(p);
-    st = prepare_layout(p, offsets, out_offsets, batch, fused);
+    st = prepare_layout(p, offsets, out_offsets, batch, fused, false);
     if (st != FIF_OK) break;
     const BatchLayout& l = p->layout;
     for (size_t c = 0; c < l.classes.size() && e == cudaSuccess; c++) {
@@ -1208,9 +1310,59 @@ fif_status fif_plan_tune(fif_plan_t p, const float* signals, const int64_t* offs
         best[cl.n] = std::make_pair(best_ms, cl.E);
     }
   }
+  for (const auto& kv : best) p->fused_E[kv.first] = kv.second.second;
+  // multi-pass classes: the two FP32 inverse levels (the path's main cost, once
+  // per IMF), one level at a time: the sub-FFT schedule (E) and the sub-FFTs a
+  // CTA transforms (TJ), each candidate timed on a whole run of the class
+  std::map<int64_t, std::vector<int>> large;
+  for (int64_t i = 0; i < batch; i++) {
+    const int64_t n = offsets[i + 1] - offsets[i];
+    if (!fits_fused(p, n)) large[n].push_back((int)i);
+  }
+  if (e == cudaSuccess && st == FIF_OK && !large.empty()) {
+    drop_layout(p);
+    st = prepare_large(p, offsets, out_offsets, large);
+    const BatchLayout& l = p->layout;
+    for (size_t c = 0; st == FIF_OK && c < l.lcls.size() && e == cudaSuccess; c++) {
+      const auto& lc = l.lcls[c];
+      LgSched& G = lc.lt->G;
+      auto run_ms = [&](const LgSched& t, float* ms) {
+        cudaError_t r = large_set_attrs(t);
+        float best_ms = 0.f;
+        for (int rep = 0; rep < 2 && r == cudaSuccess; rep++) {  // one warm-up, one timed
+          r = cudaMemsetAsync(lc.b->st, 0, sizeof(int) * kLgStateWords * (size_t)lc.count, p->stream);
+          if (r == cudaSuccess) r = cudaEventRecord(e0, p->stream);
+          if (r == cudaSuccess) r = large_run(t, lc.b->d_sigs, lc.count, p->mp, signals, o, p->stream);
+          if (r == cudaSuccess) r = cudaEventRecord(e1, p->stream);
+          if (r == cudaSuccess) r = cudaEventSynchronize(e1);
+          if (r == cudaSuccess) r = cudaEventElapsedTime(&best_ms, e0, e1);
+        }
+        *ms = best_ms;
+        return r;
+      };
+      for (int level = 1; level <= 2 && e == cudaSuccess; level++) {
+        float best_ms = 0.f;
+        e = run_ms(G, &best_ms);
+        int bE = level == 1 ? G.S1.E : G.S2.E, btj = level == 1 ? G.TJ1 : G.TJ2;
+        for (int E : {8, 16, 4, 12, 6, 24}) {
+          for (int tj : {4, 3, 2, 1}) {
+            if (e != cudaSuccess) break;
+            LgSched t = G;
+            if (!set_level(t, level, E, tj, p->smem_optin)) continue;
+            if ((level == 1 ? t.S1.E : t.S2.E) == bE && (level == 1 ? t.TJ1 : t.TJ2) == btj) continue;
+            float ms = 0.f;
+            e = run_ms(t, &ms);
+            if (e == cudaSuccess && ms < best_ms) best_ms = ms, bE = E, btj = tj;
+          }
+        }
+        if (e == cudaSuccess) set_level(G, level, bE, btj, p->smem_optin);
+      }
+      if (e == cudaSuccess) e = large_set_attrs(G);
+      if (e == cudaSuccess) p->large_sched[lc.n] = {G.S1.E, G.TJ1, G.S2.E, G.TJ2};
+    }
+  }
   if (e0) cudaEventDestroy(e0);
   if (e1) cudaEventDestroy(e1);
-  for (const auto& kv : best) p->fused_E[kv.first] = kv.second.second;
   drop_layout(p);
   if (e != cudaSuccess) {
     cudaGetLastError();
@@ -1247,11 +1399,29 @@ fif_status fif_plan_get_schedule(fif_plan_t p, int64_t n, int32_t* E, int32_t* t
   return FIF_OK;
 }
 
+fif_status fif_plan_get_multipass_schedule(fif_plan_t p, int64_t n, int32_t* R1, int32_t* R2,
+                                           int32_t* E1, int32_t* TJ1, int32_t* E2, int32_t* TJ2,
+                                           int32_t* tuned) {
+  if (!p || !R1 || !R2 || !E1 || !TJ1 || !E2 || !TJ2 || !tuned) return FIF_EINVAL;
+  if (n < 4 || n > p->desc.max_n || !is_smooth(n)) return FIF_EUNSUPPORTED;
+  if (fits_fused(p, n) && !(p->desc.flags & FIF_FORCE_MULTIPASS)) return FIF_EUNSUPPORTED;
+  LargeTables* lt = nullptr;
+  const fif_status st = get_large(p, n, &lt);
+  if (st != FIF_OK) return st;
+  const LgSched& G = lt->G;
+  *R1 = G.R1, *R2 = G.R2, *E1 = G.S1.E, *TJ1 = G.TJ1, *E2 = G.S2.E, *TJ2 = G.TJ2;
+  *tuned = p->large_sched.count(n) ? 1 : 0;
+  return FIF_OK;
+}
+
 fif_status fif_plan_save_tuning(fif_plan_t p, const char* path) {
   if (!p || !path) return FIF_EINVAL;
   FILE* f = fopen(path, "w");
   if (!f) return FIF_EINVAL;
   for (const auto& kv : p->fused_E) fprintf(f, "%lld %d\n", (long long)kv.first, kv.second);
+  for (const auto& kv : p->large_sched)
+    fprintf(f, "%lld %d %d %d %d\n", (long long)kv.first, kv.second[0], kv.second[1], kv.second[2],
+            kv.second[3]);
   return fclose(f) == 0 ? FIF_OK : FIF_EINVAL;
 }
 
@@ -1260,14 +1430,24 @@ fif_status fif_plan_load_tuning(fif_plan_t p, const char* path) {
   FILE* f = fopen(path, "r");
   if (!f) return FIF_EINVAL;
   std::map<int64_t, int> got;
+  std::map<int64_t, std::array<int, 4>> got_large;
   char line[256];
   fif_status st = FIF_OK;
   while (fgets(line, sizeof line, f)) {
     long long n = 0;
-    int E = 0;
+    int E = 0, v[3] = {0, 0, 0};
     char extra = 0;
-    const int k = sscanf(line, " %lld %d %c", &n, &E, &extra);
+    const int k = sscanf(line, " %lld %d %d %d %d %c", &n, &E, &v[0], &v[1], &v[2], &extra);
     if (k == EOF || (k <= 0 && line[strspn(line, " \t\r\n")] == 0)) continue;  // blank
+    if (k == 5) {  // a multi-pass length: E1 TJ1 E2 TJ2 of its inverse levels
+      if (n < 4 || n > p->desc.max_n || !is_smooth(n) || fits_fused(p, n)) continue;
+      LgSched G;
+      if (!make_large_sched(n, p->smem_optin, G)) continue;
+      if (!set_level(G, 1, E, v[0], p->smem_optin) || !set_level(G, 2, v[1], v[2], p->smem_optin))
+        continue;
+      got_large[(int64_t)n] = {E, v[0], v[1], v[2]};
+      continue;
+    }
     if (k != 2) {
       st = FIF_EINVAL;
       break;
@@ -1282,6 +1462,17 @@ fif_status fif_plan_load_tuning(fif_plan_t p, const char* path) {
   fclose(f);
   if (st != FIF_OK) return st;
   for (const auto& kv : got) p->fused_E[kv.first] = kv.second;
+  for (const auto& kv : got_large) {
+    p->large_sched[kv.first] = kv.second;
+    auto it = p->large.find(kv.first);  // tables already built: switch them over now
+    if (it != p->large.end()) {
+      LgSched t = it->second.G;
+      if (set_level(t, 1, kv.second[0], kv.second[1], p->smem_optin) &&
+          set_level(t, 2, kv.second[2], kv.second[3], p->smem_optin) &&
+          large_set_attrs(t) == cudaSuccess)
+        it->second.G = t;
+    }
+  }
   drop_layout(p);
   return FIF_OK;
 }

@@ -582,14 +582,17 @@ __device__ void inverse_real(float2* work, const FftSched& S, const TwSrc& ts) {
 // (k, Nc - k) that the inverse real split combines, so the multiplier needs
 // no pass of its own; then the complex inverse FFT.  Afterwards the time
 // sample t is work[t/2].x or .y (even n) or work[t].x (odd n), times n.
-__device__ __forceinline__ void inverse_real_mult_split(float2* spec, float2* work, const FftSched& S,
+// mult: the multiplier pairs, either work itself (select_m_mult's pass) or a
+// row of the plan's table for m = max_inner (global memory).
+__device__ __forceinline__ void inverse_real_mult_split(float2* spec, float2* work,
+                                                        const float2* mult, const FftSched& S,
                                                         const TwSrc& ts) {
   const int tid = threadIdx.x, nt = blockDim.x;
   if (!S.odd) {
     const int Nc = S.Nc;
     for (int k = tid; k <= Nc / 2; k += nt) {
       const int kc = Nc - k;
-      const float2 gk = work[k], gc = work[kc];
+      const float2 gk = mult[k], gc = mult[kc];
       const float2 zk = spec[k], zc = spec[kc];
       const float2 xk = make_float2(gk.x * zk.x, gk.x * zk.y);
       const float2 xc = make_float2(gc.x * zc.x, gc.x * zc.y);
@@ -607,7 +610,7 @@ __device__ __forceinline__ void inverse_real_mult_split(float2* spec, float2* wo
   } else {
     const int n = S.n;
     for (int k = tid; k < S.P; k += nt) {
-      const float2 gk = work[k], zk = spec[k];
+      const float2 gk = mult[k], zk = spec[k];
       const float2 x = make_float2(gk.x * zk.x, gk.x * zk.y);
       spec[k] = make_float2(gk.y * zk.x, gk.y * zk.y);
       work[k] = x;
@@ -618,8 +621,9 @@ __device__ __forceinline__ void inverse_real_mult_split(float2* spec, float2* wo
 }
 
 template <int E>
-__device__ void inverse_real_mult(float2* spec, float2* work, const FftSched& S, const TwSrc& ts) {
-  inverse_real_mult_split(spec, work, S, ts);
+__device__ void inverse_real_mult(float2* spec, float2* work, const float2* mult, const FftSched& S,
+                                  const TwSrc& ts) {
+  inverse_real_mult_split(spec, work, mult, S, ts);
   fft_inplace<float2, true, E>(work, S, ts);
 }
 
@@ -1135,17 +1139,24 @@ static __device__ void multiplier_pass(float2* mult, const FftSched& S, const fl
   __syncthreads();
 }
 
-// m of eq. SD (or the a-priori bound) as select_m, then the IMF's multiplier
-// pairs of every bin in mult[0..P) for inverse_real_mult.  (Computing the
+// m of eq. SD (or the a-priori bound) as select_m, and where the IMF's
+// multiplier pairs are for inverse_real_mult (src): for m = max_inner, the
+// usual outcome, the plan's table row (S.gtab, binary64-rounded), else a
+// pass that writes them into mult[0..P).  (Computing the
 // pairs inside the first screen pass, speculatively for m = max_inner, was
 // measured slower: the longer loop body spills at 64 registers a thread.)
 static __device__ int select_m_mult(const float2* spec, float2* mult, const FftSched& S, int L,
                                     const MethodParams& mp, float sc, int& flags,
-                                    RedScratch* red) {
+                                    RedScratch* red, const float2*& src) {
   const float2* row = wrow(S, L);
+  const float2* grow = S.gtab ? S.gtab + (size_t)(L - 1) * (size_t)S.P : nullptr;
+  src = mult;
   if (mp.apriori) {
     const int m = apriori_m(spec, S, L, mp, flags, red);
-    multiplier_pass(mult, S, row, L, m, mp);
+    if (grow && m == mp.max_inner)
+      src = grow;
+    else
+      multiplier_pass(mult, S, row, L, m, mp);
     return m;
   }
   MSelState st;
@@ -1167,7 +1178,10 @@ static __device__ int select_m_mult(const float2* spec, float2* mult, const FftS
     }
     m = hi;
   }
-  multiplier_pass(mult, S, row, L, m, mp);
+  if (grow && m == jmax)
+    src = grow;  // the plan's table row: no pass
+  else
+    multiplier_pass(mult, S, row, L, m, mp);
   flags |= st.flags;
   return m;
 }

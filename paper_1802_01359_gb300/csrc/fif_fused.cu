@@ -103,11 +103,12 @@ __device__ void decompose_resident(FusedShared* sh, const MethodParams& mp,
     int iflags = sh->ot[2];
     // m, the multiplier pairs of every bin in work, then IMF_hat and the spectral
     // remainder update applied inside the inverse real transform's split step
-    const int m = select_m_mult(spec, work, S, L, mp, ls.sc, iflags, red);
+    const float2* msrc;
+    const int m = select_m_mult(spec, work, S, L, mp, ls.sc, iflags, red, msrc);
     if constexpr (TC)
-      inverse_real_mult_tc(spec, work, S, ts);
+      inverse_real_mult_tc(spec, work, msrc, S, ts);
     else
-      inverse_real_mult<E>(spec, work, S, ts);
+      inverse_real_mult<E>(spec, work, msrc, S, ts);
     float* orow = out.imfs + sh->d.out_off + (size_t)ls.K * n;
     float imax, ermax;
     int ek, ezc, etie;

@@ -41,6 +41,8 @@ struct FftSched {
                                // om64[(L-1) * om64_stride + k]; nullptr for the triangle
                                // (closed form from sin64)
   int om64_stride;             // P (plan table, a row per L) or 0 (one row, the current L)
+  const float2* gtab;          // [Lmax * P] or nullptr: row L-1 holds {(1 - w_hat_k)^m,
+                               // 1 - (1 - w_hat_k)^m} for m = max_inner (build_mult_table)
   const float2* ptw;           // [Nc - 1] or nullptr: the inverse FFT's per-pass twiddles for
                                // this schedule (build_pass_twiddles); nullptr: the folded table
   const int* ltab;             // [n + 1] or nullptr: ltab[k] = mask_scale * floor((nu * n) / k)
@@ -205,6 +207,11 @@ cudaError_t launch_staged(const FftSched& s, const FftSched* d_sched, const Meth
                           const float* signal, const Outputs& out, const StagedScratch& scr,
                           cudaStream_t st);
 
+// {(1 - w_hat_k)^m, 1 - (1 - w_hat_k)^m} for every L = 1..Lmax and bin k < P in
+// binary64, rounded (bins passing whole under gamma > 0 get {1, 0}); om64:
+// the shape window's rows of 1 - w_hat, or nullptr for the triangle.
+cudaError_t build_mult_table(int n, int P, int Lmax, int m, double gamma, const double* om64,
+                             float2* gtab, cudaStream_t st);
 // The radices of a schedule, passed by value to the table kernel.
 struct PassRadix {
   int r[kMaxPass];

@@ -107,3 +107,52 @@ cudaError_t build_pass_twiddles(const FftSched& s, float2* ptw, cudaStream_t st)
 }
 
 }  // namespace fif
+
+namespace fif {
+
+// Multipliers of the usual m = max_inner for every (L, k):
+//   gtab[(L-1) P + k] = { (1 - w_hat_k)^m, 1 - (1 - w_hat_k)^m },
+// in binary64 ((1-w)^m = pow(1-w, m), the complement -expm1(m log1p(-w)),
+// without cancellation), rounded once.  With gamma > 0 a bin with
+// (1-w)^m >= 1 - gamma passes whole (eq. I_gamma): {1, 0}.  w_hat from the
+// triangle's closed form (om64 == nullptr) or the shape window's binary64
+// rows of 1 - w_hat (om64[(L-1) P + k]).
+__global__ void mult_table_kernel(float2* gtab, const double* __restrict__ om64, int n, int P,
+                                  int Lmax, int m, double gamma) {
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long total = (long long)Lmax * P;
+  if (idx >= total) return;
+  const int L = (int)(idx / P) + 1;
+  const int k = (int)(idx % P);
+  double om;
+  if (om64) {
+    om = om64[idx];
+  } else if (k == 0) {
+    om = 0.0;
+  } else {
+    long long t = ((long long)k * (long long)L) % n;
+    if (t > n - t) t = n - t;
+    const double num = sinpi((double)t / (double)n);
+    const double den = (double)L * sinpi((double)k / (double)n);
+    double w = (num / den) * (num / den);
+    w = w > 1.0 ? 1.0 : (w < 0.0 ? 0.0 : w);
+    om = 1.0 - w;
+  }
+  double g = pow(om, (double)m);
+  double keep = -expm1((double)m * log(om));  // log(0) = -inf: keep = 1
+  if (gamma > 0.0 && g >= 1.0 - gamma) {
+    g = 1.0;
+    keep = 0.0;
+  }
+  gtab[idx] = make_float2((float)g, (float)keep);
+}
+
+cudaError_t build_mult_table(int n, int P, int Lmax, int m, double gamma, const double* om64,
+                             float2* gtab, cudaStream_t st) {
+  const long long total = (long long)Lmax * P;
+  mult_table_kernel<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(gtab, om64, n, P, Lmax, m,
+                                                                     gamma);
+  return cudaGetLastError();
+}
+
+}  // namespace fif

@@ -188,9 +188,9 @@ __device__ __forceinline__ void fft_inplace_tc(float2* buf, const FftSched& S, c
 }
 
 // inverse_real_mult with the tensor-core FFT (E = 16).
-__device__ __forceinline__ void inverse_real_mult_tc(float2* spec, float2* work, const FftSched& S,
-                                                     const TwSrc& ts) {
-  inverse_real_mult_split(spec, work, S, ts);
+__device__ __forceinline__ void inverse_real_mult_tc(float2* spec, float2* work, const float2* mult,
+                                                     const FftSched& S, const TwSrc& ts) {
+  inverse_real_mult_split(spec, work, mult, S, ts);
   fft_inplace_tc<true>(work, S, ts);
 }
 

@@ -46,7 +46,8 @@ PREC_SPLIT_BF16 = 1
 EXPORTS = ("fif_plan_create", "fif_plan_destroy", "fif_plan_set_stream", "fif_plan_prepare",
            "fif_decompose", "fif_decompose_batch", "fif_decompose_batch_host", "fif_fused_max_n",
            "fif_status_string", "fif_decompose_noalloc", "fif_plan_tune", "fif_plan_get_schedule",
-           "fif_plan_save_tuning", "fif_plan_load_tuning", "fif_plan_batch_launches")
+           "fif_plan_save_tuning", "fif_plan_load_tuning", "fif_plan_batch_launches",
+           "fif_plan_get_multipass_schedule")
 NOALLOC_MAX_N = 16384
 
 
@@ -103,13 +104,14 @@ def load_library(path: str = LIB_PATH):
     lib.fif_status_string.restype = ctypes.c_char_p
     lib.fif_plan_tune.argtypes = [vp, fp, i64p, ctypes.c_int64, fp, i64p, i32p, i32p, i32p, i32p]
     lib.fif_plan_get_schedule.argtypes = [vp, ctypes.c_int64, i32p, i32p, i32p]
+    lib.fif_plan_get_multipass_schedule.argtypes = [vp, ctypes.c_int64] + [i32p] * 7
     lib.fif_plan_batch_launches.argtypes = [vp, ctypes.c_void_p]
     lib.fif_plan_save_tuning.argtypes = [vp, ctypes.c_char_p]
     lib.fif_plan_load_tuning.argtypes = [vp, ctypes.c_char_p]
     for name in ("fif_plan_create", "fif_plan_destroy", "fif_plan_set_stream", "fif_plan_prepare",
                  "fif_decompose", "fif_decompose_batch", "fif_decompose_batch_host",
                  "fif_plan_tune", "fif_plan_get_schedule", "fif_plan_save_tuning",
-                 "fif_plan_load_tuning"):
+                 "fif_plan_load_tuning", "fif_plan_get_multipass_schedule"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -331,6 +333,15 @@ class Plan:
                                                     ctypes.byref(T), ctypes.byref(tuned)),
                "fif_plan_get_schedule")
         return E.value, T.value, bool(tuned.value)
+
+    def multipass_schedule(self, n: int) -> dict:
+        """The multi-pass schedule of length n (fif_plan_get_multipass_schedule)."""
+        v = [ctypes.c_int32() for _ in range(7)]
+        _check(load_library().fif_plan_get_multipass_schedule(self._h, int(n),
+                                                              *[ctypes.byref(x) for x in v]),
+               "fif_plan_get_multipass_schedule")
+        R1, R2, E1, TJ1, E2, TJ2, tuned = (x.value for x in v)
+        return dict(R1=R1, R2=R2, E1=E1, TJ1=TJ1, E2=E2, TJ2=TJ2, tuned=bool(tuned))
 
     def batch_launches(self) -> int:
         """Kernel launches one decompose_batch call enqueues for the last prepared layout."""

@@ -193,14 +193,22 @@ def test_long_classes_of_many_signals_match_oracle(dev, oracle_mod):
 
 
 def test_batch_launch_count(dev):
-    """fif_plan_batch_launches: one fused kernel per short length class; a
-    multi-pass class adds its fixed launch sequence (counted independently
-    here from the structure of one outer iteration)."""
+    """fif_plan_batch_launches: the fused lengths of one E share a persistent
+    launch while their shared memory stays within 2x (1024 and 2048 here: one
+    launch; 256 with 2048: two); a multi-pass class adds its fixed launch
+    sequence (counted independently here from the structure of one outer
+    iteration)."""
     short = [signals.component_signal(71, i, n) for i, n in enumerate([1024, 2048, 1024])]
     x, offs = _pack(short, dev)
     with fif.Plan(max_n=1 << 15, max_imfs=3, max_inner=8) as plan:
         assert plan.batch_launches() == 0
         plan.decompose_batch(x, offs)
+        torch.cuda.synchronize()
+        assert plan.schedule(1024)[0] == plan.schedule(2048)[0]
+        assert plan.batch_launches() == 1
+        far = [signals.component_signal(71, 5, 256), signals.component_signal(71, 6, 2048)]
+        xf, offf = _pack(far, dev)
+        plan.decompose_batch(xf, offf)
         torch.cuda.synchronize()
         assert plan.batch_launches() == 2
         sigs = short + [signals.component_signal(71, 9, 1 << 15)]
@@ -209,4 +217,4 @@ def test_batch_launch_count(dev):
         torch.cuda.synchronize()
         # one long signal: grid-wide m search; max_inner = 8 fits one round of 8 candidates
         per_it = 2 + 2 * 1 + 1 + 2 + 1
-        assert plan.batch_launches() == 2 + 4 + 1 + (3 + 1) * per_it
+        assert plan.batch_launches() == 1 + 4 + 1 + (3 + 1) * per_it

@@ -54,12 +54,40 @@ def test_tune_picks_valid_schedules_and_keeps_results(dev, oracle_mod, tmp_path)
     # every schedule the tuner ran takes the same integer decisions on this batch
     assert torch.equal(res.m, again.m) and torch.equal(res.n_imfs, again.n_imfs)
     assert torch.equal(res.n_imfs, ref.n_imfs)
-    lines = open(path).read().split("\n")
-    assert {int(ln.split()[0]) for ln in lines if ln.strip()} == {4096, 3072, 2187, 16384}
+    lines = [ln.split() for ln in open(path).read().split("\n") if ln.strip()]
+    assert {int(ln[0]) for ln in lines if len(ln) == 2} == {4096, 3072, 2187, 16384}
+    assert {int(ln[0]) for ln in lines if len(ln) == 5} == {20736}   # the multi-pass length
     with fif.Plan(max_n=1 << 15, max_imfs=4) as p2:
         p2.load_tuning(path)
         for n, (E, T, tuned) in after.items():
             assert p2.schedule(n) == (E, T, True)
+        assert p2.multipass_schedule(20736)["tuned"]
+
+
+def test_multipass_tuning_keeps_results(dev, oracle_mod, tmp_path):
+    """The multi-pass classes' inverse-level schedules (E, TJ per level) are tuned,
+    valid, kept by save/load, and the tuned plan still matches the oracle."""
+    lens = [20736] * 4 + [32768] * 3 + [65536] * 2
+    sigs, x, offs = _batch(81, lens, dev)
+    with fif.Plan(max_n=1 << 16, max_imfs=3) as plan:
+        before = {n: plan.multipass_schedule(n) for n in (20736, 32768, 65536)}
+        assert not any(v["tuned"] for v in before.values())
+        plan.tune(x, offs)
+        after = {n: plan.multipass_schedule(n) for n in (20736, 32768, 65536)}
+        for n, v in after.items():
+            assert v["tuned"] and v["R1"] * v["R2"] == n // 2
+            assert v["E1"] in VALID_E and v["E2"] in VALID_E
+            assert 1 <= v["TJ1"] <= 4 and 1 <= v["TJ2"] <= 4
+        res = plan.decompose_batch(x, offs, diag=True)
+        torch.cuda.synchronize()
+        path = str(tmp_path / "mp.txt")
+        plan.save_tuning(path)
+    print("multi-pass schedules: before", before, "after", after)
+    for i in (0, 4, 7, 8):
+        parity.compare(res.signal(i), oracle_mod.direct(sigs[i].astype(np.float64), max_imfs=3))
+    with fif.Plan(max_n=1 << 16, max_imfs=3) as p2:
+        p2.load_tuning(path)
+        assert p2.multipass_schedule(32768) == after[32768]
 
 
 def test_load_tuning_skips_unusable_lines_and_rejects_garbage(dev, tmp_path):
