@@ -58,6 +58,9 @@ WORKLOADS = {
                         "2-5 chirped AM components + noise; delta=1e-3, max_imfs=10"),
     "long": dict(desc="one float32 signal, n=2^24, 6 components f0=10^{0..6}, noise 1e-3; "
                       "delta=1e-3, max_imfs=10"),
+    "long_bf16": dict(desc="the long signal with the split-BF16 tensor-core variant (radix-16 "
+                           "passes of both multi-pass inverse levels as BF16 hi+lo mma "
+                           "products, FP32 accumulation); delta=1e-3, max_imfs=10"),
     "batch16384_n0": dict(desc="the batch16384 signals with m from the a-priori bound of "
                                "Theorem 5 (eq. N0_discrete; absolute delta=2.0, "
                                "max_inner=65536, max_imfs=10)"),
@@ -143,9 +146,11 @@ def make_workload(name, rank=0):
         data, offs = generate(signals.W_UNEVEN, lens)
         if name == "uneven_sh":
             params.update(window_shape=SINE_SHAPE)
-    elif name == "long":
+    elif name in ("long", "long_bf16"):
         s = signals.long_signal()
         data, offs = s, np.array([0, s.size], dtype=np.int64)
+        if name == "long_bf16":
+            params["precision"] = 1  # FIF_PREC_SPLIT_BF16
     elif name in ("batch4096", "batch4096_d1e-4", "batch4096_bf16"):
         data, offs = generate(signals.W_BATCH_4096, np.full(65536, 4096),
                               first=first_signal(name, rank))
@@ -594,7 +599,7 @@ def main():
         rng = np.random.default_rng(12345)
         # a bounded sample: about 30 s of oracle work on the machine's cores
         order = rng.permutation(nsig)
-        budget = 16 * threads * 16384 if args.workload != "long" else 1 << 24
+        budget = 16 * threads * 16384 if not args.workload.startswith("long") else 1 << 24
         idx, tot = [], 0
         for i in order[:max(args.cpu_sample, 1)]:
             if tot + lens[i] > budget and idx:

@@ -668,7 +668,24 @@ fif_status get_large(fif_plan_t p, int64_t n, LargeTables** out) {
   G.sinff = sff;
   G.rcpff = rff;
   if (e == cudaSuccess) e = large_build_tables(G, thi, thil, tlo, tlol, sff, rff, p->stream);
-  {
+  if (p->desc.precision == FIF_PREC_SPLIT_BF16) {
+    // the split-BF16 variant: each FP32 inverse level whose sub-FFT takes an
+    // E = 16 schedule with warp-aligned transforms runs its radix-16 passes on
+    // the tensor cores
+    for (int level = 1; level <= 2; level++) {
+      for (int tj : {4, 3, 2, 1}) {
+        LgSched t = G;
+        if (!set_level(t, level, 16, tj, p->smem_optin)) continue;
+        const FftSched& sub = level == 1 ? t.S1 : t.S2;
+        bool r16 = false;
+        for (int q = 0; q < sub.npass; q++) r16 |= sub.radix[q] == 16;
+        if (!r16 || sub.T % 32) break;
+        G = t;
+        (level == 1 ? G.tc1 : G.tc2) = 1;
+        break;
+      }
+    }
+  } else {
     // a tuned (or loaded) schedule of the inverse levels replaces the rule's
     auto tv = p->large_sched.find(n);
     if (tv != p->large_sched.end()) {

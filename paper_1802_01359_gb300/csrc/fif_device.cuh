@@ -353,20 +353,26 @@ __device__ __forceinline__ void fft_pass(Cx* buf, const FftSched& S,
   }
   __syncthreads();
   if (active) {
-    const int twstep = S.n / (Ns * R);
+    // j mod Ns: a mask when Ns is a power of two (every pass of a 2^a length),
+    // else an integer division
+    const bool p2 = (Ns & (Ns - 1)) == 0;
 #pragma unroll
     for (int t = 0; t < NB; t++) {
       const int j = tid + t * T;
-      const int k = j % Ns;
+      int k;
+      if (p2)
+        k = j & (Ns - 1);
+      else
+        k = j % Ns;
       if constexpr (sizeof(Cx) == sizeof(float2)) {
         if (k != 0) {
           if (tws.p)
             apply_pass_twiddles<INV, R>(&v[t * R], tws.p + (Ns - 1) + k, Ns);
           else
-            apply_twiddles<INV, R>(&v[t * R], tws, k * twstep);
+            apply_twiddles<INV, R>(&v[t * R], tws, k * (S.n / (Ns * R)));
         }
       } else {
-        if (k != 0) apply_twiddles<INV, R>(&v[t * R], tws, k * twstep);
+        if (k != 0) apply_twiddles<INV, R>(&v[t * R], tws, k * (S.n / (Ns * R)));
       }
       butterfly<Cx, INV, R>(&v[t * R]);
       const int base = (j - k) * R + k;

@@ -142,6 +142,8 @@ struct LgSched {
   int sel_blocks;         // CTAs per signal in the grid-wide m search
   const double* shape;    // shape window: the shape's samples (device); nullptr: triangle
   int shape_len;
+  int tc1, tc2;           // FIF_PREC_SPLIT_BF16: the FP32 inverse level runs its radix-16 passes
+                          // on the tensor cores (sub-FFT schedule E = 16, T a multiple of 32)
 };
 
 // The grid-wide m search evaluates SD_j at up to kSelCand values of j per

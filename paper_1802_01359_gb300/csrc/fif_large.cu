@@ -29,6 +29,7 @@
 #include <map>
 
 #include "fif_device.cuh"
+#include "fif_tc.cuh"
 
 namespace fif {
 
@@ -144,7 +145,7 @@ __global__ void lg_pack(const LgSig* __restrict__ sigs, LgSched G, const float* 
 // One pass of TJ sub-FFTs of R points per CTA.  LV 1: butterflies j (Ns = 1)
 // read x[j + r Nc/R1], write y[j R1 + r].  LV 2: butterflies j = k < R1
 // (Ns = R1) read y[j + r R1] times W^(r j), write z[j + r R1].
-template <class Cx, bool INV, int E, int LV>
+template <class Cx, bool INV, int E, int LV, bool TC = false>
 __global__ void __launch_bounds__(512, sizeof(Cx) == 8 ? 2 : 1) lg_level(const LgSig* __restrict__ sigs, LgSched G) {
   extern __shared__ __align__(16) unsigned char smem[];
   const LgSig sg = sigs[blockIdx.y];
@@ -207,7 +208,10 @@ __global__ void __launch_bounds__(512, sizeof(Cx) == 8 ? 2 : 1) lg_level(const L
     fft_inplace<Cx, INV, E>(mine, SR, SR, lt);
   } else {
     const TwSrc ts{q, SR.tw, SR.n, SR.tw_fold};
-    fft_inplace<Cx, INV, E>(mine, SR, ts, lt);
+    if constexpr (TC)
+      fft_inplace_tc<INV>(reinterpret_cast<float2*>(mine), SR, ts, lt);
+    else
+      fft_inplace<Cx, INV, E>(mine, SR, ts, lt);
   }
   if (LV == 1) {
 #pragma unroll
@@ -1152,6 +1156,13 @@ static cudaError_t launch_level(const LgSched& G, const LgSig* d_sigs, int nsig,
   const int threads = ((TJ * SR.T + 31) / 32) * 32;
   const size_t smem = large_level_smem(G, LV, FF);
   const dim3 grid(tiles, nsig);
+  if constexpr (!FF && INV) {
+    if (LV == 1 ? G.tc1 : G.tc2) {  // split-BF16 tensor-core radix-16 passes (E = 16)
+      if (SR.E != 16) return cudaErrorInvalidValue;
+      lg_level<Cx, INV, 16, LV, true><<<grid, threads, smem, st>>>(d_sigs, G);
+      return cudaGetLastError();
+    }
+  }
   switch (SR.E) {
 #define FIF_CASE(e)                                                   \
   case e:                                                             \
@@ -1168,6 +1179,11 @@ static cudaError_t launch_level(const LgSched& G, const LgSig* d_sigs, int nsig,
 template <class Cx, bool INV, int LV>
 static cudaError_t level_attr(const LgSched& G, int smem) {
   const FftSched& SR = LV == 1 ? G.S1 : G.S2;
+  if constexpr (sizeof(Cx) == 8 && INV) {
+    if (LV == 1 ? G.tc1 : G.tc2)
+      return cudaFuncSetAttribute(lg_level<Cx, INV, 16, LV, true>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  }
   switch (SR.E) {
 #define FIF_CASE(e) \
   case e:           \

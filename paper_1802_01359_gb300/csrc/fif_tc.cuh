@@ -105,12 +105,18 @@ __device__ __forceinline__ void mma3(float (&d)[4], const uint32_t (&ahi)[4], co
 // of eight butterflies of a warp are the mma products above.  Every thread
 // of the CTA calls it (the mma is warp-collective: lanes past T feed zeros
 // and store nothing).
+// lt: the thread's index among the S.T threads of this transform (several
+// transforms may share a CTA; each must start on a warp boundary, T a
+// multiple of 32 when there is more than one), S.T or more for threads
+// without a butterfly.  The warp's first butterfly is lane 0's index (the
+// same in every lane; T or more for a warp without butterflies).
 template <bool INV>
 __device__ __forceinline__ void fft_pass16_tc(float2* buf, const FftSched& S, const TwSrc& ts,
-                                              int Ns, const TcDft16& A) {
-  const int tid = threadIdx.x, lane = tid & 31, g = lane >> 2, t = lane & 3;
-  const int T = S.T, stride = S.Nc / 16, warp0 = tid - lane;
-  const int twstep = S.n / (Ns * 16);
+                                              int Ns, const TcDft16& A, int lt) {
+  const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+  const int T = S.T, stride = S.Nc / 16, warp0 = __shfl_sync(0xffffffffu, lt, 0);
+  const bool p2 = (Ns & (Ns - 1)) == 0;  // j mod Ns by a mask (2^a lengths)
+  auto modNs = [&](int j) { return p2 ? (j & (Ns - 1)) : j % Ns; };
   // per group q: the butterfly of column g, inputs r = 2t, 2t+1, 2t+8, 2t+9
   float2 x[4][4];
 #pragma unroll
@@ -126,7 +132,7 @@ __device__ __forceinline__ void fft_pass16_tc(float2* buf, const FftSched& S, co
 #pragma unroll
   for (int q = 0; q < 4; q++) {
     const int jb = warp0 + 8 * q + g;
-    const int k = jb % Ns;
+    const int k = modNs(jb);
     if (jb < T && k != 0) {
 #pragma unroll
       for (int s = 0; s < 4; s++) {
@@ -137,7 +143,7 @@ __device__ __forceinline__ void fft_pass16_tc(float2* buf, const FftSched& S, co
           w = __ldg(ts.p + (Ns - 1) + (r - 1) * Ns + k);  // the per-pass table: inverse
           if (!INV) w = cconj(w);
         } else {
-          w = tw_dir<INV>(ts, r * k * twstep);
+          w = tw_dir<INV>(ts, r * k * (S.n / (Ns * 16)));
         }
         x[q][s] = cmul(x[q][s], w);
       }
@@ -157,7 +163,7 @@ __device__ __forceinline__ void fft_pass16_tc(float2* buf, const FftSched& S, co
     for (int c = 0; c < 2; c++) {
       const int jo = warp0 + 8 * q + 2 * t + c;
       if (jo < T) {
-        const int ko = jo % Ns;
+        const int ko = modNs(jo);
         const int base = (jo - ko) * 16 + ko;
         buf[base + g * Ns] = make_float2(yr[c], yi[c]);
         buf[base + (g + 8) * Ns] = make_float2(yr[2 + c], yi[2 + c]);
@@ -170,18 +176,19 @@ __device__ __forceinline__ void fft_pass16_tc(float2* buf, const FftSched& S, co
 // Complex FFT of S.Nc points with every radix-16 pass on the tensor cores
 // (E = 16 schedules; the other passes as fft_inplace).
 template <bool INV>
-__device__ __forceinline__ void fft_inplace_tc(float2* buf, const FftSched& S, const TwSrc& ts) {
+__device__ __forceinline__ void fft_inplace_tc(float2* buf, const FftSched& S, const TwSrc& ts,
+                                               int lt = threadIdx.x) {
   const TcDft16 A = tc_dft16_fragments<INV>();
   int Ns = 1;
 #pragma unroll 1
   for (int p = 0; p < S.npass; p++) {
     const int R = S.radix[p];
     if (R == 16) {
-      fft_pass16_tc<INV>(buf, S, ts, Ns, A);
+      fft_pass16_tc<INV>(buf, S, ts, Ns, A, lt);
     } else if (R == 8) {
-      fft_pass<float2, INV, 8, 16>(buf, S, ts, Ns, threadIdx.x);
+      fft_pass<float2, INV, 8, 16>(buf, S, ts, Ns, lt);
     } else {
-      fft_tail_pass<float2, INV, 16>(buf, S, ts, Ns, R, threadIdx.x);
+      fft_tail_pass<float2, INV, 16>(buf, S, ts, Ns, R, lt);
     }
     Ns *= R;
   }

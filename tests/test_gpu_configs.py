@@ -30,6 +30,7 @@ pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 
 MAX_FLAGGED = 0.10
+TC_TOL = 1e-4  # the split-BF16 variant's stated IMF bound (tests/test_gpu_tc.py)
 
 
 @pytest.fixture(scope="module")
@@ -132,7 +133,19 @@ def test_long_signal_2p24(dev, oracle_mod, pool):
         res = plan.decompose_batch(x, offs, diag=True)
         torch.cuda.synchronize()
         d = res.signal(0)
-        rep = parity.compare(d, fut.result())
+        ref = fut.result()
+        rep = parity.compare(d, ref)
+    # the split-BF16 variant (tensor-core radix-16 passes in both inverse levels)
+    # against the same oracle result, within its own stated bound
+    with fif.Plan(max_n=n, precision=fif.PREC_SPLIT_BF16) as plan:
+        ms = plan.multipass_schedule(n)
+        assert ms["E1"] == 16 and ms["E2"] == 16, ms
+        rt = plan.decompose_batch(x, offs, diag=True)
+        torch.cuda.synchronize()
+        rep_tc = parity.compare(rt.signal(0), ref, tol=TC_TOL)
+    print("long signal, split-BF16:", {k: v for k, v in rep_tc.items() if k != "errors"},
+          "IMF errors", [f"{e:.2e}" for e in rep_tc["errors"]])
+    assert len(rep_tc["errors"]) >= 3, rep_tc
     # a divergence is allowed only as a flagged tie (parity.compare); every IMF before
     # it is compared element by element
     print("long signal:", {k: v for k, v in rep.items() if k != "errors"},

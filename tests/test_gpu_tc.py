@@ -82,3 +82,24 @@ def test_tc_variant_agrees_with_fp32_path(dev):
           f"largest IMF difference {worst:.2e}")
     assert same >= 0.9 * len(sigs)
     assert worst < TC_TOL
+
+
+def test_tc_variant_on_the_multipass_path(dev, oracle_mod):
+    """A multi-pass inverse level whose sub-FFT has a radix-16 pass and warp-aligned
+    transforms (E = 16) runs it on the tensor cores: 2^20 = 2 x 1024 x 512 (the
+    1024-point level; 512 points schedule as 8 x 8 x 8), 2^21 = 2 x 1024 x 1024 (both)."""
+    sigs = [signals.component_signal(97, 0, 1 << 20), signals.component_signal(97, 1, 1 << 21)]
+    x, offs = _pack(sigs, dev)
+    with fif.Plan(max_n=1 << 21, max_imfs=4, precision=fif.PREC_SPLIT_BF16) as plan:
+        ms = plan.multipass_schedule(1 << 20)
+        assert (ms["R1"], ms["E1"]) == (1024, 16), ms
+        ms = plan.multipass_schedule(1 << 21)
+        assert ms["E1"] == 16 and ms["E2"] == 16, ms
+        res = plan.decompose_batch(x, offs, diag=True)
+        torch.cuda.synchronize()
+    worst = 0.0
+    for i, s in enumerate(sigs):
+        rep = parity.compare(res.signal(i), oracle_mod.direct(s.astype(np.float64), max_imfs=4),
+                             tol=TC_TOL)
+        worst = max([worst] + rep["errors"])
+    print(f"split-BF16, multi-pass: largest IMF relative L2 error {worst:.2e}")
