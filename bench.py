@@ -165,7 +165,8 @@ def make_workload(name, rank=0):
 L2_FLUSH_BYTES = 512 << 20
 FUSED_SOURCES = ("paper_1802_01359_gb300/csrc/fif_device.cuh",
                  "paper_1802_01359_gb300/csrc/fif_fused.cu",
-                 "paper_1802_01359_gb300/csrc/fif_internal.h")
+                 "paper_1802_01359_gb300/csrc/fif_internal.h",
+                 "paper_1802_01359_gb300/csrc/fif_tc.cuh")
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "fused_kernel_traffic.json")
 
 
@@ -186,16 +187,18 @@ def fused_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def recorded_traffic(n_units: int):
-    """DRAM bytes per launch from the committed ncu summary, scaled to this launch's
-    signal count, if the kernel sources still match the profiled ones."""
+def recorded_traffic(n_units: int, key: str):
+    """DRAM bytes per launch from the committed ncu record of this kernel and length (key
+    "n" or "n_bf16"), scaled from the captured launch to this launch's signal count, if the
+    kernel sources still match the profiled ones; else None."""
     if not os.path.exists(TRAFFIC_FILE):
         return None
     with open(TRAFFIC_FILE) as f:
         t = json.load(f)
     if t.get("source_hash") != fused_source_hash():
         return None
-    return float(t["dram_bytes_per_signal"]) * n_units
+    rec = t.get("records", {}).get(key)
+    return None if rec is None else float(rec["dram_bytes_per_signal"]) * n_units
 
 
 class ClockSampler:
@@ -409,6 +412,9 @@ def main():
     ap.add_argument("--plain-signals", type=int, default=64)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-tune", action="store_true", help="fixed schedules, no autotuning")
+    ap.add_argument("--signals", type=int, default=0,
+                    help="decompose only the first N signals of the workload (reduced cases for "
+                         "profiler captures); 0 = all")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -433,6 +439,9 @@ def main():
 
     # inputs first: the generator pool is spawned before any CUDA call
     data, offs, params = make_workload(args.workload, rank)
+    if 0 < args.signals < offs.size - 1:
+        offs = offs[:args.signals + 1].copy()
+        data = data[:int(offs[-1])]
     lens = np.diff(offs)
     nsig = lens.size
 
@@ -514,7 +523,10 @@ def main():
     peak, peak_kind = peaks()
     achieved = alg_bytes / kern_s / 1e9
     fused_only = args.workload.startswith("batch") or args.workload == "single4096"
-    traffic = recorded_traffic(nsig) if args.workload == "batch16384" else None
+    traffic = None
+    if args.workload in UNIFORM:
+        tkey = str(UNIFORM[args.workload][2]) + ("_bf16" if params.get("precision") else "")
+        traffic = recorded_traffic(nsig, tkey)
 
     desc = WORKLOADS[args.workload]["desc"]
     result = {
