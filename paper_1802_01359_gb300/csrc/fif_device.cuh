@@ -1222,34 +1222,6 @@ static __device__ int select_m_on_row(const float2* spec, const FftSched& S, con
   return m;
 }
 
-// IMF spectrum work = (1 - w_hat)^m r_hat (eq. One step_algo) and the
-// spectral remainder update r_hat <- r_hat - IMF_hat = (1 - g) r_hat
-// (Algorithm 2: s = s - s_m).
-static __device__ void apply_multiplier(float2* spec, float2* work, const FftSched& S, int L, int m,
-                                        const MethodParams& mp) {
-  const float2* row = wrow(S, L);
-  const int nt = blockDim.x;
-  for (int k0 = threadIdx.x; k0 < S.P; k0 += kSdBatch * nt) {
-    float hl[kSdBatch];
-#pragma unroll
-    for (int u = 0; u < kSdBatch; u++) {
-      const int k = k0 + u * nt;
-      hl[u] = k < S.P ? __ldg(&row[k].x) : 0.f;
-    }
-#pragma unroll
-    for (int u = 0; u < kSdBatch; u++) {
-      const int k = k0 + u * nt;
-      if (k >= S.P) break;
-      const float2 z = spec[k];
-      float g, omg;
-      multiplier_th(m, hl[u], S, L, k, mp, g, omg);
-      work[k] = make_float2(g * z.x, g * z.y);
-      spec[k] = make_float2(omg * z.x, omg * z.y);
-    }
-  }
-  __syncthreads();
-}
-
 // Time-domain epilogue of one IMF: scale the inverse transform by 1/n, store
 // the IMF row, subtract it from the remainder.  Returns ||IMF||_inf.
 static __device__ float store_imf_update_rem(const float2* work, float* rem, float* out_row,
