@@ -249,7 +249,7 @@ fif_status fif_decompose_batch_host(fif_plan_t plan, const float* signals, const
  * class in it, times each class's launch with CUDA events after a warm-up,
  * and keeps the fastest schedule per length in the plan; then, for every
  * multi-pass length class, it times whole runs of the class with each
- * candidate (E in {8, 16, 4, 12, 6, 24}, TJ in {4, 3, 2, 1}, as fits) for the first
+ * candidate (E in {8, 16, 4, 12, 6, 24, 9, 18}, TJ in {4, 3, 2, 1}, as fits) for the first
  * inverse level, keeps the fastest, then does the same for the second.
  * Later calls use the choices.  Results of the last run are left in the
  * outputs (a valid decomposition).  Under FIF_PREC_SPLIT_BF16 the fused

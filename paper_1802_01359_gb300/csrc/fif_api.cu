@@ -123,7 +123,8 @@ bool is_smooth(int64_t n) {
 // FFT plan with E elements per thread for a complex FFT of Nc = 2^p 3^q
 // points: T = Nc / E threads (at most max_threads), radix passes that all
 // divide E (a thread holds E/R butterflies of one pass in registers): the
-// radix-3 passes first, then 2^p as passes of the main radix RM (largest power
+// factors 3 first (as radix-9 passes when 9 divides E, the odd one left as a
+// radix-3 pass; else radix-3 passes), then 2^p as passes of the main radix RM (largest power
 // of two dividing E, at most 16) and of RM/2, both kept inline by the kernels
 // (p = a log2(RM) + b log2(RM/2) with the fewest passes); a single other
 // radix only when no such split exists.  half_first puts the RM/2 passes
@@ -146,7 +147,14 @@ bool plan_with_E(int Nc, int E, int max_threads, FftSched& s, bool half_first = 
   t.E = E;
   t.T = Nc / E;
   t.npass = 0;
-  for (int i = 0; i < q; i++) t.radix[t.npass++] = 3;
+  // the factors 3 first: radix 9 (two radix-3 stages in registers) where E
+  // holds nine points, radix 3 otherwise
+  if (E % 9 == 0) {
+    for (int i = 0; i < q / 2; i++) t.radix[t.npass++] = 9;
+    if (q % 2) t.radix[t.npass++] = 3;
+  } else {
+    for (int i = 0; i < q; i++) t.radix[t.npass++] = 3;
+  }
   int lm = 0;
   while (lm < 4 && E % (2 << lm) == 0) lm++;  // RM = 2^lm
   int a = -1, b = 0;
@@ -1361,7 +1369,7 @@ fif_status fif_plan_tune(fif_plan_t p, const float* signals, const int64_t* offs
         float best_ms = 0.f;
         e = run_ms(G, &best_ms);
         int bE = level == 1 ? G.S1.E : G.S2.E, btj = level == 1 ? G.TJ1 : G.TJ2;
-        for (int E : {8, 16, 4, 12, 6, 24}) {
+        for (int E : {8, 16, 4, 12, 6, 24, 9, 18}) {
           for (int tj : {4, 3, 2, 1}) {
             if (e != cudaSuccess) break;
             LgSched t = G;

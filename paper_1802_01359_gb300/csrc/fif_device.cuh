@@ -99,6 +99,13 @@ struct Kc<float2> {
   __device__ static float s16() { return 0.382683432365089772f; }
   __device__ static float r2() { return 0.707106781186547524f; }
   __device__ static float h3() { return 0.866025403784438647f; }
+  // cos and sin of 2 pi m/9, m = 1, 2, 4 (the radix-9 twiddles)
+  __device__ static float c91() { return 0.766044443118978035f; }
+  __device__ static float s91() { return 0.642787609686539326f; }
+  __device__ static float c92() { return 0.173648177666930349f; }
+  __device__ static float s92() { return 0.984807753012208059f; }
+  __device__ static float c94() { return -0.939692620785908384f; }
+  __device__ static float s94() { return 0.342020143325668733f; }
   __device__ static float neg(float a) { return -a; }
 };
 template <>
@@ -107,6 +114,12 @@ struct Kc<ffc> {
   __device__ static ff s16() { return ff{0.3826834261417389f, 6.2233507236442165e-09f}; }
   __device__ static ff r2() { return ff{0.7071067690849304f, 1.2101617485882343e-08f}; }
   __device__ static ff h3() { return ff{0.8660253882408142f, 1.5543625053737742e-08f}; }
+  __device__ static ff c91() { return ff{0.7660444378852844f, 5.2336934786012534e-09f}; }
+  __device__ static ff s91() { return ff{0.6427876353263855f, -2.5639845802061245e-08f}; }
+  __device__ static ff c92() { return ff{0.1736481785774231f, -9.10492736760915e-10f}; }
+  __device__ static ff s92() { return ff{0.9848077297210693f, 2.3291137907222037e-08f}; }
+  __device__ static ff c94() { return ff{-0.9396926164627075f, -4.323200908373792e-09f}; }
+  __device__ static ff s94() { return ff{0.3420201539993286f, -1.0673660177928923e-08f}; }
   __device__ static ff neg(ff a) { return ff_neg(a); }
 };
 
@@ -149,6 +162,36 @@ __device__ __forceinline__ void dft3(Cx* v) {
   v[0] = cadd(v[0], t1);
   v[1] = cadd(t2, t3);
   v[2] = csub(t2, t3);
+}
+
+template <class Cx, bool INV>
+__device__ __forceinline__ void dft3r(Cx& a, Cx& b, Cx& c) {
+  const Cx t1 = cadd(b, c);
+  const Cx t2 = csub(a, chalf(t1));
+  const Cx t3 = rot_i<INV>(cscale(csub(b, c), Kc<Cx>::h3()));
+  a = cadd(a, t1);
+  b = cadd(t2, t3);
+  c = csub(t2, t3);
+}
+
+// 9 = 3 x 3: DFT3 over x[3 n1 + n2], twiddle w9^(n2 k1), DFT3 over n2; one
+// pass of shared-memory traffic where two radix-3 passes took two.
+template <class Cx, bool INV>
+__device__ __forceinline__ void dft9(Cx* v) {
+#pragma unroll
+  for (int n2 = 0; n2 < 3; n2++) dft3r<Cx, INV>(v[n2], v[3 + n2], v[6 + n2]);
+  // v[3 k1 + n2] now holds Y[n2][k1]
+  v[4] = rot<INV>(v[4], Kc<Cx>::c91(), Kc<Cx>::s91());
+  v[7] = rot<INV>(v[7], Kc<Cx>::c92(), Kc<Cx>::s92());
+  v[5] = rot<INV>(v[5], Kc<Cx>::c92(), Kc<Cx>::s92());
+  v[8] = rot<INV>(v[8], Kc<Cx>::c94(), Kc<Cx>::s94());
+#pragma unroll
+  for (int k1 = 0; k1 < 3; k1++) dft3r<Cx, INV>(v[3 * k1], v[3 * k1 + 1], v[3 * k1 + 2]);
+  // v[3 k1 + k2] now holds X[k1 + 3 k2]: transpose the 3 x 3 block
+  Cx t;
+  t = v[1], v[1] = v[3], v[3] = t;
+  t = v[2], v[2] = v[6], v[6] = t;
+  t = v[5], v[5] = v[7], v[7] = t;
 }
 
 template <class Cx, bool INV>
@@ -221,6 +264,7 @@ __device__ __forceinline__ void butterfly(Cx* v) {
   if (R == 4) dft4<Cx, INV>(v);
   if (R == 8) dft8<Cx, INV>(v);
   if (R == 16) dft16<Cx, INV>(v);
+  if (R == 9) dft9<Cx, INV>(v);
 }
 
 // ------------------------------------------------------- Stockham passes
@@ -292,6 +336,7 @@ __device__ __forceinline__ void apply_twiddles(float2* v, const TwSrc& ts, int b
   if (R == 8) return;
   const float2 w8 = tw_dir<INV>(ts, 8 * b);
   v[8] = cmul(v[8], w8);
+  if (R == 9) return;
   v[9] = cmul(v[9], cmul(w8, w1));
   v[10] = cmul(v[10], cmul(w8, w2));
   v[11] = cmul(v[11], cmul(w8, w3));
@@ -431,6 +476,8 @@ __device__ __forceinline__ void fft_inplace(Cx* buf, const FftSched& S,
       // FP32 transforms (once per IMF) keep the half-radix pass inline; the
       // float-float forward transform (once per signal) calls it out of line
       if constexpr (sizeof(Cx) == 8 && RM >= 4) fft_pass<Cx, INV, RM / 2, E>(buf, S, tws, Ns, tid);
+    } else if (E % 9 == 0 && R == 9) {
+      if constexpr (E % 9 == 0) fft_pass<Cx, INV, 9, E>(buf, S, tws, Ns, tid);
     } else if (E % 3 == 0 && R == 3) {
       if constexpr (E % 3 == 0 && RM != 3) fft_pass<Cx, INV, 3, E>(buf, S, tws, Ns, tid);
     } else {
