@@ -58,7 +58,31 @@ struct BatchLayout {
 struct LargeTables {
   LgSched G;
   std::vector<void*> allocs;
+  std::map<std::vector<int>, float2*> ptw;  // per-pass twiddles per (R, radix sequence)
 };
+
+// The per-pass twiddle tables of the FP32 levels' sub-FFT schedules (global
+// memory, read through L1, in place of the folded shared-memory table), built
+// once per (R, radix sequence) and owned by lt.
+static cudaError_t large_pass_tables(LargeTables& lt, LgSched& G, cudaStream_t st) {
+  for (FftSched* s : {&G.S1, &G.S2}) {
+    std::vector<int> key{s->n};
+    key.insert(key.end(), s->radix, s->radix + s->npass);
+    auto it = lt.ptw.find(key);
+    if (it == lt.ptw.end()) {
+      float2* d = nullptr;
+      cudaError_t e = cudaMalloc(&d, sizeof(float2) * (size_t)std::max(s->Nc - 1, 1));
+      if (e == cudaSuccess) e = build_pass_twiddles(*s, d, st);
+      if (e != cudaSuccess) {
+        cudaFree(d);
+        return e;
+      }
+      it = lt.ptw.emplace(key, d).first;
+    }
+    s->ptw = it->second;
+  }
+  return cudaSuccess;
+}
 
 struct LargeBuffers {
   int64_t n = 0;
@@ -587,9 +611,10 @@ bool make_large_sched(int64_t n64, int smem_limit, LgSched& G) {
   G.TJF1 = pick_tj(G.R1, G.S1.T, G.R2, 16, 0, smem_limit);
   G.TJF2 = pick_tj(G.R2, G.S2.T, G.R1, 16, 0, smem_limit);
   if (!G.TJ1 || !G.TJ2 || !G.TJF1 || !G.TJF2) return false;
-  int B = 1;
-  while ((int64_t)B * B < Nc) B++;
-  G.B = B;
+  // the inter-level twiddle split: B the least power of two with B^2 >= Nc
+  G.Bs = 0;
+  while ((int64_t)1 << (2 * G.Bs) < Nc) G.Bs++;
+  G.B = 1 << G.Bs;
   return true;
 }
 
@@ -600,6 +625,7 @@ bool set_level(LgSched& G, int level, int E, int tj, int smem_limit) {
   const int R = level == 1 ? G.R1 : G.R2, count = level == 1 ? G.R2 : G.R1;
   FftSched sub = level == 1 ? G.S1 : G.S2;
   if (!plan_with_E(R, E, 512, sub)) return false;
+  sub.ptw = nullptr;  // the per-pass table of the new radix sequence: large_pass_tables
   if (tj < 1 || count % tj || tj * sub.T > 512) return false;
   if ((size_t)tj * R * 8 + tw_slots(sub) * sizeof(float2) + 1024 > (size_t)smem_limit) return false;
   // the float-float forward level keeps its own sub-FFT count, which must
@@ -703,9 +729,11 @@ fif_status get_large(fif_plan_t p, int64_t n, LargeTables** out) {
         G = t;
     }
   }
+  if (e == cudaSuccess) e = large_pass_tables(lt, G, p->stream);
   if (e == cudaSuccess) e = large_set_attrs(G);
   if (e != cudaSuccess) {
     for (void* a : lt.allocs) cudaFree(a);
+    for (auto& pw : lt.ptw) cudaFree(pw.second);
     cudaGetLastError();
     return cuda_status(e);
   }
@@ -1034,8 +1062,10 @@ fif_status fif_plan_destroy(fif_plan_t p) {
   }
   cudaFree(p->d_shape);
   free_layout(p->layout);
-  for (auto& kv : p->large)
+  for (auto& kv : p->large) {
     for (void* a : kv.second.allocs) cudaFree(a);
+    for (auto& pw : kv.second.ptw) cudaFree(pw.second);
+  }
   for (auto& kv : p->large_bufs) free_large_buffers(kv.second);
   cudaFree(p->scr.spec);
   cudaFree(p->scr.work);
@@ -1351,8 +1381,9 @@ fif_status fif_plan_tune(fif_plan_t p, const float* signals, const int64_t* offs
     for (size_t c = 0; st == FIF_OK && c < l.lcls.size() && e == cudaSuccess; c++) {
       const auto& lc = l.lcls[c];
       LgSched& G = lc.lt->G;
-      auto run_ms = [&](const LgSched& t, float* ms) {
-        cudaError_t r = large_set_attrs(t);
+      auto run_ms = [&](LgSched t, float* ms) {
+        cudaError_t r = large_pass_tables(*lc.lt, t, p->stream);
+        if (r == cudaSuccess) r = large_set_attrs(t);
         float best_ms = 0.f;
         for (int rep = 0; rep < 2 && r == cudaSuccess; rep++) {  // one warm-up, one timed
           r = cudaMemsetAsync(lc.b->st, 0, sizeof(int) * kLgStateWords * (size_t)lc.count, p->stream);
@@ -1382,6 +1413,7 @@ fif_status fif_plan_tune(fif_plan_t p, const float* signals, const int64_t* offs
         }
         if (e == cudaSuccess) set_level(G, level, bE, btj, p->smem_optin);
       }
+      if (e == cudaSuccess) e = large_pass_tables(*lc.lt, G, p->stream);
       if (e == cudaSuccess) e = large_set_attrs(G);
       if (e == cudaSuccess) p->large_sched[lc.n] = {G.S1.E, G.TJ1, G.S2.E, G.TJ2};
     }
@@ -1494,7 +1526,7 @@ fif_status fif_plan_load_tuning(fif_plan_t p, const char* path) {
       LgSched t = it->second.G;
       if (set_level(t, 1, kv.second[0], kv.second[1], p->smem_optin) &&
           set_level(t, 2, kv.second[2], kv.second[3], p->smem_optin) &&
-          large_set_attrs(t) == cudaSuccess)
+          large_pass_tables(it->second, t, p->stream) == cudaSuccess && large_set_attrs(t) == cudaSuccess)
         it->second.G = t;
     }
   }

@@ -132,7 +132,7 @@ struct LgSched {
   int R1, R2;
   int TJ1, TJ2;           // sub-FFTs per CTA in the FP32 passes
   int TJF1, TJF2;         // sub-FFTs per CTA in the float-float passes
-  int B;                  // W^m = thi[m / B] * tlo[m % B], W = exp(-2 pi i / Nc)
+  int B, Bs;              // W^m = thi[m >> Bs] * tlo[m & (B - 1)], B = 2^Bs, W = exp(-2 pi i / Nc)
   const float2* thi;
   const float2* thi_lo;
   const float2* tlo;

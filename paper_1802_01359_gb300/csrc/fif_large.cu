@@ -78,7 +78,7 @@ template <class Cx, bool INV>
 __device__ __forceinline__ Cx inter_twiddle(const LgSched& G, int m);
 template <>
 __device__ __forceinline__ float2 inter_twiddle<float2, false>(const LgSched& G, int m) {
-  const int a = m / G.B, b = m - a * G.B;
+  const int a = m >> G.Bs, b = m & (G.B - 1);
   return cmul(__ldg(&G.thi[a]), __ldg(&G.tlo[b]));
 }
 template <>
@@ -87,7 +87,7 @@ __device__ __forceinline__ float2 inter_twiddle<float2, true>(const LgSched& G, 
 }
 template <>
 __device__ __forceinline__ ffc inter_twiddle<ffc, false>(const LgSched& G, int m) {
-  const int a = m / G.B, b = m - a * G.B;
+  const int a = m >> G.Bs, b = m & (G.B - 1);
   const float2 h1 = __ldg(&G.thi[a]), l1 = __ldg(&G.thi_lo[a]);
   const float2 h2 = __ldg(&G.tlo[b]), l2 = __ldg(&G.tlo_lo[b]);
   return cmul(ffc{ff{h1.x, l1.x}, ff{h1.y, l1.y}}, ffc{ff{h2.x, l2.x}, ff{h2.y, l2.y}});
@@ -170,6 +170,19 @@ __global__ void __launch_bounds__(512, sizeof(Cx) == 8 ? 2 : 1) lg_level(const L
   const int tid = threadIdx.x, nt = blockDim.x;
   const int j0 = blockIdx.x * TJ;
   const int tile = TJ * R;  // at most E elements per thread (nt >= TJ R / E)
+  // element f = tid + u nt of the tile is row r = f / TJ of column g = f % TJ;
+  // when TJ divides nt, r = r0 + u nt / TJ and g = g0 (no division per element)
+  const bool tj_div = nt % TJ == 0;
+  const int r0 = tid / TJ, g0 = tid - r0 * TJ, rstep = nt / TJ;
+  auto row_col = [&](int u, int f, int& r, int& g) {
+    if (tj_div) {
+      r = r0 + u * rstep;
+      g = g0;
+    } else {
+      r = f / TJ;
+      g = f - r * TJ;
+    }
+  };
   {
     // all of this thread's loads in flight together, then the transposed
     // stores to shared memory
@@ -178,7 +191,8 @@ __global__ void __launch_bounds__(512, sizeof(Cx) == 8 ? 2 : 1) lg_level(const L
     for (int u = 0; u < E; u++) {
       const int f = tid + u * nt;
       if (f < tile) {
-        const int r = f / TJ, g = f - r * TJ;
+        int r, g;
+        row_col(u, f, r, g);
         v[u] = in[j0 + g + r * stride_in];
       }
     }
@@ -186,7 +200,8 @@ __global__ void __launch_bounds__(512, sizeof(Cx) == 8 ? 2 : 1) lg_level(const L
     for (int u = 0; u < E; u++) {
       const int f = tid + u * nt;
       if (f < tile) {
-        const int r = f / TJ, g = f - r * TJ;
+        int r, g;
+        row_col(u, f, r, g);
         if (LV == 2) v[u] = cmul(v[u], inter_twiddle<Cx, INV>(G, r * (j0 + g)));
         buf[g * R + r] = v[u];
       }
@@ -194,10 +209,13 @@ __global__ void __launch_bounds__(512, sizeof(Cx) == 8 ? 2 : 1) lg_level(const L
   }
   float2* q = nullptr;
   if constexpr (!FF) {
-    q = reinterpret_cast<float2*>(smem + (size_t)TJ * R * sizeof(Cx));
-    for (int u = tid; u < SR.tw_entries; u += nt) {
-      const float2 w = __ldg(&SR.tw[u]);
-      q[tw_slot(u)] = make_float2(w.x, -w.y);
+    // the folded table in shared memory, unless the schedule has a per-pass table
+    if (!SR.ptw) {
+      q = reinterpret_cast<float2*>(smem + (size_t)TJ * R * sizeof(Cx));
+      for (int u = tid; u < SR.tw_entries; u += nt) {
+        const float2 w = __ldg(&SR.tw[u]);
+        q[tw_slot(u)] = make_float2(w.x, -w.y);
+      }
     }
   }
   __syncthreads();
@@ -207,27 +225,26 @@ __global__ void __launch_bounds__(512, sizeof(Cx) == 8 ? 2 : 1) lg_level(const L
   if constexpr (FF) {
     fft_inplace<Cx, INV, E>(mine, SR, SR, lt);
   } else {
-    const TwSrc ts{q, SR.tw, SR.n, SR.tw_fold};
+    const TwSrc ts{q, SR.tw, SR.n, SR.tw_fold, SR.ptw};
     if constexpr (TC)
       fft_inplace_tc<INV>(reinterpret_cast<float2*>(mine), SR, ts, lt);
     else
       fft_inplace<Cx, INV, E>(mine, SR, ts, lt);
   }
   if (LV == 1) {
+    // column j0 + gg, row r goes to (j0 + gg) R + r = j0 R + f
 #pragma unroll
     for (int u = 0; u < E; u++) {
       const int f = tid + u * nt;
-      if (f < tile) {
-        const int gg = f / R, r = f - gg * R;
-        out[(size_t)(j0 + gg) * R + r] = buf[f];
-      }
+      if (f < tile) out[(size_t)j0 * R + f] = buf[f];
     }
   } else {
 #pragma unroll
     for (int u = 0; u < E; u++) {
       const int f = tid + u * nt;
       if (f < tile) {
-        const int r = f / TJ, gg = f - r * TJ;
+        int r, gg;
+        row_col(u, f, r, gg);
         out[j0 + gg + r * G.R1] = buf[gg * R + r];
       }
     }
@@ -1140,7 +1157,7 @@ size_t large_level_smem(const LgSched& G, int level, bool ff) {
   const FftSched& SR = level == 1 ? G.S1 : G.S2;
   const int TJ = ff ? (level == 1 ? G.TJF1 : G.TJF2) : (level == 1 ? G.TJ1 : G.TJ2);
   size_t b = (size_t)TJ * R * (ff ? 16 : 8);
-  if (!ff) b += tw_slots(SR) * sizeof(float2);
+  if (!ff && !SR.ptw) b += tw_slots(SR) * sizeof(float2);
   return b;
 }
 
