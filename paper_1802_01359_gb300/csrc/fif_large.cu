@@ -777,9 +777,13 @@ constexpr int kSelCtaMinSignals = 8;
 // term of sd_below (sd_term) for each candidate, accumulated online per
 // thread, merged per CTA into sg.part; the last CTA merges the CTAs in index
 // order and classifies each candidate against delta with the error band of
-// this reduction (screen_margin).
+// this reduction (screen_margin).  ONE: the round tests max_inner alone (one
+// accumulator).  Each thread takes the bins k, k + stride, ... in that order,
+// kSdBatch of them per step with their loads issued together.
+template <bool ONE>
 __global__ void __launch_bounds__(kSelThreads) lg_sel32(const LgSig* __restrict__ sigs, LgSched G,
                                                          MethodParams mp, int round) {
+  constexpr int NC = ONE ? 1 : kSelCand;
   __shared__ Online wpart[kSelThreads / 32][kSelCand];
   __shared__ Online fin[kSelCand];
   const LgSig sg = sigs[blockIdx.y];
@@ -788,37 +792,47 @@ __global__ void __launch_bounds__(kSelThreads) lg_sel32(const LgSig* __restrict_
   const int jmax = mp.max_inner, lo = st[LG_LO], hi = st[LG_HI];
   const int c = sel_count(lo, hi, jmax, round);
   if (c == 0) return;
+  if (ONE && c != 1) return;  // (the host launches ONE for such rounds only)
   const FftSched& S = G.S;
   const float sc = spectrum_scale(S.n, __int_as_float(st[LG_SMAX]));
-  Online o[kSelCand];
-  float e2[kSelCand];
+  Online o[NC];
+  float e2[NC];
 #pragma unroll
-  for (int i = 0; i < kSelCand; i++) {
+  for (int i = 0; i < NC; i++) {
     o[i] = Online{-INFINITY, 0.f, 0.f, 0.f, 0.f};
     e2[i] = i < c ? 2.f * (float)(sel_cand(lo, hi, jmax, round, i) - 1) : 0.f;
   }
   const int stride = gridDim.x * blockDim.x;
-  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < S.P; k += stride) {
-    const float2 z = sg.spec[k];
-    if (z.x == 0.f && z.y == 0.f) continue;
-    const float2 tv = sg.row[k];
-    const float re = z.x * sc, im = z.y * sc;
-    const float q = parseval_weight(S, k) * fmaf(re, re, im * im);
-    if (!(q > 0.f)) continue;
-    float qm, qe;
-    q_split(q, qm, qe);
-    const float w2 = tv.y * tv.y;
+  for (int k0 = blockIdx.x * blockDim.x + threadIdx.x; k0 < S.P; k0 += kSdBatch * stride) {
+    float2 z[kSdBatch], tv[kSdBatch];
 #pragma unroll
-    for (int i = 0; i < kSelCand; i++) {
-      if (i < c) {
-        const float e = e2[i] == 0.f ? 0.f : e2[i] * tv.x;
-        if (e != -INFINITY) sd_term(qm, qe, e, w2, o[i]);  // w_hat = 1: no weight for j > 1
+    for (int u = 0; u < kSdBatch; u++) {
+      const int k = k0 + u * stride;
+      z[u] = k < S.P ? sg.spec[k] : make_float2(0.f, 0.f);
+      tv[u] = k < S.P ? sg.row[k] : make_float2(0.f, 0.f);
+    }
+#pragma unroll
+    for (int u = 0; u < kSdBatch; u++) {
+      if (z[u].x == 0.f && z[u].y == 0.f) continue;  // also bins past the end
+      const int k = k0 + u * stride;
+      const float re = z[u].x * sc, im = z[u].y * sc;
+      const float q = parseval_weight(S, k) * fmaf(re, re, im * im);
+      if (!(q > 0.f)) continue;
+      float qm, qe;
+      q_split(q, qm, qe);
+      const float w2 = tv[u].y * tv[u].y;
+#pragma unroll
+      for (int i = 0; i < NC; i++) {
+        if (i < c) {
+          const float e = e2[i] == 0.f ? 0.f : e2[i] * tv[u].x;
+          if (e != -INFINITY) sd_term(qm, qe, e, w2, o[i]);  // w_hat = 1: no weight for j > 1
+        }
       }
     }
   }
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
-  for (int i = 0; i < kSelCand; i++) {
+  for (int i = 0; i < NC; i++) {
     if (i < c) {
       const Online r = warp_merge(o[i]);
       if (lane == 0) wpart[wid][i] = r;
@@ -1282,7 +1296,10 @@ cudaError_t large_run(const LgSched& G, const LgSig* d_sigs, int nsig, const Met
       lg_select_cta<<<nsig, 512, 0, st>>>(d_sigs, G, mp);
     } else {
       for (int r = 0; r < rounds; r++) {
-        lg_sel32<<<dim3(G.sel_blocks, nsig), kSelThreads, 0, st>>>(d_sigs, G, mp, r);
+        if (sel_count(0, 0, mp.max_inner, r) == 1 && r == 0)  // max_inner tested alone
+          lg_sel32<true><<<dim3(G.sel_blocks, nsig), kSelThreads, 0, st>>>(d_sigs, G, mp, r);
+        else
+          lg_sel32<false><<<dim3(G.sel_blocks, nsig), kSelThreads, 0, st>>>(d_sigs, G, mp, r);
         lg_sel64<<<dim3(G.sel_blocks, nsig), kSelThreads, 0, st>>>(d_sigs, G, mp, r);
       }
     }
