@@ -608,8 +608,10 @@ bool make_large_sched(int64_t n64, int smem_limit, LgSched& G) {
   const size_t t1 = tw_slots(G.S1) * sizeof(float2), t2 = tw_slots(G.S2) * sizeof(float2);
   G.TJ1 = pick_tj(G.R1, G.S1.T, G.R2, 8, t1, smem_limit);
   G.TJ2 = pick_tj(G.R2, G.S2.T, G.R1, 8, t2, smem_limit);
-  G.TJF1 = pick_tj(G.R1, G.S1.T, G.R2, 16, 0, smem_limit);
-  G.TJF2 = pick_tj(G.R2, G.S2.T, G.R1, 16, 0, smem_limit);
+  G.F1 = G.S1;
+  G.F2 = G.S2;
+  G.TJF1 = pick_tj(G.R1, G.F1.T, G.R2, 16, 0, smem_limit);
+  G.TJF2 = pick_tj(G.R2, G.F2.T, G.R1, 16, 0, smem_limit);
   if (!G.TJ1 || !G.TJ2 || !G.TJF1 || !G.TJF2) return false;
   // the inter-level twiddle split: B the least power of two with B^2 >= Nc
   G.Bs = 0;
@@ -628,10 +630,6 @@ bool set_level(LgSched& G, int level, int E, int tj, int smem_limit) {
   sub.ptw = nullptr;  // the per-pass table of the new radix sequence: large_pass_tables
   if (tj < 1 || count % tj || tj * sub.T > 512) return false;
   if ((size_t)tj * R * 8 + tw_slots(sub) * sizeof(float2) + 1024 > (size_t)smem_limit) return false;
-  // the float-float forward level keeps its own sub-FFT count, which must
-  // still fit the schedule's threads
-  const int tjf = level == 1 ? G.TJF1 : G.TJF2;
-  if (tjf * sub.T > 512) return false;
   if (level == 1) {
     G.S1 = sub;
     G.TJ1 = tj;
@@ -691,10 +689,10 @@ fif_status get_large(fif_plan_t p, int64_t n, LargeTables** out) {
   G.S.om64_stride = 0;
   G.shape = p->d_shape;
   G.shape_len = (int)p->shape.size();
-  G.S1.tw = tw1;
-  G.S1.tw_lo = tw1l;
-  G.S2.tw = tw2;
-  G.S2.tw_lo = tw2l;
+  G.S1.tw = G.F1.tw = tw1;
+  G.S1.tw_lo = G.F1.tw_lo = tw1l;
+  G.S2.tw = G.F2.tw = tw2;
+  G.S2.tw_lo = G.F2.tw_lo = tw2l;
   G.thi = thi;
   G.thi_lo = thil;
   G.tlo = tlo;

@@ -128,7 +128,9 @@ inline int sched_threads(const FftSched& s) {
 // memory, each a set of shared-memory sub-FFTs of R1 (then R2) points.
 struct LgSched {
   FftSched S;             // the signal length: n, Nc, odd, P, Lmax, tw/tw_lo over n, sin64
-  FftSched S1, S2;        // complex sub-FFTs of R1 and R2 points (n = Nc = R)
+  FftSched S1, S2;        // complex sub-FFTs of R1 and R2 points (n = Nc = R): the FP32 inverse levels
+  FftSched F1, F2;        // the same sub-FFTs for the float-float forward levels (the fixed
+                          // rule's schedules; the tuner changes S1 and S2 only)
   int R1, R2;
   int TJ1, TJ2;           // sub-FFTs per CTA in the FP32 passes
   int TJF1, TJF2;         // sub-FFTs per CTA in the float-float passes

@@ -153,7 +153,7 @@ __global__ void __launch_bounds__(512, sizeof(Cx) == 8 ? 2 : 1) lg_level(const L
   // transform a shape window's h, which an unchanged L does not need again)
   if (sg.st[LG_DONE] || (!INV && sg.st[LG_ROWOK])) return;
   constexpr bool FF = sizeof(Cx) == 16;
-  const FftSched& SR = LV == 1 ? G.S1 : G.S2;
+  const FftSched& SR = FF ? (LV == 1 ? G.F1 : G.F2) : (LV == 1 ? G.S1 : G.S2);
   const int R = LV == 1 ? G.R1 : G.R2;
   const int TJ = FF ? (LV == 1 ? G.TJF1 : G.TJF2) : (LV == 1 ? G.TJ1 : G.TJ2);
   const int stride_in = LV == 1 ? G.R2 : G.R1;
@@ -1168,7 +1168,7 @@ cudaError_t large_build_tables(const LgSched& G, float2* thi, float2* thi_lo, fl
 
 size_t large_level_smem(const LgSched& G, int level, bool ff) {
   const int R = level == 1 ? G.R1 : G.R2;
-  const FftSched& SR = level == 1 ? G.S1 : G.S2;
+  const FftSched& SR = ff ? (level == 1 ? G.F1 : G.F2) : (level == 1 ? G.S1 : G.S2);
   const int TJ = ff ? (level == 1 ? G.TJF1 : G.TJF2) : (level == 1 ? G.TJ1 : G.TJ2);
   size_t b = (size_t)TJ * R * (ff ? 16 : 8);
   if (!ff && !SR.ptw) b += tw_slots(SR) * sizeof(float2);
@@ -1180,7 +1180,7 @@ size_t large_level_smem(const LgSched& G, int level, bool ff) {
 template <class Cx, bool INV, int LV>
 static cudaError_t launch_level(const LgSched& G, const LgSig* d_sigs, int nsig, cudaStream_t st) {
   constexpr bool FF = sizeof(Cx) == 16;
-  const FftSched& SR = LV == 1 ? G.S1 : G.S2;
+  const FftSched& SR = FF ? (LV == 1 ? G.F1 : G.F2) : (LV == 1 ? G.S1 : G.S2);
   const int TJ = FF ? (LV == 1 ? G.TJF1 : G.TJF2) : (LV == 1 ? G.TJ1 : G.TJ2);
   const int R = LV == 1 ? G.R1 : G.R2;
   const int tiles = (G.S.Nc / R) / TJ;
@@ -1209,7 +1209,7 @@ static cudaError_t launch_level(const LgSched& G, const LgSig* d_sigs, int nsig,
 
 template <class Cx, bool INV, int LV>
 static cudaError_t level_attr(const LgSched& G, int smem) {
-  const FftSched& SR = LV == 1 ? G.S1 : G.S2;
+  const FftSched& SR = sizeof(Cx) == 16 ? (LV == 1 ? G.F1 : G.F2) : (LV == 1 ? G.S1 : G.S2);
   if constexpr (sizeof(Cx) == 8 && INV) {
     if (LV == 1 ? G.tc1 : G.tc2)
       return cudaFuncSetAttribute(lg_level<Cx, INV, 16, LV, true>,
