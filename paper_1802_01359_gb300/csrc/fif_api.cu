@@ -572,6 +572,13 @@ bool make_sub_sched(int R, FftSched& s) {
   return make_fft_plan(R, s);
 }
 
+// The swizzled column layout of an FP32 level (work_slot; kernels for the
+// E = 8 and 16 schedules of sub-FFTs in whole 16-point blocks): mask 15, else
+// 0 (plain layout, no slot arithmetic).  Measured on the 4096 x 2048 levels of
+// n = 2^24: both levels about 21 % faster (the first pass's 16-way store
+// conflicts gone); neutral on the uneven batch's lengths.
+int level_swizzle(int R, int E) { return R % 16 == 0 && (E == 8 || E == 16) ? 15 : 0; }
+
 int pick_tj(int R, int T, int count, size_t elem, size_t extra, int smem_limit) {
   for (int tj : {4, 3, 2, 1}) {
     if (count % tj) continue;
@@ -610,6 +617,8 @@ bool make_large_sched(int64_t n64, int smem_limit, LgSched& G) {
   G.TJ2 = pick_tj(G.R2, G.S2.T, G.R1, 8, t2, smem_limit);
   G.F1 = G.S1;
   G.F2 = G.S2;
+  G.S1.swz = level_swizzle(G.R1, G.S1.E);
+  G.S2.swz = level_swizzle(G.R2, G.S2.E);
   G.TJF1 = pick_tj(G.R1, G.F1.T, G.R2, 16, 0, smem_limit);
   G.TJF2 = pick_tj(G.R2, G.F2.T, G.R1, 16, 0, smem_limit);
   if (!G.TJ1 || !G.TJ2 || !G.TJF1 || !G.TJF2) return false;
@@ -628,8 +637,10 @@ bool set_level(LgSched& G, int level, int E, int tj, int smem_limit) {
   FftSched sub = level == 1 ? G.S1 : G.S2;
   if (!plan_with_E(R, E, 512, sub)) return false;
   sub.ptw = nullptr;  // the per-pass table of the new radix sequence: large_pass_tables
+  sub.swz = level_swizzle(R, E);
   if (tj < 1 || count % tj || tj * sub.T > 512) return false;
-  if ((size_t)tj * R * 8 + tw_slots(sub) * sizeof(float2) + 1024 > (size_t)smem_limit) return false;
+  if ((size_t)tj * (R + kLgColPad) * 8 + tw_slots(sub) * sizeof(float2) + 1024 > (size_t)smem_limit)
+    return false;
   if (level == 1) {
     G.S1 = sub;
     G.TJ1 = tj;

@@ -280,6 +280,14 @@ struct TwSrc {
   const float2* p;   // or the schedule's per-pass table (FftSched::ptw; inverse direction)
 };
 
+// Slot of point i in a swizzled transform buffer: i with its low four bits
+// XOR-ed by five times its 16-point block index (mask m = 15), or i itself
+// (m = 0).  A bijection inside every aligned block of 16 points, so a
+// half-warp reading 16 consecutive points still meets every bank pair once,
+// while the Stockham stores R or Ns points apart spread over all bank pairs
+// instead of meeting in one (up to 16-way conflicts in the first pass).
+__device__ __forceinline__ int work_slot(int i, int m) { return i ^ (((i >> 4) * 5) & m); }
+
 // exp(-2 pi i t/n), 0 <= t < n
 __device__ __forceinline__ float2 tw_value(const TwSrc& ts, int t) {
   if (!ts.q) return __ldg(&ts.g[t]);
@@ -379,10 +387,12 @@ struct TwArg<ffc> {
 // One radix-R pass of the self-sorting (Stockham) FFT, in place: every thread
 // first loads its E/R butterflies (inputs at j + r*Nc/R), the CTA
 // synchronises, then each butterfly is twiddled by w_{Ns R}^{r (j mod Ns)},
-// transformed, and stored at (j - j mod Ns) R + j mod Ns + r Ns.
-template <class Cx, bool INV, int R, int E>
+// transformed, and stored at (j - j mod Ns) R + j mod Ns + r Ns.  SWZ: point
+// i lives in slot work_slot(i, S.swz) of buf.
+template <class Cx, bool INV, int R, int E, bool SWZ = false>
 __device__ __forceinline__ void fft_pass(Cx* buf, const FftSched& S,
                                          const typename TwArg<Cx>::type& tws, int Ns, int tid) {
+  auto slot = [&](int i) { return SWZ ? work_slot(i, S.swz) : i; };
   constexpr int NB = E / R;
   const int T = S.T;
   const int stride = S.Nc / R;
@@ -393,7 +403,7 @@ __device__ __forceinline__ void fft_pass(Cx* buf, const FftSched& S,
     for (int t = 0; t < NB; t++) {
       const int j = tid + t * T;
 #pragma unroll
-      for (int r = 0; r < R; r++) v[t * R + r] = buf[j + r * stride];
+      for (int r = 0; r < R; r++) v[t * R + r] = buf[slot(j + r * stride)];
     }
   }
   __syncthreads();
@@ -422,7 +432,7 @@ __device__ __forceinline__ void fft_pass(Cx* buf, const FftSched& S,
       butterfly<Cx, INV, R>(&v[t * R]);
       const int base = (j - k) * R + k;
 #pragma unroll
-      for (int r = 0; r < R; r++) buf[base + r * Ns] = v[t * R + r];
+      for (int r = 0; r < R; r++) buf[slot(base + r * Ns)] = v[t * R + r];
     }
   }
   __syncthreads();
@@ -432,21 +442,21 @@ __device__ __forceinline__ void fft_pass(Cx* buf, const FftSched& S,
 // it (the host emits at most one such pass per transform, and only for
 // power-of-two parts that are not sums of those).  Kept out of line so that
 // its register needs do not add to the main loop's.
-template <class Cx, bool INV, int E>
+template <class Cx, bool INV, int E, bool SWZ = false>
 __device__ __noinline__ void fft_tail_pass(Cx* buf, const FftSched& S,
                                            const typename TwArg<Cx>::type& tws, int Ns, int R,
                                            int tid) {
   if constexpr (E % 16 == 0) {
-    if (R == 16) fft_pass<Cx, INV, 16, E>(buf, S, tws, Ns, tid);
+    if (R == 16) fft_pass<Cx, INV, 16, E, SWZ>(buf, S, tws, Ns, tid);
   }
   if constexpr (E % 8 == 0) {
-    if (R == 8) fft_pass<Cx, INV, 8, E>(buf, S, tws, Ns, tid);
+    if (R == 8) fft_pass<Cx, INV, 8, E, SWZ>(buf, S, tws, Ns, tid);
   }
   if constexpr (E % 4 == 0) {
-    if (R == 4) fft_pass<Cx, INV, 4, E>(buf, S, tws, Ns, tid);
+    if (R == 4) fft_pass<Cx, INV, 4, E, SWZ>(buf, S, tws, Ns, tid);
   }
   if constexpr (E % 2 == 0) {
-    if (R == 2) fft_pass<Cx, INV, 2, E>(buf, S, tws, Ns, tid);
+    if (R == 2) fft_pass<Cx, INV, 2, E, SWZ>(buf, S, tws, Ns, tid);
   }
 }
 
@@ -461,7 +471,7 @@ __host__ __device__ constexpr int main_radix() {
 // radix 3 (inline); the exception runs out of line.
 // tid is the thread's index among the S.T threads of this transform (several
 // independent transforms may share a CTA); every thread of the CTA calls it.
-template <class Cx, bool INV, int E>
+template <class Cx, bool INV, int E, bool SWZ = false>
 __device__ __forceinline__ void fft_inplace(Cx* buf, const FftSched& S,
                                             const typename TwArg<Cx>::type& tws,
                                             int tid = threadIdx.x) {
@@ -471,17 +481,17 @@ __device__ __forceinline__ void fft_inplace(Cx* buf, const FftSched& S,
   for (int p = 0; p < S.npass; p++) {
     const int R = S.radix[p];
     if (R == RM) {
-      fft_pass<Cx, INV, RM, E>(buf, S, tws, Ns, tid);
+      fft_pass<Cx, INV, RM, E, SWZ>(buf, S, tws, Ns, tid);
     } else if (sizeof(Cx) == 8 && RM >= 4 && R == RM / 2) {
       // FP32 transforms (once per IMF) keep the half-radix pass inline; the
       // float-float forward transform (once per signal) calls it out of line
-      if constexpr (sizeof(Cx) == 8 && RM >= 4) fft_pass<Cx, INV, RM / 2, E>(buf, S, tws, Ns, tid);
+      if constexpr (sizeof(Cx) == 8 && RM >= 4) fft_pass<Cx, INV, RM / 2, E, SWZ>(buf, S, tws, Ns, tid);
     } else if (E % 9 == 0 && R == 9) {
-      if constexpr (E % 9 == 0) fft_pass<Cx, INV, 9, E>(buf, S, tws, Ns, tid);
+      if constexpr (E % 9 == 0) fft_pass<Cx, INV, 9, E, SWZ>(buf, S, tws, Ns, tid);
     } else if (E % 3 == 0 && R == 3) {
-      if constexpr (E % 3 == 0 && RM != 3) fft_pass<Cx, INV, 3, E>(buf, S, tws, Ns, tid);
+      if constexpr (E % 3 == 0 && RM != 3) fft_pass<Cx, INV, 3, E, SWZ>(buf, S, tws, Ns, tid);
     } else {
-      fft_tail_pass<Cx, INV, E>(buf, S, tws, Ns, R, tid);
+      fft_tail_pass<Cx, INV, E, SWZ>(buf, S, tws, Ns, R, tid);
     }
     Ns *= R;
   }

@@ -33,6 +33,8 @@ struct FftSched {
   int tw_entries;              // entries of the shared twiddle table: n / 2^tw_fold + 1
                                // (stored in tw_slots() slots, see tw_slot)
   int tw_shared;               // 1 if the fused kernel keeps the table in shared memory
+  int swz;                     // multi-pass FP32 levels: XOR mask of the swizzled column
+                               // layout (work_slot, whole 16-point blocks), 0: plain
   const float2* tw;            // [n]  exp(-2 pi i t/n), rounded from binary64
   const float2* tw_lo;         // [n]  binary64 value minus tw, rounded (float-float twiddles)
   const float2* wtab;          // [Lmax * P]  row L-1: {log2(1 - w_hat_k), w_hat_k}
@@ -152,6 +154,8 @@ struct LgSched {
 // round; each CTA leaves one partial per candidate (kSelPartBytes each, FP32
 // screen and binary64 tie-break side by side).
 constexpr int kSelCand = 8;
+// Points of padding between the columns of an FP32 level tile in shared memory.
+constexpr int kLgColPad = 4;
 constexpr int kSelBlocksMax = 1024;
 constexpr int kSelPartBytes = 48;
 constexpr int kLgStateWords = 32;

@@ -145,7 +145,10 @@ __global__ void lg_pack(const LgSig* __restrict__ sigs, LgSched G, const float* 
 // One pass of TJ sub-FFTs of R points per CTA.  LV 1: butterflies j (Ns = 1)
 // read x[j + r Nc/R1], write y[j R1 + r].  LV 2: butterflies j = k < R1
 // (Ns = R1) read y[j + r R1] times W^(r j), write z[j + r R1].
-template <class Cx, bool INV, int E, int LV, bool TC = false>
+// SWZ (FP32 levels with S.swz set): columns kLgColPad points apart beyond R
+// (the transposed tile stores of adjacent columns meet different banks), each
+// in the swizzled layout of S.swz (work_slot).
+template <class Cx, bool INV, int E, int LV, bool TC = false, bool SWZ = false>
 __global__ void __launch_bounds__(512, sizeof(Cx) == 8 ? 2 : 1) lg_level(const LgSig* __restrict__ sigs, LgSched G) {
   extern __shared__ __align__(16) unsigned char smem[];
   const LgSig sg = sigs[blockIdx.y];
@@ -170,6 +173,8 @@ __global__ void __launch_bounds__(512, sizeof(Cx) == 8 ? 2 : 1) lg_level(const L
   const int tid = threadIdx.x, nt = blockDim.x;
   const int j0 = blockIdx.x * TJ;
   const int tile = TJ * R;  // at most E elements per thread (nt >= TJ R / E)
+  const int Rp = SWZ ? R + kLgColPad : R;
+  auto cslot = [&](int g, int r) { return g * Rp + (SWZ ? work_slot(r, SR.swz) : r); };
   // element f = tid + u nt of the tile is row r = f / TJ of column g = f % TJ;
   // when TJ divides nt, r = r0 + u nt / TJ and g = g0 (no division per element)
   const bool tj_div = nt % TJ == 0;
@@ -203,7 +208,7 @@ __global__ void __launch_bounds__(512, sizeof(Cx) == 8 ? 2 : 1) lg_level(const L
         int r, g;
         row_col(u, f, r, g);
         if (LV == 2) v[u] = cmul(v[u], inter_twiddle<Cx, INV>(G, r * (j0 + g)));
-        buf[g * R + r] = v[u];
+        buf[cslot(g, r)] = v[u];
       }
     }
   }
@@ -211,7 +216,7 @@ __global__ void __launch_bounds__(512, sizeof(Cx) == 8 ? 2 : 1) lg_level(const L
   if constexpr (!FF) {
     // the folded table in shared memory, unless the schedule has a per-pass table
     if (!SR.ptw) {
-      q = reinterpret_cast<float2*>(smem + (size_t)TJ * R * sizeof(Cx));
+      q = reinterpret_cast<float2*>(smem + (size_t)TJ * Rp * sizeof(Cx));
       for (int u = tid; u < SR.tw_entries; u += nt) {
         const float2 w = __ldg(&SR.tw[u]);
         q[tw_slot(u)] = make_float2(w.x, -w.y);
@@ -221,22 +226,27 @@ __global__ void __launch_bounds__(512, sizeof(Cx) == 8 ? 2 : 1) lg_level(const L
   __syncthreads();
   const int T = SR.T, g = tid / T;
   const int lt = g < TJ ? tid - g * T : T;  // T: inactive in the sub-FFT
-  Cx* mine = buf + (size_t)(g < TJ ? g : 0) * R;
+  Cx* mine = buf + (size_t)(g < TJ ? g : 0) * Rp;
   if constexpr (FF) {
     fft_inplace<Cx, INV, E>(mine, SR, SR, lt);
   } else {
     const TwSrc ts{q, SR.tw, SR.n, SR.tw_fold, SR.ptw};
     if constexpr (TC)
-      fft_inplace_tc<INV>(reinterpret_cast<float2*>(mine), SR, ts, lt);
+      fft_inplace_tc<INV, SWZ>(reinterpret_cast<float2*>(mine), SR, ts, lt);
     else
-      fft_inplace<Cx, INV, E>(mine, SR, ts, lt);
+      fft_inplace<Cx, INV, E, SWZ>(mine, SR, ts, lt);
   }
   if (LV == 1) {
     // column j0 + gg, row r goes to (j0 + gg) R + r = j0 R + f
+    const bool rp2 = (R & (R - 1)) == 0;
+    const int rs = __ffs(R) - 1;
 #pragma unroll
     for (int u = 0; u < E; u++) {
       const int f = tid + u * nt;
-      if (f < tile) out[(size_t)j0 * R + f] = buf[f];
+      if (f < tile) {
+        const int gg = TJ == 1 ? 0 : rp2 ? f >> rs : f / R, r = f - gg * R;
+        out[(size_t)j0 * R + f] = buf[cslot(gg, r)];
+      }
     }
   } else {
 #pragma unroll
@@ -245,7 +255,7 @@ __global__ void __launch_bounds__(512, sizeof(Cx) == 8 ? 2 : 1) lg_level(const L
       if (f < tile) {
         int r, gg;
         row_col(u, f, r, gg);
-        out[j0 + gg + r * G.R1] = buf[gg * R + r];
+        out[j0 + gg + r * G.R1] = buf[cslot(gg, r)];
       }
     }
   }
@@ -1170,7 +1180,7 @@ size_t large_level_smem(const LgSched& G, int level, bool ff) {
   const int R = level == 1 ? G.R1 : G.R2;
   const FftSched& SR = ff ? (level == 1 ? G.F1 : G.F2) : (level == 1 ? G.S1 : G.S2);
   const int TJ = ff ? (level == 1 ? G.TJF1 : G.TJF2) : (level == 1 ? G.TJ1 : G.TJ2);
-  size_t b = (size_t)TJ * R * (ff ? 16 : 8);
+  size_t b = (size_t)TJ * (!ff && SR.swz ? R + kLgColPad : R) * (ff ? 16 : 8);
   if (!ff && !SR.ptw) b += tw_slots(SR) * sizeof(float2);
   return b;
 }
@@ -1190,7 +1200,19 @@ static cudaError_t launch_level(const LgSched& G, const LgSig* d_sigs, int nsig,
   if constexpr (!FF && INV) {
     if (LV == 1 ? G.tc1 : G.tc2) {  // split-BF16 tensor-core radix-16 passes (E = 16)
       if (SR.E != 16) return cudaErrorInvalidValue;
-      lg_level<Cx, INV, 16, LV, true><<<grid, threads, smem, st>>>(d_sigs, G);
+      if (SR.swz)
+        lg_level<Cx, INV, 16, LV, true, true><<<grid, threads, smem, st>>>(d_sigs, G);
+      else
+        lg_level<Cx, INV, 16, LV, true><<<grid, threads, smem, st>>>(d_sigs, G);
+      return cudaGetLastError();
+    }
+    if (SR.swz) {  // swizzled columns (E = 8 and 16 schedules only)
+      if (SR.E == 8)
+        lg_level<Cx, INV, 8, LV, false, true><<<grid, threads, smem, st>>>(d_sigs, G);
+      else if (SR.E == 16)
+        lg_level<Cx, INV, 16, LV, false, true><<<grid, threads, smem, st>>>(d_sigs, G);
+      else
+        return cudaErrorInvalidValue;
       return cudaGetLastError();
     }
   }
@@ -1212,8 +1234,19 @@ static cudaError_t level_attr(const LgSched& G, int smem) {
   const FftSched& SR = sizeof(Cx) == 16 ? (LV == 1 ? G.F1 : G.F2) : (LV == 1 ? G.S1 : G.S2);
   if constexpr (sizeof(Cx) == 8 && INV) {
     if (LV == 1 ? G.tc1 : G.tc2)
-      return cudaFuncSetAttribute(lg_level<Cx, INV, 16, LV, true>,
-                                  cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+      return SR.swz ? cudaFuncSetAttribute(lg_level<Cx, INV, 16, LV, true, true>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, smem)
+                    : cudaFuncSetAttribute(lg_level<Cx, INV, 16, LV, true>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (SR.swz) {
+      if (SR.E == 8)
+        return cudaFuncSetAttribute(lg_level<Cx, INV, 8, LV, false, true>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+      if (SR.E == 16)
+        return cudaFuncSetAttribute(lg_level<Cx, INV, 16, LV, false, true>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+      return cudaErrorInvalidValue;
+    }
   }
   switch (SR.E) {
 #define FIF_CASE(e) \

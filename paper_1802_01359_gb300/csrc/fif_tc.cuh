@@ -110,9 +110,11 @@ __device__ __forceinline__ void mma3(float (&d)[4], const uint32_t (&ahi)[4], co
 // multiple of 32 when there is more than one), S.T or more for threads
 // without a butterfly.  The warp's first butterfly is lane 0's index (the
 // same in every lane; T or more for a warp without butterflies).
-template <bool INV>
+// SWZ: the buffer is in the swizzled layout of S.swz (work_slot).
+template <bool INV, bool SWZ = false>
 __device__ __forceinline__ void fft_pass16_tc(float2* buf, const FftSched& S, const TwSrc& ts,
                                               int Ns, const TcDft16& A, int lt) {
+  auto slot = [&](int i) { return SWZ ? work_slot(i, S.swz) : i; };
   const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
   const int T = S.T, stride = S.Nc / 16, warp0 = __shfl_sync(0xffffffffu, lt, 0);
   const bool p2 = (Ns & (Ns - 1)) == 0;  // j mod Ns by a mask (2^a lengths)
@@ -125,7 +127,7 @@ __device__ __forceinline__ void fft_pass16_tc(float2* buf, const FftSched& S, co
 #pragma unroll
     for (int s = 0; s < 4; s++) {
       const int r = 2 * t + (s & 1) + 8 * (s >> 1);
-      x[q][s] = jb < T ? buf[jb + r * stride] : make_float2(0.f, 0.f);
+      x[q][s] = jb < T ? buf[slot(jb + r * stride)] : make_float2(0.f, 0.f);
     }
   }
   __syncthreads();
@@ -165,8 +167,8 @@ __device__ __forceinline__ void fft_pass16_tc(float2* buf, const FftSched& S, co
       if (jo < T) {
         const int ko = modNs(jo);
         const int base = (jo - ko) * 16 + ko;
-        buf[base + g * Ns] = make_float2(yr[c], yi[c]);
-        buf[base + (g + 8) * Ns] = make_float2(yr[2 + c], yi[2 + c]);
+        buf[slot(base + g * Ns)] = make_float2(yr[c], yi[c]);
+        buf[slot(base + (g + 8) * Ns)] = make_float2(yr[2 + c], yi[2 + c]);
       }
     }
   }
@@ -175,7 +177,7 @@ __device__ __forceinline__ void fft_pass16_tc(float2* buf, const FftSched& S, co
 
 // Complex FFT of S.Nc points with every radix-16 pass on the tensor cores
 // (E = 16 schedules; the other passes as fft_inplace).
-template <bool INV>
+template <bool INV, bool SWZ = false>
 __device__ __forceinline__ void fft_inplace_tc(float2* buf, const FftSched& S, const TwSrc& ts,
                                                int lt = threadIdx.x) {
   const TcDft16 A = tc_dft16_fragments<INV>();
@@ -184,11 +186,11 @@ __device__ __forceinline__ void fft_inplace_tc(float2* buf, const FftSched& S, c
   for (int p = 0; p < S.npass; p++) {
     const int R = S.radix[p];
     if (R == 16) {
-      fft_pass16_tc<INV>(buf, S, ts, Ns, A, lt);
+      fft_pass16_tc<INV, SWZ>(buf, S, ts, Ns, A, lt);
     } else if (R == 8) {
-      fft_pass<float2, INV, 8, 16>(buf, S, ts, Ns, lt);
+      fft_pass<float2, INV, 8, 16, SWZ>(buf, S, ts, Ns, lt);
     } else {
-      fft_tail_pass<float2, INV, 16>(buf, S, ts, Ns, R, lt);
+      fft_tail_pass<float2, INV, 16, SWZ>(buf, S, ts, Ns, R, lt);
     }
     Ns *= R;
   }
