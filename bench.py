@@ -412,6 +412,11 @@ def main():
     ap.add_argument("--plain-signals", type=int, default=64)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-tune", action="store_true", help="fixed schedules, no autotuning")
+    ap.add_argument("--schedule", default="",
+                    help="schedules to load instead of autotuning, in the plan's tuning-file line "
+                         "format ('n E' fused, 'n E1 TJ1 E2 TJ2' multi-pass), lines separated by "
+                         "';' (reproduces a tuned run under a profiler, whose timings would "
+                         "mislead the tuner)")
     ap.add_argument("--signals", type=int, default=0,
                     help="decompose only the first N signals of the workload (reduced cases for "
                          "profiler captures); 0 = all")
@@ -464,7 +469,13 @@ def main():
     plan.prepare(sorted(set(int(v) for v in lens)))
     out = plan.alloc_batch_outputs(lens, dev)
     tune_s = None
-    if not args.no_tune:
+    if args.schedule:
+        import tempfile
+        with tempfile.NamedTemporaryFile("w", suffix=".txt", delete=False) as f:
+            f.write("\n".join(ln.strip() for ln in args.schedule.split(";")) + "\n")
+        plan.load_tuning(f.name)
+        os.unlink(f.name)
+    elif not args.no_tune:
         # schedule autotuning per length class, before (and outside) the timed region
         t0 = time.perf_counter()
         with torch.cuda.stream(stream):
@@ -540,7 +551,8 @@ def main():
                    "path": "fused batch (one CTA per signal, shared-memory resident)" if fused_only
                    else "batch: fused for short signals, multi-pass for long ones, one CUDA graph",
                    "l2": f"flushed between steps ({L2_FLUSH_BYTES >> 20} MiB write)",
-                   "schedule": ("fixed rule" if tune_s is None
+                   "schedule": ("loaded (--schedule)" if args.schedule
+                                else "fixed rule" if tune_s is None
                                 else f"autotuned per length class (fif_plan_tune, {tune_s:.2f} s "
                                      "before timing)") + ("; " + "; ".join(chosen) if chosen else ""),
                    "mean_imfs": float(nim.mean())},
