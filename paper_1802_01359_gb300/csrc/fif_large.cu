@@ -1083,20 +1083,32 @@ __global__ void __launch_bounds__(256, 8) lg_epilogue_ext(const LgSig* __restric
   float imax = 0.f, rmax = 0.f;
   int ext = 0, zc = 0, tie = 0, step;
   if (!odd) {
-    for (int t = first_signal_point(step); t < G.S.Nc; t += step) {
-      const float2 z = w2[t];
+    // sample pairs (2t, 2t+1) as float2: the remainder buffers are plan-allocated
+    // (8-byte aligned), the IMF row is whenever its offset is even; the neighbours
+    // 2t-1, 2t+2, 2t+3 come from the pairs t-1 and t+1 (cyclically), with the same
+    // arithmetic as new_rem
+    const float2* ro2 = reinterpret_cast<const float2*>(ro);
+    float2* rn2 = reinterpret_cast<float2*>(rn);
+    const bool vec = (reinterpret_cast<uintptr_t>(orow) & 7) == 0;
+    const int Nc = G.S.Nc;
+    for (int t = first_signal_point(step); t < Nc; t += step) {
+      const int tm = t == 0 ? Nc - 1 : t - 1, tp = t + 1 == Nc ? 0 : t + 1;
+      const float2 z = w2[t], zm = w2[tm], zp = w2[tp];
+      const float2 q = ro2[t], qm = ro2[tm], qp = ro2[tp];
       const float a = z.x * inv_n, b = z.y * inv_n;
-      orow[2 * t] = a;
-      orow[2 * t + 1] = b;
-      const float r0 = ro[2 * t] - a, r1 = ro[2 * t + 1] - b;
-      rn[2 * t] = r0;
-      rn[2 * t + 1] = r1;
+      if (vec) {
+        *reinterpret_cast<float2*>(orow + 2 * (size_t)t) = make_float2(a, b);
+      } else {
+        orow[2 * t] = a;
+        orow[2 * t + 1] = b;
+      }
+      const float r0 = q.x - a, r1 = q.y - b;
+      rn2[t] = make_float2(r0, r1);
       imax = fmaxf(imax, fmaxf(fabsf(a), fabsf(b)));
       rmax = fmaxf(rmax, fmaxf(fabsf(r0), fabsf(r1)));
-      const int s0 = 2 * t;
-      const float rm1 = new_rem(ro, w2, s0 == 0 ? n - 1 : s0 - 1, false, inv_n);
-      const float r2 = new_rem(ro, w2, s0 + 2 >= n ? s0 + 2 - n : s0 + 2, false, inv_n);
-      const float r3 = new_rem(ro, w2, s0 + 3 >= n ? s0 + 3 - n : s0 + 3, false, inv_n);
+      const float rm1 = qm.y - zm.y * inv_n;
+      const float r2 = qp.x - zp.x * inv_n;
+      const float r3 = qp.y - zp.y * inv_n;
       pair_terms(rm1, r0, r1, r2, r3, tau, ext, zc, tie);
     }
   } else {
