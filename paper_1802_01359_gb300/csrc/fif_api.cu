@@ -572,11 +572,13 @@ bool make_sub_sched(int R, FftSched& s) {
   return make_fft_plan(R, s);
 }
 
-// The swizzled column layout of an FP32 level (work_slot; kernels for the
-// E = 8 and 16 schedules of sub-FFTs in whole 16-point blocks): mask 15, else
-// 0 (plain layout, no slot arithmetic).  Measured on the 4096 x 2048 levels of
-// n = 2^24: both levels about 21 % faster (the first pass's 16-way store
-// conflicts gone); neutral on the uneven batch's lengths.
+// The swizzled column layout of a level (work_slot; kernels for the FP32
+// levels' E = 8 and 16 schedules and the float-float forward levels' E = 8
+// schedules of sub-FFTs in whole 16-point blocks): mask 15, else
+// 0 (plain layout, no slot arithmetic).  Measured on the 4096 x 2048 FP32
+// inverse levels of n = 2^24: both about 21 % faster (the first pass's 16-way
+// store conflicts gone); the float-float forward levels gain less (0.7 % of a
+// 2^24 decomposition); neutral on the uneven batch's lengths.
 int level_swizzle(int R, int E) { return R % 16 == 0 && (E == 8 || E == 16) ? 15 : 0; }
 
 int pick_tj(int R, int T, int count, size_t elem, size_t extra, int smem_limit) {
@@ -619,6 +621,8 @@ bool make_large_sched(int64_t n64, int smem_limit, LgSched& G) {
   G.F2 = G.S2;
   G.S1.swz = level_swizzle(G.R1, G.S1.E);
   G.S2.swz = level_swizzle(G.R2, G.S2.E);
+  G.F1.swz = G.F1.E == 8 ? level_swizzle(G.R1, 8) : 0;  // (float-float kernels: E = 8 only)
+  G.F2.swz = G.F2.E == 8 ? level_swizzle(G.R2, 8) : 0;
   G.TJF1 = pick_tj(G.R1, G.F1.T, G.R2, 16, 0, smem_limit);
   G.TJF2 = pick_tj(G.R2, G.F2.T, G.R1, 16, 0, smem_limit);
   if (!G.TJ1 || !G.TJ2 || !G.TJF1 || !G.TJF2) return false;

@@ -145,7 +145,7 @@ __global__ void lg_pack(const LgSig* __restrict__ sigs, LgSched G, const float* 
 // One pass of TJ sub-FFTs of R points per CTA.  LV 1: butterflies j (Ns = 1)
 // read x[j + r Nc/R1], write y[j R1 + r].  LV 2: butterflies j = k < R1
 // (Ns = R1) read y[j + r R1] times W^(r j), write z[j + r R1].
-// SWZ (FP32 levels with S.swz set): columns kLgColPad points apart beyond R
+// SWZ (levels with S.swz set): columns kLgColPad points apart beyond R
 // (the transposed tile stores of adjacent columns meet different banks), each
 // in the swizzled layout of S.swz (work_slot).
 template <class Cx, bool INV, int E, int LV, bool TC = false, bool SWZ = false>
@@ -228,7 +228,7 @@ __global__ void __launch_bounds__(512, sizeof(Cx) == 8 ? 2 : 1) lg_level(const L
   const int lt = g < TJ ? tid - g * T : T;  // T: inactive in the sub-FFT
   Cx* mine = buf + (size_t)(g < TJ ? g : 0) * Rp;
   if constexpr (FF) {
-    fft_inplace<Cx, INV, E>(mine, SR, SR, lt);
+    fft_inplace<Cx, INV, E, SWZ>(mine, SR, SR, lt);
   } else {
     const TwSrc ts{q, SR.tw, SR.n, SR.tw_fold, SR.ptw};
     if constexpr (TC)
@@ -1192,7 +1192,7 @@ size_t large_level_smem(const LgSched& G, int level, bool ff) {
   const int R = level == 1 ? G.R1 : G.R2;
   const FftSched& SR = ff ? (level == 1 ? G.F1 : G.F2) : (level == 1 ? G.S1 : G.S2);
   const int TJ = ff ? (level == 1 ? G.TJF1 : G.TJF2) : (level == 1 ? G.TJ1 : G.TJ2);
-  size_t b = (size_t)TJ * (!ff && SR.swz ? R + kLgColPad : R) * (ff ? 16 : 8);
+  size_t b = (size_t)TJ * (SR.swz ? R + kLgColPad : R) * (ff ? 16 : 8);
   if (!ff && !SR.ptw) b += tw_slots(SR) * sizeof(float2);
   return b;
 }
@@ -1228,6 +1228,13 @@ static cudaError_t launch_level(const LgSched& G, const LgSig* d_sigs, int nsig,
       return cudaGetLastError();
     }
   }
+  if constexpr (FF) {
+    if (SR.swz) {  // swizzled columns (the forward levels' E = 8 schedules)
+      if (SR.E != 8) return cudaErrorInvalidValue;
+      lg_level<Cx, INV, 8, LV, false, true><<<grid, threads, smem, st>>>(d_sigs, G);
+      return cudaGetLastError();
+    }
+  }
   switch (SR.E) {
 #define FIF_CASE(e)                                                   \
   case e:                                                             \
@@ -1259,6 +1266,12 @@ static cudaError_t level_attr(const LgSched& G, int smem) {
                                     cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
       return cudaErrorInvalidValue;
     }
+  }
+  if constexpr (sizeof(Cx) == 16) {
+    if (SR.swz)
+      return SR.E == 8 ? cudaFuncSetAttribute(lg_level<Cx, INV, 8, LV, false, true>,
+                                              cudaFuncAttributeMaxDynamicSharedMemorySize, smem)
+                       : cudaErrorInvalidValue;
   }
   switch (SR.E) {
 #define FIF_CASE(e) \
